@@ -1,0 +1,169 @@
+/*
+ * aimx.h -- C ABI of the GB300 AIMx library.
+ *
+ * AIMx (Sharma & Triverio, "AIMx: An Extended Adaptive Integral Method for the
+ * Fast Electromagnetic Modeling of Complex Structures", arXiv 2009.02281)
+ * writes every surface-integral operator as
+ *
+ *     A(k) = (L_s,NR - L_s,P) + W H(k) P                      (Eq. LAIMx, Eq. KAIMx)
+ *
+ * with a frequency-independent sparse near part built once (Sec. III-A) and a
+ * frequency-dependent part evaluated on a regular auxiliary grid by a
+ * zero-padded FFT convolution (Sec. II-B, Eq. aimLFR) whose kernel carries
+ * the modified self term H(0) = -jk / (4 pi) (Eq. Hmm).
+ *
+ * Conventions shared by every entry point
+ *   - Time dependence e^{j w t}.  Complex numbers are interleaved (re, im).
+ *   - Unknown vectors are RHS-major: element (b, n) of an [nrhs][nunk] array
+ *     sits at index b * nunk + n.  nunk = N (EFIE) or 2N (PMCHWT: [J ; M/eta0])
+ *     where N is the number of RWG functions (one per interior mesh edge,
+ *     ordered by (smaller vertex id, larger vertex id)).
+ *   - Pointers documented as "device" must be CUDA device memory of the
+ *     current device; "host" pointers are ordinary host memory.  The caller
+ *     keeps ownership of everything it passes in; the context owns all memory
+ *     it allocates and frees it in aimx_destroy.
+ *   - stream is a cudaStream_t passed as void*; NULL means the legacy default
+ *     stream.  Calls that take a stream are asynchronous with respect to the
+ *     host unless stated otherwise.
+ *   - Every call returns an int status: AIMX_OK (0), a negative error, or a
+ *     positive warning.  No call aborts the process or throws; the message of
+ *     the last failure is available from aimx_last_error.
+ */
+#ifndef AIMX_H
+#define AIMX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+#define AIMX_OK          0
+#define AIMX_E_ARG      -1   /* invalid argument (null pointer, size <= 0, bad enum)  */
+#define AIMX_E_MESH     -2   /* degenerate triangle, edge shared by > 2 triangles,
+                                inconsistent orientation                               */
+#define AIMX_E_GRID     -3   /* a basis stencil falls outside the grid                 */
+#define AIMX_E_NOMEM    -4   /* device or host allocation failed                       */
+#define AIMX_E_CUDA     -5   /* a CUDA runtime call failed                             */
+#define AIMX_E_TIMEOUT  -6   /* a bounded device wait expired                          */
+#define AIMX_E_STATE    -7   /* call not valid for this context (e.g. wrong formulation) */
+#define AIMX_E_NOCONV    1   /* warning: at least one RHS missed the solver tolerance  */
+
+/* ------------------------------------------------------------------ inputs */
+
+/* Closed (or open) triangle mesh.  xyz: host [nv][3] float64 coordinates in
+ * metres; tri: host [nt][3] int32 vertex ids, counter-clockwise when seen from
+ * the side the normal points to (outward for a closed body).  Copied by
+ * aimx_setup.  Sec. II-A: RWG functions on pairs of adjacent triangles. */
+typedef struct {
+    int32_t nv;
+    int32_t nt;
+    const double* xyz;
+    const int32_t* tri;
+} aimx_mesh;
+
+#define AIMX_EFIE    0   /* PEC body in a homogeneous background (Eq. EFIEAIMx)          */
+#define AIMX_PMCHWT  1   /* penetrable body, two regions, unknowns [J ; M/eta0]            */
+
+/* Materials.  Relative permittivity / permeability of the background (region
+ * 1) and, for AIMX_PMCHWT, of the body (region 2).  Lossless values only. */
+typedef struct {
+    int32_t formulation;
+    double eps_out, mu_out;
+    double eps_in, mu_in;
+} aimx_material;
+
+/* Auxiliary grid (Sec. II-B).  n: nodes per axis (required).  h: spacing per
+ * axis; all zero = derived from the vertex bounding box as
+ * h_a = (hi_a - lo_a) / (n_a - 1 - 2m), origin_a = lo_a - m h_a with margin
+ * m = floor((order + 1) / 2).  When h is given, origin must be given too.
+ * near_radius: near-region radius in cells (Chebyshev distance of stencil
+ * anchors), 0 = 3.  pad: zero-padded FFT length per axis, 0 = smallest power
+ * of two >= 2 n_a - 1 (any value >= 2 n_a - 1 gives the same product). */
+typedef struct {
+    int32_t n[3];
+    double h[3];
+    double origin[3];
+    int32_t near_radius;
+    int32_t pad[3];
+} aimx_grid;
+
+typedef struct aimx_ctx aimx_ctx;
+
+/* Sizes of a context (filled by aimx_info). */
+typedef struct {
+    int32_t n_basis;       /* N, RWG functions                       */
+    int32_t n_unknowns;    /* N (EFIE) or 2N (PMCHWT)                */
+    int64_t near_nnz;      /* stored near pairs (m, n), m = n included */
+    int32_t grid_n[3];
+    int32_t pad[3];
+    double grid_h[3];
+    double grid_origin[3];
+    int32_t order;
+    int32_t formulation;
+    int64_t device_bytes;  /* device memory held by the context      */
+} aimx_info_t;
+
+/* ------------------------------------------------------------------ lifecycle */
+
+/* Build a context: RWG functions, grid, stencil anchors (Sec. II-B),
+ * moment-matching projection weights P (W = P^T), the near-region pair list
+ * and the frequency-independent near matrices N = L_s,NR - L_s,P for the
+ * vector potential, scalar potential and K operator (Eqs. Lmatdecomp2,
+ * aimLPs, KAIMx), all in FP64 on the current device.  order: stencil order n
+ * (n + 1 nodes per axis), 1..3.  Errors: AIMX_E_ARG, AIMX_E_MESH, AIMX_E_GRID,
+ * AIMX_E_NOMEM, AIMX_E_CUDA.  Synchronous. */
+int aimx_setup(const aimx_mesh* mesh, const aimx_material* mat, const aimx_grid* grid,
+               int order, aimx_ctx** out);
+
+/* Free every resource of ctx (NULL is accepted).  Synchronises the device. */
+int aimx_destroy(aimx_ctx* ctx);
+
+int aimx_info(const aimx_ctx* ctx, aimx_info_t* out);
+
+/* Human-readable text for a status code (static storage). */
+const char* aimx_status_string(int status);
+
+/* Message of the last failure on ctx (static per context; "" when none). */
+const char* aimx_last_error(const aimx_ctx* ctx);
+
+/* ------------------------------------------------------------------ hot path */
+
+#define AIMX_F32 0
+#define AIMX_F64 1
+
+/* y = A(k) x for nrhs vectors (Eq. EFIEAIMx for AIMX_EFIE; the two-region form
+ * for AIMX_PMCHWT), at frequency freq in Hz:
+ *   projection P onto the grid, zero-padded 3-D FFT convolution with the grid
+ *   kernels H(k) (and grad H(k) for the K operator), interpolation W = P^T,
+ *   and the sparse near correction.
+ * x, y: device [nrhs][nunk] complex (float2 for AIMX_F32, double2 for
+ * AIMX_F64), x and y must not overlap.  The grid kernels for freq are
+ * generated on the first call at that frequency and cached.  Work buffers are
+ * grown on demand (the first call at a new nrhs may allocate).  Asynchronous
+ * on stream; errors of queued work surface at the next synchronising call. */
+int aimx_matvec(aimx_ctx* ctx, double freq, int nrhs, const void* x, void* y,
+                int precision, void* stream);
+
+/* Same product with host arrays x, y ([nrhs][nunk] complex, same precision
+ * rules); copies in, runs aimx_matvec, copies out and synchronises stream. */
+int aimx_matvec_host(aimx_ctx* ctx, double freq, int nrhs, const void* x, void* y,
+                     int precision, void* stream);
+
+/* ------------------------------------------------------------------ export (tests) */
+
+/* Copy setup products to host arrays (any pointer may be NULL to skip it).
+ * Order and layout follow the caller's RWG numbering:
+ *   anchors  int32 [N][3]           stencil start node (x, y, z)
+ *   weights  double [N][(n+1)^3][4] projection weights (x, y, z, rho)
+ *   row_ptr  int64 [N+1], cols int32 [nnz]  near pairs, columns ascending
+ *   na, nphi, nk double [nnz]       near matrices N^A, N^Phi, N^K
+ * Synchronous. */
+int aimx_export_setup(const aimx_ctx* ctx, int32_t* anchors, double* weights,
+                      int64_t* row_ptr, int32_t* cols, double* na, double* nphi, double* nk);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AIMX_H */

@@ -1,0 +1,7 @@
+"""GB300-native AIMx: the accelerated surface-integral-equation matvec, solve and sweep.
+
+The compute path is the CUDA library ``libaimx.so`` (sources in ``csrc/``, C ABI in
+``include/aimx.h``); ``aimx`` is its thin ctypes binding.
+"""
+
+from .aimx import (AimxError, Context, EFIE, PMCHWT, F32, F64, load)  # noqa: F401

@@ -1,0 +1,200 @@
+"""ctypes binding of libaimx (argument marshalling only; every step runs in the library).
+
+The library must have been built (``paper_2009_02281_gb300.build.build()``);
+there is no fallback: a missing library raises ``AimxError``.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+EFIE = 0
+PMCHWT = 1
+F32 = 0
+F64 = 1
+
+_STATUS = {0: "ok", -1: "invalid argument", -2: "invalid mesh", -3: "stencil outside the grid",
+           -4: "out of memory", -5: "CUDA error", -6: "bounded device wait expired",
+           -7: "call not valid for this context", 1: "solver did not reach the tolerance"}
+
+
+class AimxError(RuntimeError):
+    def __init__(self, code, msg=""):
+        super().__init__("aimx status %d (%s)%s" % (code, _STATUS.get(code, "?"), (": " + msg) if msg else ""))
+        self.code = code
+
+
+class _Mesh(ctypes.Structure):
+    _fields_ = [("nv", ctypes.c_int32), ("nt", ctypes.c_int32),
+                ("xyz", ctypes.POINTER(ctypes.c_double)), ("tri", ctypes.POINTER(ctypes.c_int32))]
+
+
+class _Material(ctypes.Structure):
+    _fields_ = [("formulation", ctypes.c_int32), ("eps_out", ctypes.c_double), ("mu_out", ctypes.c_double),
+                ("eps_in", ctypes.c_double), ("mu_in", ctypes.c_double)]
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32 * 3), ("h", ctypes.c_double * 3), ("origin", ctypes.c_double * 3),
+                ("near_radius", ctypes.c_int32), ("pad", ctypes.c_int32 * 3)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("n_basis", ctypes.c_int32), ("n_unknowns", ctypes.c_int32), ("near_nnz", ctypes.c_int64),
+                ("grid_n", ctypes.c_int32 * 3), ("pad", ctypes.c_int32 * 3), ("grid_h", ctypes.c_double * 3),
+                ("grid_origin", ctypes.c_double * 3), ("order", ctypes.c_int32),
+                ("formulation", ctypes.c_int32), ("device_bytes", ctypes.c_int64)]
+
+
+_lib = None
+
+# (name, restype, argtypes) of every exported entry point
+_SIGS = [
+    ("aimx_setup", ctypes.c_int, [ctypes.POINTER(_Mesh), ctypes.POINTER(_Material), ctypes.POINTER(_Grid),
+                                  ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+    ("aimx_destroy", ctypes.c_int, [ctypes.c_void_p]),
+    ("aimx_info", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(_Info)]),
+    ("aimx_status_string", ctypes.c_char_p, [ctypes.c_int]),
+    ("aimx_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
+    ("aimx_matvec", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    ("aimx_matvec_host", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    ("aimx_export_setup", ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 7),
+]
+
+
+def lib_path():
+    return _build.LIB
+
+
+def load(build_if_missing=False):
+    """Load libaimx.so (optionally building it first); raises AimxError if it is absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not os.path.exists(path):
+        if build_if_missing:
+            _build.build()
+        else:
+            raise AimxError(-5, "libaimx.so not built at %s; run paper_2009_02281_gb300.build.build()" % path)
+    lib = ctypes.CDLL(path)
+    for name, res, args in _SIGS:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+class Context:
+    """An AIMx problem on the current CUDA device (wraps aimx_setup / aimx_destroy)."""
+
+    def __init__(self, xyz, tri, grid_n, order=2, formulation=EFIE, eps_out=1.0, mu_out=1.0,
+                 eps_in=1.0, mu_in=1.0, h=None, origin=None, near_radius=3, pad=None):
+        self._lib = load()
+        self._xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+        self._tri = np.ascontiguousarray(tri, dtype=np.int32)
+        mesh = _Mesh(len(self._xyz), len(self._tri),
+                     self._xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                     self._tri.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+        mat = _Material(formulation, eps_out, mu_out, eps_in, mu_in)
+        g = _Grid()
+        for a in range(3):
+            g.n[a] = int(grid_n[a])
+            g.h[a] = 0.0 if h is None else float(h[a])
+            g.origin[a] = 0.0 if origin is None else float(origin[a])
+            g.pad[a] = 0 if pad is None else int(pad[a])
+        g.near_radius = int(near_radius)
+        out = ctypes.c_void_p()
+        rc = self._lib.aimx_setup(ctypes.byref(mesh), ctypes.byref(mat), ctypes.byref(g), int(order),
+                                  ctypes.byref(out))
+        if rc != 0:
+            raise AimxError(rc)
+        self._ctx = out
+        self.info = self._info()
+        self.N = self.info["n_basis"]
+        self.nunk = self.info["n_unknowns"]
+        self.formulation = formulation
+
+    def _check(self, rc):
+        if rc < 0:
+            msg = self._lib.aimx_last_error(self._ctx)
+            raise AimxError(rc, msg.decode() if msg else "")
+        return rc
+
+    def _info(self):
+        inf = _Info()
+        self._check(self._lib.aimx_info(self._ctx, ctypes.byref(inf)))
+        return dict(n_basis=inf.n_basis, n_unknowns=inf.n_unknowns, near_nnz=inf.near_nnz,
+                    grid_n=tuple(inf.grid_n), pad=tuple(inf.pad), grid_h=tuple(inf.grid_h),
+                    grid_origin=tuple(inf.grid_origin), order=inf.order, formulation=inf.formulation,
+                    device_bytes=inf.device_bytes)
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            self._lib.aimx_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- hot path
+    def matvec(self, freq, x, y=None, stream=None):
+        """y = A(k) x for a CUDA tensor x [nrhs, nunk] (complex64 -> FP32, complex128 -> FP64)."""
+        import torch
+        if not x.is_cuda or not x.is_contiguous():
+            raise AimxError(-1, "x must be a contiguous CUDA tensor")
+        if x.dim() == 1:
+            x = x.unsqueeze(0)
+        prec = {torch.complex64: F32, torch.complex128: F64}.get(x.dtype)
+        if prec is None or x.shape[-1] != self.nunk:
+            raise AimxError(-1, "x must be complex64/complex128 with last dim = %d" % self.nunk)
+        if y is None:
+            y = torch.empty_like(x)
+        self._check(self._lib.aimx_matvec(self._ctx, float(freq), x.shape[0], ctypes.c_void_p(x.data_ptr()),
+                                          ctypes.c_void_p(y.data_ptr()), prec, _stream_handle(stream)))
+        return y
+
+    def matvec_host(self, freq, x, stream=None):
+        """Same product on host numpy arrays (copies in and out inside the library)."""
+        x = np.ascontiguousarray(np.atleast_2d(x))
+        prec = F64 if x.dtype == np.complex128 else F32
+        x = x.astype(np.complex128 if prec == F64 else np.complex64, copy=False)
+        y = np.empty_like(x)
+        self._check(self._lib.aimx_matvec_host(self._ctx, float(freq), x.shape[0], _ptr(x), _ptr(y), prec,
+                                               _stream_handle(stream)))
+        return y
+
+    # ---------------------------------------------------------------- export
+    def export_setup(self):
+        N, U = self.N, (self.info["order"] + 1) ** 3
+        nnz = self.info["near_nnz"]
+        anc = np.zeros((N, 3), dtype=np.int32)
+        w = np.zeros((N, U, 4))
+        rp = np.zeros(N + 1, dtype=np.int64)
+        cols = np.zeros(nnz, dtype=np.int32)
+        na, nphi, nk = np.zeros(nnz), np.zeros(nnz), np.zeros(nnz)
+        self._check(self._lib.aimx_export_setup(self._ctx, _ptr(anc), _ptr(w), _ptr(rp), _ptr(cols), _ptr(na),
+                                                _ptr(nphi), _ptr(nk)))
+        return dict(anchors=anc, weights=w, row_ptr=rp, cols=cols, NA=na, NP=nphi, NK=nk)

@@ -1,0 +1,161 @@
+// Internal declarations shared by the translation units of libaimx.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/aimx.h"
+
+namespace aimx {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kMu0 = 4.0e-7 * kPi;
+constexpr double kC0 = 299792458.0;
+constexpr double kEps0 = 1.0 / (kMu0 * kC0 * kC0);
+constexpr double kEta0 = kMu0 * kC0;
+
+constexpr int kMaxQuad = 64;        // points of the largest triangle rule kept on the device
+constexpr int kTwiddleLen = 4096;   // largest power-of-two FFT length supported
+
+// Status carrier used inside the library (never crosses the ABI).
+struct Error {
+    int code;
+    std::string msg;
+};
+
+#define AIMX_CUDA_TRY(expr)                                                        \
+    do {                                                                           \
+        cudaError_t e_ = (expr);                                                   \
+        if (e_ != cudaSuccess)                                                     \
+            throw ::aimx::Error{AIMX_E_CUDA, std::string(#expr) + ": " +           \
+                                                 cudaGetErrorString(e_)};          \
+    } while (0)
+
+// Typed device allocation owned by a context.
+template <class T>
+struct DArray {
+    T* p = nullptr;
+    size_t n = 0;
+};
+
+// Per-precision device data of a context.
+template <class T>
+struct PrecData {
+    T* w = nullptr;        // projection weights [N][U][4] (internal order)
+    T* na = nullptr;       // near N^A  [nnz]
+    T* np = nullptr;       // near N^Phi[nnz]
+    T* nk = nullptr;       // near N^K  [nnz]
+    T* spec = nullptr;     // octant spectra [nspec][Oz][Oy][Ox] complex (2 T each)
+    double spec_freq = -1.0;
+    // work buffers of the generic FFT path
+    T* grid = nullptr;     // [chunk][F][Mz][My][Mx] complex
+    size_t grid_elems = 0; // complex elements allocated
+};
+
+}  // namespace aimx
+
+struct aimx_ctx {
+    // problem description
+    int form = AIMX_EFIE;
+    int order = 2;
+    int P = 3;             // stencil nodes per axis
+    int U = 27;            // stencil nodes per basis
+    int N = 0;             // RWG functions
+    int nunk = 0;          // unknowns (N or 2N)
+    int n[3] = {0, 0, 0};  // grid nodes
+    int M[3] = {0, 0, 0};  // padded FFT lengths
+    double h[3] = {0, 0, 0};
+    double origin[3] = {0, 0, 0};
+    int radius = 3;
+    double eps_out = 1, mu_out = 1, eps_in = 1, mu_in = 1;
+    int F = 4;             // grid fields per RHS (4 EFIE, 8 PMCHWT)
+    int nspec = 2;         // spectra per frequency (2 EFIE, 7 PMCHWT)
+    int64_t nnz = 0;
+
+    // host-side products (internal order = bases sorted by anchor z, y, x)
+    std::vector<int> perm;         // internal -> caller index
+    std::vector<int> iperm;        // caller index -> internal
+    std::vector<int> anc;          // [N][3] internal order
+    std::vector<int> row_ptr;      // near CSR, internal order [N+1]
+    std::vector<int> cols;         // [nnz] internal column ids, ascending
+    std::vector<int> plane_lo, plane_hi;   // per z plane: internal bases touching it
+
+    // device geometry / topology
+    int nt = 0, nv = 0;
+    double* d_xyz = nullptr;       // [nv][3]
+    int* d_tri = nullptr;          // [nt][3]
+    double* d_area = nullptr;      // [nt]
+    int* d_btri = nullptr;         // [N][2] triangle of T+ / T- (internal order)
+    int* d_bfree = nullptr;        // [N][2] free vertex id
+    double* d_blen = nullptr;      // [N] edge length
+    int* d_anc = nullptr;          // [N][3]
+    int* d_perm = nullptr;         // [N]
+    int* d_row_ptr = nullptr;      // [N+1]
+    int* d_cols = nullptr;         // [nnz]
+    int* d_node_ptr = nullptr;     // [Nz*Ny*Nx + 1]
+    int* d_node_w = nullptr;       // [N*U] weight row index i*U+u
+    int* d_node_x = nullptr;       // [N*U] caller basis index of that entry
+    double* d_diag = nullptr;      // [N][3] static self terms L^A_s, L^Phi_s, K_s
+
+    aimx::PrecData<float> f32;
+    aimx::PrecData<double> f64;
+
+    // kernel-generation scratch (FP64 full grids)
+    double* d_kgen = nullptr;
+    size_t kgen_elems = 0;
+
+    // matvec host-buffer staging
+    void* d_stage = nullptr;
+    size_t stage_bytes = 0;
+
+    int64_t device_bytes = 0;
+    std::string last_error;
+};
+
+namespace aimx {
+
+// memory helpers (throw Error on failure, book-keep ctx->device_bytes)
+void* dev_alloc(aimx_ctx* ctx, size_t bytes);
+void dev_free(aimx_ctx* ctx, void* p);
+
+// setup.cu
+void setup_context(aimx_ctx* ctx, const aimx_mesh* mesh, const aimx_material* mat,
+                   const aimx_grid* grid, int order);
+
+// fft.cu
+const double2* twiddles64();
+const float2* twiddles32();
+template <class T>
+void fft3d_padded(T* grid, int batch, const int M[3], const int act[3], bool inverse,
+                  cudaStream_t s);
+template <class T>
+void fft3d_full(T* grid, int batch, const int M[3], bool inverse, cudaStream_t s);
+
+// kernelgen.cu
+template <class T>
+void ensure_spectra(aimx_ctx* ctx, double freq, cudaStream_t s);
+struct Coefs {
+    // spectral combinations (EFIE uses s[0], s[1]; PMCHWT all) and near coefficients
+    double2 near[6];  // EFIE: aA, aPhi ; PMCHWT: aA, aPhi, aK, bK, bA, bPhi
+};
+Coefs near_coefs(const aimx_ctx* ctx, double freq);
+
+template <class T>
+inline PrecData<T>& prec(aimx_ctx* ctx);
+template <>
+inline PrecData<float>& prec<float>(aimx_ctx* ctx) {
+    return ctx->f32;
+}
+template <>
+inline PrecData<double>& prec<double>(aimx_ctx* ctx) {
+    return ctx->f64;
+}
+
+// matvec.cu
+template <class T>
+void matvec_generic(aimx_ctx* ctx, double freq, int nrhs, const T* x, T* y, cudaStream_t s);
+
+}  // namespace aimx

@@ -1,0 +1,204 @@
+// C ABI entry points of libaimx (declared in include/aimx.h).  Every entry
+// point catches internal errors and returns a status code; nothing throws
+// across the ABI.
+
+#include <algorithm>
+#include <cstring>
+#include <map>
+
+#include "aimx_internal.h"
+
+namespace aimx {
+
+void* dev_alloc(aimx_ctx* ctx, size_t bytes) {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes ? bytes : 1);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw Error{AIMX_E_NOMEM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e)};
+    }
+    ctx->device_bytes += (int64_t)bytes;
+    return p;
+}
+
+void dev_free(aimx_ctx* ctx, void* p) {
+    (void)ctx;
+    if (p) cudaFree(p);
+}
+
+static int fail(aimx_ctx* ctx, const Error& e) {
+    if (ctx) ctx->last_error = e.msg;
+    return e.code;
+}
+
+static void free_all(aimx_ctx* c) {
+    void* ptrs[] = {c->d_xyz,     c->d_tri,     c->d_area,     c->d_btri,   c->d_bfree,  c->d_blen,
+                    c->d_anc,     c->d_perm,    c->d_row_ptr,  c->d_cols,   c->d_node_ptr,
+                    c->d_node_w,  c->d_node_x,  c->d_diag,     c->f32.w,    c->f32.na,   c->f32.np,
+                    c->f32.nk,    c->f32.spec,  c->f32.grid,   c->f64.w,    c->f64.na,   c->f64.np,
+                    c->f64.nk,    c->f64.spec,  c->f64.grid,   c->d_kgen,   c->d_stage};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+}
+
+}  // namespace aimx
+
+using namespace aimx;
+
+extern "C" {
+
+const char* aimx_status_string(int status) {
+    switch (status) {
+        case AIMX_OK: return "ok";
+        case AIMX_E_ARG: return "invalid argument";
+        case AIMX_E_MESH: return "invalid mesh";
+        case AIMX_E_GRID: return "stencil outside the grid";
+        case AIMX_E_NOMEM: return "out of memory";
+        case AIMX_E_CUDA: return "CUDA error";
+        case AIMX_E_TIMEOUT: return "bounded device wait expired";
+        case AIMX_E_STATE: return "call not valid for this context";
+        case AIMX_E_NOCONV: return "solver did not reach the tolerance";
+        default: return "unknown status";
+    }
+}
+
+const char* aimx_last_error(const aimx_ctx* ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+int aimx_setup(const aimx_mesh* mesh, const aimx_material* mat, const aimx_grid* grid, int order,
+               aimx_ctx** out) {
+    if (!out) return AIMX_E_ARG;
+    *out = nullptr;
+    aimx_ctx* ctx = new (std::nothrow) aimx_ctx();
+    if (!ctx) return AIMX_E_NOMEM;
+    try {
+        setup_context(ctx, mesh, mat, grid, order);
+    } catch (const Error& e) {
+        cudaDeviceSynchronize();
+        cudaGetLastError();
+        free_all(ctx);
+        int code = e.code;
+        delete ctx;
+        return code;
+    } catch (const std::bad_alloc&) {
+        free_all(ctx);
+        delete ctx;
+        return AIMX_E_NOMEM;
+    }
+    *out = ctx;
+    return AIMX_OK;
+}
+
+int aimx_destroy(aimx_ctx* ctx) {
+    if (!ctx) return AIMX_OK;
+    cudaDeviceSynchronize();
+    free_all(ctx);
+    delete ctx;
+    return AIMX_OK;
+}
+
+int aimx_info(const aimx_ctx* ctx, aimx_info_t* out) {
+    if (!ctx || !out) return AIMX_E_ARG;
+    std::memset(out, 0, sizeof(*out));
+    out->n_basis = ctx->N;
+    out->n_unknowns = ctx->nunk;
+    out->near_nnz = ctx->nnz;
+    for (int a = 0; a < 3; ++a) {
+        out->grid_n[a] = ctx->n[a];
+        out->pad[a] = ctx->M[a];
+        out->grid_h[a] = ctx->h[a];
+        out->grid_origin[a] = ctx->origin[a];
+    }
+    out->order = ctx->order;
+    out->formulation = ctx->form;
+    out->device_bytes = ctx->device_bytes;
+    return AIMX_OK;
+}
+
+int aimx_matvec(aimx_ctx* ctx, double freq, int nrhs, const void* x, void* y, int precision,
+                void* stream) {
+    if (!ctx || !x || !y || nrhs <= 0 || !(freq > 0)) return ctx ? fail(ctx, Error{AIMX_E_ARG, "bad argument"}) : AIMX_E_ARG;
+    if (precision != AIMX_F32 && precision != AIMX_F64) return fail(ctx, Error{AIMX_E_ARG, "bad precision"});
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    try {
+        if (precision == AIMX_F32)
+            matvec_generic<float>(ctx, freq, nrhs, (const float*)x, (float*)y, s);
+        else
+            matvec_generic<double>(ctx, freq, nrhs, (const double*)x, (double*)y, s);
+    } catch (const Error& e) {
+        return fail(ctx, e);
+    }
+    return AIMX_OK;
+}
+
+int aimx_matvec_host(aimx_ctx* ctx, double freq, int nrhs, const void* x, void* y, int precision,
+                     void* stream) {
+    if (!ctx || !x || !y || nrhs <= 0) return ctx ? fail(ctx, Error{AIMX_E_ARG, "bad argument"}) : AIMX_E_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    size_t es = precision == AIMX_F64 ? 2 * sizeof(double) : 2 * sizeof(float);
+    size_t bytes = es * (size_t)nrhs * ctx->nunk;
+    try {
+        if (ctx->stage_bytes < 2 * bytes) {
+            if (ctx->d_stage) dev_free(ctx, ctx->d_stage);
+            ctx->d_stage = dev_alloc(ctx, 2 * bytes);
+            ctx->stage_bytes = 2 * bytes;
+        }
+        char* dx = (char*)ctx->d_stage;
+        char* dy = dx + bytes;
+        AIMX_CUDA_TRY(cudaMemcpyAsync(dx, x, bytes, cudaMemcpyHostToDevice, s));
+        int rc = aimx_matvec(ctx, freq, nrhs, dx, dy, precision, stream);
+        if (rc != AIMX_OK) return rc;
+        AIMX_CUDA_TRY(cudaMemcpyAsync(y, dy, bytes, cudaMemcpyDeviceToHost, s));
+        AIMX_CUDA_TRY(cudaStreamSynchronize(s));
+    } catch (const Error& e) {
+        return fail(ctx, e);
+    }
+    return AIMX_OK;
+}
+
+int aimx_export_setup(const aimx_ctx* ctx, int32_t* anchors, double* weights, int64_t* row_ptr,
+                      int32_t* cols, double* na, double* nphi, double* nk) {
+    if (!ctx) return AIMX_E_ARG;
+    aimx_ctx* c = const_cast<aimx_ctx*>(ctx);
+    try {
+        const int N = ctx->N, U = ctx->U;
+        if (anchors)
+            for (int i = 0; i < N; ++i)
+                for (int a = 0; a < 3; ++a) anchors[3 * ctx->perm[i] + a] = ctx->anc[3 * i + a];
+        if (weights) {
+            std::vector<double> w((size_t)N * U * 4);
+            AIMX_CUDA_TRY(cudaMemcpy(w.data(), ctx->f64.w, w.size() * sizeof(double), cudaMemcpyDeviceToHost));
+            for (int i = 0; i < N; ++i)
+                std::memcpy(weights + (size_t)ctx->perm[i] * U * 4, &w[(size_t)i * U * 4], sizeof(double) * U * 4);
+        }
+        // near pairs re-indexed to caller numbering, columns ascending
+        if (row_ptr || cols || na || nphi || nk) {
+            std::vector<double> va(ctx->nnz), vp(ctx->nnz), vk(ctx->nnz);
+            AIMX_CUDA_TRY(cudaMemcpy(va.data(), ctx->f64.na, ctx->nnz * sizeof(double), cudaMemcpyDeviceToHost));
+            AIMX_CUDA_TRY(cudaMemcpy(vp.data(), ctx->f64.np, ctx->nnz * sizeof(double), cudaMemcpyDeviceToHost));
+            AIMX_CUDA_TRY(cudaMemcpy(vk.data(), ctx->f64.nk, ctx->nnz * sizeof(double), cudaMemcpyDeviceToHost));
+            std::vector<int64_t> rp(N + 1, 0);
+            for (int i = 0; i < N; ++i) rp[ctx->perm[i] + 1] = ctx->row_ptr[i + 1] - ctx->row_ptr[i];
+            for (int i = 0; i < N; ++i) rp[i + 1] += rp[i];
+            if (row_ptr) std::memcpy(row_ptr, rp.data(), sizeof(int64_t) * (N + 1));
+            std::vector<std::pair<int, int>> tmp;
+            for (int i = 0; i < N; ++i) {
+                int o = ctx->perm[i];
+                tmp.clear();
+                for (int e = ctx->row_ptr[i]; e < ctx->row_ptr[i + 1]; ++e) tmp.push_back({ctx->perm[ctx->cols[e]], e});
+                std::sort(tmp.begin(), tmp.end());
+                int64_t base = rp[o];
+                for (size_t k = 0; k < tmp.size(); ++k) {
+                    if (cols) cols[base + k] = tmp[k].first;
+                    if (na) na[base + k] = va[tmp[k].second];
+                    if (nphi) nphi[base + k] = vp[tmp[k].second];
+                    if (nk) nk[base + k] = vk[tmp[k].second];
+                }
+            }
+        }
+    } catch (const Error& e) {
+        return fail(c, e);
+    }
+    return AIMX_OK;
+}
+
+}  // extern "C"

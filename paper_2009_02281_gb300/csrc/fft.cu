@@ -1,0 +1,405 @@
+// Generic power-of-two 3-D FFT on padded grids (radix-2, shared-memory tiles)
+// and the per-frequency generation of the grid-kernel spectra.
+//
+// The convolution matrix H(k) is 3-level Toeplitz (Eq. Hmn, Sec. III-A-1);
+// its first row, sampled at the grid offsets d with the AIMx self term
+// H(0) = -jk/(4 pi) (Eq. Hmm), is embedded in a circulant of the padded size
+// M >= 2n - 1 per axis (offset d -> index d mod M, unused slots zero) and
+// transformed once per frequency in FP64.  Only the octant 0..M/2 of each
+// spectrum is stored: the scalar kernel is even in every axis, the gradient
+// component along axis a is odd in that axis and even in the others.
+
+#include <cmath>
+#include <mutex>
+
+#include "aimx_internal.h"
+#include "cplx.cuh"
+
+namespace aimx {
+
+// ------------------------------------------------------------------ twiddles
+
+static double2* g_tw64 = nullptr;
+static float2* g_tw32 = nullptr;
+static std::mutex g_tw_mutex;
+
+static void init_twiddles() {
+    std::lock_guard<std::mutex> lock(g_tw_mutex);
+    if (g_tw64) return;
+    const int H = kTwiddleLen / 2;
+    std::vector<double2> t64(H);
+    std::vector<float2> t32(H);
+    for (int k = 0; k < H; ++k) {
+        double a = -2.0 * kPi * (double)k / (double)kTwiddleLen;
+        t64[k] = make_double2(std::cos(a), std::sin(a));
+        t32[k] = make_float2((float)t64[k].x, (float)t64[k].y);
+    }
+    double2* d64;
+    float2* d32;
+    AIMX_CUDA_TRY(cudaMalloc(&d64, H * sizeof(double2)));
+    AIMX_CUDA_TRY(cudaMalloc(&d32, H * sizeof(float2)));
+    AIMX_CUDA_TRY(cudaMemcpy(d64, t64.data(), H * sizeof(double2), cudaMemcpyHostToDevice));
+    AIMX_CUDA_TRY(cudaMemcpy(d32, t32.data(), H * sizeof(float2), cudaMemcpyHostToDevice));
+    g_tw32 = d32;
+    g_tw64 = d64;
+}
+
+const double2* twiddles64() {
+    if (!g_tw64) init_twiddles();
+    return g_tw64;
+}
+const float2* twiddles32() {
+    if (!g_tw64) init_twiddles();
+    return g_tw32;
+}
+
+template <class T>
+static const cplx_t<T>* twiddles();
+template <>
+const float2* twiddles<float>() {
+    return twiddles32();
+}
+template <>
+const double2* twiddles<double>() {
+    return twiddles64();
+}
+
+// ------------------------------------------------------------------ radix-2 FFT on smem lines
+
+__device__ inline int bitrev(int v, int bits) { return (int)(__brev((unsigned)v) >> (32 - bits)); }
+
+// In-place iterative decimation-in-time FFT of nl lines (pitch elements apart)
+// that were loaded in bit-reversed order.  inv selects e^{+j..} twiddles.
+template <class C>
+__device__ void smem_fft_lines(C* s, int nl, int pitch, int L, int logL, bool inv, const C* tw) {
+    const int halfL = L >> 1;
+    for (int st = 1; st <= logL; ++st) {
+        const int half = 1 << (st - 1);
+        const int tstep = kTwiddleLen / (2 * half);
+        for (int idx = threadIdx.x; idx < nl * halfL; idx += blockDim.x) {
+            int l = idx / halfL, j = idx - l * halfL;
+            int pos = j & (half - 1);
+            int i0 = ((j >> (st - 1)) << st) + pos;
+            int i1 = i0 + half;
+            C w = tw[pos * tstep];
+            if (inv) w = conj(w);
+            C* line = s + l * pitch;
+            C b = w * line[i1];
+            C a = line[i0];
+            line[i0] = a + b;
+            line[i1] = a - b;
+        }
+        __syncthreads();
+    }
+}
+
+// Lines that are contiguous rows: row r at base + a*S1 + b*S2 + c*S3 with
+// r = (a*D1 + b)*D2 + c.  RPB rows per block.
+template <class T>
+__global__ void k_fft_rows(cplx_t<T>* base, int64_t nrows, int D1, int D2, int64_t S1, int64_t S2,
+                           int64_t S3, int L, int logL, int RPB, int inv, const cplx_t<T>* tw) {
+    using C = cplx_t<T>;
+    extern __shared__ unsigned char smraw[];
+    C* s = reinterpret_cast<C*>(smraw);
+    const int pitch = L + 1;
+    int64_t r0 = (int64_t)blockIdx.x * RPB;
+    int64_t rem = nrows - r0;
+    int nl = rem < RPB ? (int)rem : RPB;
+    for (int idx = threadIdx.x; idx < nl * L; idx += blockDim.x) {
+        int rr = idx / L, p = idx - rr * L;
+        int64_t r = r0 + rr;
+        int64_t c = r % D2, b = (r / D2) % D1, a = r / ((int64_t)D1 * D2);
+        s[rr * pitch + bitrev(p, logL)] = base[a * S1 + b * S2 + c * S3 + p];
+    }
+    __syncthreads();
+    smem_fft_lines<C>(s, nl, pitch, L, logL, inv != 0, tw);
+    for (int idx = threadIdx.x; idx < nl * L; idx += blockDim.x) {
+        int rr = idx / L, p = idx - rr * L;
+        int64_t r = r0 + rr;
+        int64_t c = r % D2, b = (r / D2) % D1, a = r / ((int64_t)D1 * D2);
+        base[a * S1 + b * S2 + c * S3 + p] = s[rr * pitch + p];
+    }
+}
+
+// Strided lines: line (o, x) starts at base + (o / D1)*S1 + (o % D1)*S2 + x and
+// its points are S apart; each block takes TC consecutive x of one o.
+template <class T>
+__global__ void k_fft_cols(cplx_t<T>* base, int64_t nouter, int D1, int64_t S1, int64_t S2, int64_t S,
+                           int Mx, int L, int logL, int TC, int inv, const cplx_t<T>* tw) {
+    using C = cplx_t<T>;
+    extern __shared__ unsigned char smraw[];
+    C* s = reinterpret_cast<C*>(smraw);
+    const int pitch = L + 1;
+    int ntiles = (Mx + TC - 1) / TC;
+    int64_t o = blockIdx.x / ntiles;
+    int x0 = (blockIdx.x % ntiles) * TC;
+    int nl = min(TC, Mx - x0);
+    C* lb = base + (o / D1) * S1 + (o % D1) * S2 + x0;
+    for (int idx = threadIdx.x; idx < nl * L; idx += blockDim.x) {
+        int p = idx / nl, c = idx - p * nl;
+        s[c * pitch + bitrev(p, logL)] = lb[(int64_t)p * S + c];
+    }
+    __syncthreads();
+    smem_fft_lines<C>(s, nl, pitch, L, logL, inv != 0, tw);
+    for (int idx = threadIdx.x; idx < nl * L; idx += blockDim.x) {
+        int p = idx / nl, c = idx - p * nl;
+        lb[(int64_t)p * S + c] = s[c * pitch + p];
+    }
+}
+
+static int ilog2(int v) {
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+
+template <class T>
+static void fft_rows(cplx_t<T>* g, int64_t nrows, int D1, int D2, int64_t S1, int64_t S2, int64_t S3,
+                     int L, bool inv, cudaStream_t s) {
+    if (nrows <= 0) return;
+    int RPB = std::max(1, 8192 / L);
+    size_t sm = (size_t)RPB * (L + 1) * sizeof(cplx_t<T>);
+    if (sm > 48 * 1024) {
+        RPB = std::max(1, (int)((48 * 1024) / ((L + 1) * sizeof(cplx_t<T>))));
+        sm = (size_t)RPB * (L + 1) * sizeof(cplx_t<T>);
+    }
+    unsigned nb = (unsigned)((nrows + RPB - 1) / RPB);
+    k_fft_rows<T><<<nb, 256, sm, s>>>(g, nrows, D1, D2, S1, S2, S3, L, ilog2(L), RPB, inv ? 1 : 0,
+                                      twiddles<T>());
+    AIMX_CUDA_TRY(cudaGetLastError());
+}
+
+template <class T>
+static void fft_cols(cplx_t<T>* g, int64_t nouter, int D1, int64_t S1, int64_t S2, int64_t S, int Mx,
+                     int L, bool inv, cudaStream_t s) {
+    if (nouter <= 0) return;
+    int TC = sizeof(T) == 4 ? 32 : 16;
+    TC = std::min(TC, Mx);
+    while ((size_t)TC * (L + 1) * sizeof(cplx_t<T>) > 48 * 1024 && TC > 1) TC >>= 1;
+    size_t sm = (size_t)TC * (L + 1) * sizeof(cplx_t<T>);
+    int ntiles = (Mx + TC - 1) / TC;
+    unsigned nb = (unsigned)(nouter * ntiles);
+    k_fft_cols<T><<<nb, 256, sm, s>>>(g, nouter, D1, S1, S2, S, Mx, L, ilog2(L), TC, inv ? 1 : 0,
+                                      twiddles<T>());
+    AIMX_CUDA_TRY(cudaGetLastError());
+}
+
+// 3-D transform of `batch` padded grids [batch][Mz][My][Mx] whose non-zero
+// input (forward) or needed output (inverse) lies in z < act[2], y < act[1]:
+// forward = x rows (y < act1, z < act2), y columns (z < act2), z columns (all);
+// inverse runs the same passes in reverse order.
+template <class T>
+void fft3d_padded(T* grid, int batch, const int M[3], const int act[3], bool inverse, cudaStream_t s) {
+    using C = cplx_t<T>;
+    C* g = reinterpret_cast<C*>(grid);
+    const int64_t Mx = M[0], My = M[1], Mz = M[2];
+    const int64_t SB = Mx * My * Mz;
+    auto xpass = [&]() {
+        fft_rows<T>(g, (int64_t)batch * act[2] * act[1], act[2], act[1], SB, My * Mx, Mx, M[0], inverse, s);
+    };
+    auto ypass = [&]() { fft_cols<T>(g, (int64_t)batch * act[2], act[2], SB, My * Mx, Mx, M[0], M[1], inverse, s); };
+    auto zpass = [&]() { fft_cols<T>(g, (int64_t)batch * My, (int)My, SB, Mx, My * Mx, M[0], M[2], inverse, s); };
+    if (!inverse) {
+        xpass();
+        ypass();
+        zpass();
+    } else {
+        zpass();
+        ypass();
+        xpass();
+    }
+}
+
+template <class T>
+void fft3d_full(T* grid, int batch, const int M[3], bool inverse, cudaStream_t s) {
+    int act[3] = {M[0], M[1], M[2]};
+    fft3d_padded<T>(grid, batch, M, act, inverse, s);
+}
+
+template void fft3d_padded<float>(float*, int, const int*, const int*, bool, cudaStream_t);
+template void fft3d_padded<double>(double*, int, const int*, const int*, bool, cudaStream_t);
+template void fft3d_full<float>(float*, int, const int*, bool, cudaStream_t);
+template void fft3d_full<double>(double*, int, const int*, bool, cudaStream_t);
+
+// ------------------------------------------------------------------ kernel generation
+
+struct Region {
+    double k;       // wavenumber
+    double gscale;  // multiplier of this region's gradient samples in V (eta0 for PMCHWT)
+};
+
+// Circulant samples: scalar G per region (arrays 0..nreg-1) and, for the
+// K operator, V_a = sum_reg eta0 * d_a G_reg (arrays nreg..nreg+2).
+__global__ void k_sample(double2* out, int nreg, int want_grad, Region r0, Region r1, int Mx, int My,
+                         int Mz, int nx, int ny, int nz, double hx, double hy, double hz) {
+    int64_t MT = (int64_t)Mx * My * Mz;
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= MT) return;
+    int ix = (int)(t % Mx), iy = (int)((t / Mx) % My), iz = (int)(t / ((int64_t)Mx * My));
+    auto off = [](int i, int M, int n, bool& gap) {
+        if (i <= n - 1) return i;
+        if (i >= M - n + 1) return i - M;
+        gap = true;
+        return 0;
+    };
+    bool gap = false;
+    int dx = off(ix, Mx, nx, gap), dy = off(iy, My, ny, gap), dz = off(iz, Mz, nz, gap);
+    int nout = nreg + (want_grad ? 3 : 0);
+    if (gap) {
+        for (int a = 0; a < nout; ++a) out[a * MT + t] = make_double2(0.0, 0.0);
+        return;
+    }
+    double rx = dx * hx, ry = dy * hy, rz = dz * hz;
+    double r = sqrt(rx * rx + ry * ry + rz * rz);
+    bool self = (dx == 0 && dy == 0 && dz == 0);
+    double2 V[3] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0)};
+    for (int g = 0; g < nreg; ++g) {
+        Region R = g == 0 ? r0 : r1;
+        double2 H;
+        if (self) {
+            H = make_double2(0.0, -R.k / (4.0 * kPi));   // Eq. Hmm
+        } else {
+            double s_, c_;
+            sincos(R.k * r, &s_, &c_);
+            double inv = 1.0 / (4.0 * kPi * r);
+            H = make_double2(c_ * inv, -s_ * inv);        // e^{-jkr} / (4 pi r)
+            if (want_grad) {
+                // grad G = -(1 + jkr) e^{-jkr} / (4 pi r^3) * r_vec
+                double inv3 = -1.0 / (4.0 * kPi * r * r * r);
+                double2 f = make_double2((c_ + R.k * r * s_) * inv3, (R.k * r * c_ - s_) * inv3);
+                V[0] = V[0] + (R.gscale * rx) * f;
+                V[1] = V[1] + (R.gscale * ry) * f;
+                V[2] = V[2] + (R.gscale * rz) * f;
+            }
+        }
+        out[g * MT + t] = H;
+    }
+    if (want_grad)
+        for (int a = 0; a < 3; ++a) out[(nreg + a) * MT + t] = V[a];
+}
+
+struct SpecCoef {
+    double2 c[4][2];  // scalar spectrum s = sum_reg c[s][reg] * Htilde_reg
+};
+
+// Octant spectra: spec[s][kz][ky][kx] for 0 <= k <= M/2, divided by M (the
+// 1/M of the inverse transform).
+__global__ void k_octant(const double2* full, int nreg, int nscal, int want_grad, SpecCoef cf, int Mx,
+                         int My, int Mz, double invM, double2* spec64, float2* spec32) {
+    int Ox = Mx / 2 + 1, Oy = My / 2 + 1, Oz = Mz / 2 + 1;
+    int64_t OT = (int64_t)Ox * Oy * Oz;
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= OT) return;
+    int ox = (int)(t % Ox), oy = (int)((t / Ox) % Oy), oz = (int)(t / ((int64_t)Ox * Oy));
+    int64_t MT = (int64_t)Mx * My * Mz;
+    int64_t src = ((int64_t)oz * My + oy) * Mx + ox;
+    for (int s = 0; s < nscal; ++s) {
+        double2 acc = make_double2(0, 0);
+        for (int g = 0; g < nreg; ++g) acc = acc + cf.c[s][g] * full[g * MT + src];
+        acc = invM * acc;
+        spec64[s * OT + t] = acc;
+        spec32[s * OT + t] = make_float2((float)acc.x, (float)acc.y);
+    }
+    if (want_grad)
+        for (int a = 0; a < 3; ++a) {
+            double2 v = invM * full[(nreg + a) * MT + src];
+            spec64[(nscal + a) * OT + t] = v;
+            spec32[(nscal + a) * OT + t] = make_float2((float)v.x, (float)v.y);
+        }
+}
+
+struct Mats {
+    int nreg;
+    double w;
+    double mu[2], eps[2], k[2];
+};
+
+static Mats materials(const aimx_ctx* ctx, double freq) {
+    Mats m;
+    m.w = 2.0 * kPi * freq;
+    m.nreg = ctx->form == AIMX_EFIE ? 1 : 2;
+    m.mu[0] = kMu0 * ctx->mu_out;
+    m.eps[0] = kEps0 * ctx->eps_out;
+    m.mu[1] = kMu0 * ctx->mu_in;
+    m.eps[1] = kEps0 * ctx->eps_in;
+    for (int g = 0; g < 2; ++g) m.k[g] = m.w * std::sqrt(m.mu[g] * m.eps[g]);
+    return m;
+}
+
+// j*a as a complex number
+static double2 jmul(double a) { return make_double2(0.0, a); }
+
+Coefs near_coefs(const aimx_ctx* ctx, double freq) {
+    Mats m = materials(ctx, freq);
+    Coefs c;
+    for (auto& v : c.near) v = make_double2(0, 0);
+    if (ctx->form == AIMX_EFIE) {
+        c.near[0] = jmul(m.w * m.mu[0]);
+        c.near[1] = jmul(-m.w * m.mu[0] / (m.k[0] * m.k[0]));
+    } else {
+        for (int g = 0; g < 2; ++g) {
+            c.near[0] = c.near[0] + jmul(m.w * m.mu[g]);
+            c.near[1] = c.near[1] + jmul(-m.w * m.mu[g] / (m.k[g] * m.k[g]));
+            c.near[4] = c.near[4] + jmul(kEta0 * kEta0 * m.w * m.eps[g]);
+            c.near[5] = c.near[5] + jmul(-kEta0 * kEta0 * m.w * m.eps[g] / (m.k[g] * m.k[g]));
+        }
+        c.near[2] = make_double2(2.0 * kEta0, 0.0);
+        c.near[3] = make_double2(-2.0 * kEta0, 0.0);
+    }
+    return c;
+}
+
+template <class T>
+void ensure_spectra(aimx_ctx* ctx, double freq, cudaStream_t s) {
+    if (prec<T>(ctx).spec_freq == freq && prec<T>(ctx).spec) return;
+    if (!(freq > 0.0)) throw Error{AIMX_E_ARG, "frequency must be positive"};
+    Mats m = materials(ctx, freq);
+    const int want_grad = ctx->form == AIMX_PMCHWT;
+    const int nreg = m.nreg;
+    const int narr = nreg + (want_grad ? 3 : 0);
+    const int64_t MT = (int64_t)ctx->M[0] * ctx->M[1] * ctx->M[2];
+    const int Ox = ctx->M[0] / 2 + 1, Oy = ctx->M[1] / 2 + 1, Oz = ctx->M[2] / 2 + 1;
+    const int64_t OT = (int64_t)Ox * Oy * Oz;
+    if (ctx->kgen_elems < (size_t)(narr * MT)) {
+        if (ctx->d_kgen) dev_free(ctx, ctx->d_kgen);
+        ctx->d_kgen = (double*)dev_alloc(ctx, sizeof(double2) * narr * MT);
+        ctx->kgen_elems = narr * MT;
+    }
+    if (!ctx->f64.spec) ctx->f64.spec = (double*)dev_alloc(ctx, sizeof(double2) * ctx->nspec * OT);
+    if (!ctx->f32.spec) ctx->f32.spec = (float*)dev_alloc(ctx, sizeof(float2) * ctx->nspec * OT);
+    Region r0{m.k[0], want_grad ? kEta0 : 0.0}, r1{m.k[1], want_grad ? kEta0 : 0.0};
+    double2* full = reinterpret_cast<double2*>(ctx->d_kgen);
+    k_sample<<<(unsigned)((MT + 255) / 256), 256, 0, s>>>(full, nreg, want_grad, r0, r1, ctx->M[0],
+                                                          ctx->M[1], ctx->M[2], ctx->n[0], ctx->n[1],
+                                                          ctx->n[2], ctx->h[0], ctx->h[1], ctx->h[2]);
+    AIMX_CUDA_TRY(cudaGetLastError());
+    fft3d_full<double>(ctx->d_kgen, narr, ctx->M, false, s);
+    SpecCoef cf;
+    for (auto& row : cf.c)
+        for (auto& v : row) v = make_double2(0, 0);
+    int nscal;
+    if (ctx->form == AIMX_EFIE) {
+        nscal = 2;
+        cf.c[0][0] = jmul(m.w * m.mu[0]);
+        cf.c[1][0] = jmul(-m.w * m.mu[0] / (m.k[0] * m.k[0]));
+    } else {
+        nscal = 4;
+        for (int g = 0; g < 2; ++g) {
+            cf.c[0][g] = jmul(m.w * m.mu[g]);
+            cf.c[1][g] = jmul(-m.w * m.mu[g] / (m.k[g] * m.k[g]));
+            cf.c[2][g] = jmul(kEta0 * kEta0 * m.w * m.eps[g]);
+            cf.c[3][g] = jmul(-kEta0 * kEta0 * m.w * m.eps[g] / (m.k[g] * m.k[g]));
+        }
+    }
+    k_octant<<<(unsigned)((OT + 255) / 256), 256, 0, s>>>(
+        full, nreg, nscal, want_grad, cf, ctx->M[0], ctx->M[1], ctx->M[2], 1.0 / (double)MT,
+        reinterpret_cast<double2*>(ctx->f64.spec), reinterpret_cast<float2*>(ctx->f32.spec));
+    AIMX_CUDA_TRY(cudaGetLastError());
+    ctx->f64.spec_freq = freq;
+    ctx->f32.spec_freq = freq;
+}
+
+template void ensure_spectra<float>(aimx_ctx*, double, cudaStream_t);
+template void ensure_spectra<double>(aimx_ctx*, double, cudaStream_t);
+
+}  // namespace aimx

@@ -1,0 +1,215 @@
+// AIMx matrix-vector product, generic path (any precision, any power-of-two pad).
+//
+//   y = N x + W H(k) P x                                   (Eq. LAIMx / Eq. KAIMx)
+//
+// 1. projection P: each grid node gathers the weighted coefficients of the
+//    bases whose stencil contains it (node-major lists, no atomics);
+// 2. zero-padded 3-D FFT, per-point multiply with the kernel spectra
+//    (scalar L parts; cross product with the gradient spectra for K),
+//    inverse FFT;
+// 3. interpolation W = P^T and the sparse near correction, written once.
+
+#include "aimx_internal.h"
+#include "cplx.cuh"
+
+namespace aimx {
+
+struct NearCoefs {
+    double2 c[6];
+};
+
+// Fields per RHS: EFIE (Jx, Jy, Jz, rho); PMCHWT adds (Mx, My, Mz, rho_M).
+// Field f uses weight component f % 4 and unknown block f / 4.
+template <class T>
+__global__ void k_project(const T* __restrict__ w, const int* __restrict__ node_ptr,
+                          const int* __restrict__ node_w, const int* __restrict__ node_x,
+                          const cplx_t<T>* __restrict__ x, cplx_t<T>* grid, int nrhs, int F, int N,
+                          int nunk, int nx, int ny, int nz, int Mx, int My, int Mz) {
+    using C = cplx_t<T>;
+    int64_t NG = (int64_t)nx * ny * nz;
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= NG * nrhs) return;
+    int64_t g = t % NG;
+    int b = (int)(t / NG);
+    int gx = (int)(g % nx), gy = (int)((g / nx) % ny), gz = (int)(g / ((int64_t)nx * ny));
+    C acc[8];
+    for (int f = 0; f < 8; ++f) acc[f] = czero<T>();
+    const C* xb = x + (int64_t)b * nunk;
+    for (int e = node_ptr[g]; e < node_ptr[g + 1]; ++e) {
+        const T* we = w + (int64_t)node_w[e] * 4;
+        int xi = node_x[e];
+        C xj = xb[xi];
+        for (int f = 0; f < 4; ++f) rfma(acc[f], we[f], xj);
+        if (F == 8) {
+            C xm = xb[N + xi];
+            for (int f = 0; f < 4; ++f) rfma(acc[4 + f], we[f], xm);
+        }
+    }
+    int64_t SB = (int64_t)Mx * My * Mz;
+    C* gb = grid + (int64_t)b * F * SB + ((int64_t)gz * My + gy) * Mx + gx;
+    for (int f = 0; f < F; ++f) gb[f * SB] = acc[f];
+}
+
+template <class T>
+__device__ inline cplx_t<T> load_spec(const cplx_t<T>* spec, int s, int64_t OT, int64_t oi) {
+    return spec[s * OT + oi];
+}
+
+// Per spectral point: out = mix(in) with the octant spectra (EFIE: 2 scalar,
+// PMCHWT: 4 scalar + gradient vector V with odd symmetry per component).
+template <class T>
+__global__ void k_mix(cplx_t<T>* grid, const cplx_t<T>* __restrict__ spec, int nrhs, int F, int Mx,
+                      int My, int Mz) {
+    using C = cplx_t<T>;
+    int64_t MT = (int64_t)Mx * My * Mz;
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= MT) return;
+    int kx = (int)(t % Mx), ky = (int)((t / Mx) % My), kz = (int)(t / ((int64_t)Mx * My));
+    int ox = kx <= Mx / 2 ? kx : Mx - kx;
+    int oy = ky <= My / 2 ? ky : My - ky;
+    int oz = kz <= Mz / 2 ? kz : Mz - kz;
+    int Ox = Mx / 2 + 1, Oy = My / 2 + 1, Oz = Mz / 2 + 1;
+    int64_t OT = (int64_t)Ox * Oy * Oz;
+    int64_t oi = ((int64_t)oz * Oy + oy) * Ox + ox;
+    if (F == 4) {
+        C s1 = load_spec<T>(spec, 0, OT, oi), s2 = load_spec<T>(spec, 1, OT, oi);
+        for (int b = 0; b < nrhs; ++b) {
+            C* g = grid + (int64_t)b * 4 * MT + t;
+            g[0] = s1 * g[0];
+            g[MT] = s1 * g[MT];
+            g[2 * MT] = s1 * g[2 * MT];
+            g[3 * MT] = s2 * g[3 * MT];
+        }
+    } else {
+        C s1 = load_spec<T>(spec, 0, OT, oi), s2 = load_spec<T>(spec, 1, OT, oi);
+        C s3 = load_spec<T>(spec, 2, OT, oi), s4 = load_spec<T>(spec, 3, OT, oi);
+        C vx = load_spec<T>(spec, 4, OT, oi), vy = load_spec<T>(spec, 5, OT, oi),
+          vz = load_spec<T>(spec, 6, OT, oi);
+        if (kx > Mx / 2) vx = -vx;
+        if (ky > My / 2) vy = -vy;
+        if (kz > Mz / 2) vz = -vz;
+        for (int b = 0; b < nrhs; ++b) {
+            C* g = grid + (int64_t)b * 8 * MT + t;
+            C jx = g[0], jy = g[MT], jz = g[2 * MT], rj = g[3 * MT];
+            C mx = g[4 * MT], my = g[5 * MT], mz = g[6 * MT], rm = g[7 * MT];
+            // E rows: S1 J + V x M ; H rows: -V x J + S3 M
+            g[0] = s1 * jx + (vy * mz - vz * my);
+            g[MT] = s1 * jy + (vz * mx - vx * mz);
+            g[2 * MT] = s1 * jz + (vx * my - vy * mx);
+            g[3 * MT] = s2 * rj;
+            g[4 * MT] = s3 * mx - (vy * jz - vz * jy);
+            g[5 * MT] = s3 * my - (vz * jx - vx * jz);
+            g[6 * MT] = s3 * mz - (vx * jy - vy * jx);
+            g[7 * MT] = s4 * rm;
+        }
+    }
+}
+
+// y[b][perm i] (and y[b][N + perm i]) = W-gather of the output fields + near correction.
+template <class T>
+__global__ void k_interp_near(const T* __restrict__ w, const int* __restrict__ anc,
+                              const int* __restrict__ perm, const int* __restrict__ row_ptr,
+                              const int* __restrict__ cols, const T* __restrict__ na,
+                              const T* __restrict__ np, const T* __restrict__ nk,
+                              const cplx_t<T>* __restrict__ grid, const cplx_t<T>* __restrict__ x,
+                              cplx_t<T>* y, NearCoefs nc, int nrhs, int F, int N, int nunk, int P,
+                              int Mx, int My, int Mz) {
+    using C = cplx_t<T>;
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)N * nrhs) return;
+    int i = (int)(t % N);
+    int b = (int)(t / N);
+    int U = P * P * P;
+    int64_t MT = (int64_t)Mx * My * Mz;
+    const C* gb = grid + (int64_t)b * F * MT;
+    const T* wi = w + (int64_t)i * U * 4;
+    C aE = czero<T>(), aH = czero<T>();
+    int sx = anc[3 * i], sy = anc[3 * i + 1], sz = anc[3 * i + 2];
+    for (int u = 0; u < U; ++u) {
+        int64_t node = ((int64_t)(sz + u / (P * P)) * My + (sy + (u / P) % P)) * Mx + (sx + u % P);
+        for (int f = 0; f < 4; ++f) rfma(aE, wi[4 * u + f], gb[f * MT + node]);
+        if (F == 8)
+            for (int f = 0; f < 4; ++f) rfma(aH, wi[4 * u + f], gb[(4 + f) * MT + node]);
+    }
+    const C* xb = x + (int64_t)b * nunk;
+    C cA = mk((T)nc.c[0].x, (T)nc.c[0].y), cP = mk((T)nc.c[1].x, (T)nc.c[1].y);
+    if (F == 4) {
+        C sA = czero<T>(), sP = czero<T>();
+        for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            C xj = xb[perm[cols[e]]];
+            rfma(sA, na[e], xj);
+            rfma(sP, np[e], xj);
+        }
+        aE = aE + cA * sA + cP * sP;
+        y[(int64_t)b * nunk + perm[i]] = aE;
+    } else {
+        C cK = mk((T)nc.c[2].x, (T)nc.c[2].y), dK = mk((T)nc.c[3].x, (T)nc.c[3].y);
+        C dA = mk((T)nc.c[4].x, (T)nc.c[4].y), dP = mk((T)nc.c[5].x, (T)nc.c[5].y);
+        C aJ = czero<T>(), pJ = czero<T>(), kJ = czero<T>(), aM = czero<T>(), pM = czero<T>(),
+          kM = czero<T>();
+        for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            int j = perm[cols[e]];
+            C xj = xb[j], xm = xb[N + j];
+            rfma(aJ, na[e], xj);
+            rfma(pJ, np[e], xj);
+            rfma(kJ, nk[e], xj);
+            rfma(aM, na[e], xm);
+            rfma(pM, np[e], xm);
+            rfma(kM, nk[e], xm);
+        }
+        aE = aE + cA * aJ + cP * pJ + cK * kM;
+        aH = aH + dK * kJ + dA * aM + dP * pM;
+        y[(int64_t)b * nunk + perm[i]] = aE;
+        y[(int64_t)b * nunk + N + perm[i]] = aH;
+    }
+}
+
+template <class T>
+void matvec_generic(aimx_ctx* ctx, double freq, int nrhs, const T* x, T* y, cudaStream_t s) {
+    using C = cplx_t<T>;
+    PrecData<T>& pd = prec<T>(ctx);
+    ensure_spectra<T>(ctx, freq, s);
+    Coefs cf = near_coefs(ctx, freq);
+    NearCoefs nc;
+    for (int k = 0; k < 6; ++k) nc.c[k] = cf.near[k];
+    const int F = ctx->F;
+    const int64_t MT = (int64_t)ctx->M[0] * ctx->M[1] * ctx->M[2];
+    const size_t per_rhs = (size_t)F * MT;
+    const size_t budget = (size_t)4 << 30;  // bytes of padded-grid work buffer
+    int chunk = (int)std::max<size_t>(1, std::min<size_t>(nrhs, budget / (per_rhs * sizeof(C))));
+    if (pd.grid_elems < per_rhs * chunk) {
+        if (pd.grid) dev_free(ctx, pd.grid);
+        pd.grid = (T*)dev_alloc(ctx, sizeof(C) * per_rhs * chunk);
+        pd.grid_elems = per_rhs * chunk;
+    }
+    C* grid = reinterpret_cast<C*>(pd.grid);
+    const C* xc = reinterpret_cast<const C*>(x);
+    C* yc = reinterpret_cast<C*>(y);
+    const int act[3] = {ctx->n[0], ctx->n[1], ctx->n[2]};
+    const int64_t NG = (int64_t)ctx->n[0] * ctx->n[1] * ctx->n[2];
+    for (int b0 = 0; b0 < nrhs; b0 += chunk) {
+        int nb = std::min(chunk, nrhs - b0);
+        AIMX_CUDA_TRY(cudaMemsetAsync(grid, 0, sizeof(C) * per_rhs * nb, s));
+        int64_t tot = NG * nb;
+        k_project<T><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
+            pd.w, ctx->d_node_ptr, ctx->d_node_w, ctx->d_node_x, xc + (int64_t)b0 * ctx->nunk, grid, nb,
+            F, ctx->N, ctx->nunk, ctx->n[0], ctx->n[1], ctx->n[2], ctx->M[0], ctx->M[1], ctx->M[2]);
+        AIMX_CUDA_TRY(cudaGetLastError());
+        fft3d_padded<T>(reinterpret_cast<T*>(grid), nb * F, ctx->M, act, false, s);
+        k_mix<T><<<(unsigned)((MT + 255) / 256), 256, 0, s>>>(
+            grid, reinterpret_cast<const C*>(pd.spec), nb, F, ctx->M[0], ctx->M[1], ctx->M[2]);
+        AIMX_CUDA_TRY(cudaGetLastError());
+        fft3d_padded<T>(reinterpret_cast<T*>(grid), nb * F, ctx->M, act, true, s);
+        int64_t tn = (int64_t)ctx->N * nb;
+        k_interp_near<T><<<(unsigned)((tn + 127) / 128), 128, 0, s>>>(
+            pd.w, ctx->d_anc, ctx->d_perm, ctx->d_row_ptr, ctx->d_cols, pd.na, pd.np, pd.nk, grid,
+            xc + (int64_t)b0 * ctx->nunk, yc + (int64_t)b0 * ctx->nunk, nc, nb, F, ctx->N, ctx->nunk,
+            ctx->P, ctx->M[0], ctx->M[1], ctx->M[2]);
+        AIMX_CUDA_TRY(cudaGetLastError());
+    }
+}
+
+template void matvec_generic<float>(aimx_ctx*, double, int, const float*, float*, cudaStream_t);
+template void matvec_generic<double>(aimx_ctx*, double, int, const double*, double*, cudaStream_t);
+
+}  // namespace aimx
