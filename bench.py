@@ -1,0 +1,355 @@
+"""Benchmark: batched AIMx matvec throughput on one GB300 (one JSON line on stdout).
+
+Workload (default): dielectric_sphere_61440 -- eps_r = 4 sphere, 30720 RWG /
+61440 unknowns (two-region formulation), 64^3 grid padded to 128^3, order 2,
+64 right-hand sides, FP32 matvec at 449.7 MHz.  One step = one batched
+matvec y = A(k) x of all 64 right-hand sides (projection, zero-padded FFT
+convolution with the kernel multiply, interpolation, near correction); the
+grid-kernel spectra of the frequency are generated during warm-up.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (direct grid summation) on the
+host cores on a bounded sample of the same workload: a few rows of one
+matvec, reported in the same unit (full-matvec equivalents per second).
+Under torchrun each rank runs an independent replica of the workload (weak
+scaling, no data-path collective); rank 0 prints the line.
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "AIMx matvecs/s"
+UNIT = "RHS-matvecs/s"
+FALLBACK_HBM = 6800.0
+L2_FLUSH_BYTES = 512 << 20
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM, "fallback"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+def _barrier_max(value, ws, device=None):
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class Clocks:
+    """nvidia-smi clock and throttle sampling during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _traffic_record(kernel, workload):
+    """dram bytes per launch from the committed ncu summary, if its source hash matches."""
+    path = os.path.join(ROOT, "profiles", "%s_%s.md" % (kernel, workload))
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    h = re.search(r"source_sha256:\s*([0-9a-f]+)", txt)
+    if not m or not h:
+        return None
+    src = open(os.path.join(ROOT, "paper_2009_02281_gb300", "csrc", "fused.cu"), "rb").read()
+    src += open(os.path.join(ROOT, "paper_2009_02281_gb300", "csrc", "fftreg.cuh"), "rb").read()
+    if hashlib.sha256(src).hexdigest()[:16] != h.group(1)[:16]:
+        return None
+    return float(m.group(1))
+
+
+def _algorithmic_bytes(info, wl, B):
+    """Compulsory DRAM bytes per batched FP32 matvec and per launch of each fused stage."""
+    nx, ny, nz = info["grid_n"]
+    Mx, My, Mz = info["pad"]
+    F = 8 if wl["formulation"] == "pmchwt" else 4
+    nspec = 7 if F == 8 else 2
+    oct_pts = (Mx // 2 + 1) * (My // 2 + 1) * (Mz // 2 + 1)
+    half = nz * My * Mx                      # stored half-spectrum points per field
+    N = info["n_basis"]
+    nunk = info["n_unknowns"]
+    nnz = info["near_nnz"]
+    U = (info["order"] + 1) ** 3
+    grid = 8.0 * Mx * My * Mz * (F + F) * B  # each field written and read once per direction
+    kern = 8.0 * nspec * oct_pts
+    weights = 2 * U * 4 * 4.0 * N
+    near = nnz * (4.0 * (3 if F == 8 else 2) + 4.0)
+    vec = 2 * 8.0 * nunk * B
+    step = grid + kern + weights + near + vec
+    stages = {
+        "z_fft_mix_inverse": 2 * 8.0 * F * half * B + kern,
+        "xy_fft_forward": 8.0 * F * nx * ny * nz * B + 8.0 * F * half * B,
+        "xy_fft_inverse_interp": 8.0 * F * half * B + weights / 2,
+        "gather_projection": 8.0 * F * nx * ny * nz * B + weights / 2 + 8.0 * nunk * B,
+    }
+    return step, stages
+
+
+def run_ours(args):
+    import torch
+    ws, rank = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from synth import workloads, random_complex
+    from paper_2009_02281_gb300 import Context, build, PMCHWT, EFIE, F32
+    build.build()
+    wl = workloads.WORKLOADS[args.workload]() if args.nrhs is None else \
+        workloads.WORKLOADS[args.workload](nrhs=args.nrhs)
+    B = wl["nrhs"]
+    t0 = time.time()
+    ctx = Context(wl["xyz"], wl["tri"], wl["grid_n"], order=wl["order"],
+                  formulation=PMCHWT if wl["formulation"] == "pmchwt" else EFIE,
+                  eps_out=wl["eps_out"], eps_in=wl["eps_in"] or 1.0, near_radius=wl["radius"])
+    torch.cuda.synchronize()
+    setup_s = time.time() - t0
+    info = ctx.info
+    x_np = random_complex((B, ctx.nunk), seed=100 + rank).astype(np.complex64)
+    x = torch.tensor(x_np, device="cuda")
+    y = torch.empty_like(x)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    freq = wl["freq"]
+    # kernel generation for this frequency, timed once
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    ctx.matvec(freq, x, y)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    first_ms = ev0.elapsed_time(ev1)
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        ctx.matvec(freq, x, y)
+    torch.cuda.synchronize()
+    # timed region
+    clocks = Clocks(local)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ctx.profile(True)
+    ctx.profile_read()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for k in range(args.steps):
+        flush.fill_(1.0)                      # evict L2 between steps (not timed)
+        starts[k].record(stream)
+        ctx.matvec(freq, x, y)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    total_ms = _barrier_max(total_ms, ws, device="cuda")
+    launches = sum(c for _, c in prof.values())
+
+    # end-to-end through the public host-buffer call (pinned host memory, copies inside)
+    xh = torch.tensor(x_np).pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    for _ in range(2):
+        ctx.matvec_host_ptr(freq, B, xh.data_ptr(), yh.data_ptr(), F32, stream)
+    torch.cuda.synchronize()
+    e2e_steps = max(1, min(args.steps, 10))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ctx.matvec_host_ptr(freq, B, xh.data_ptr(), yh.data_ptr(), F32, stream)
+    torch.cuda.synchronize()
+    e2e_s = _barrier_max(time.perf_counter() - t0, ws, device="cuda")
+
+    hbm, peak_kind = _peaks()
+    step_bytes, stage_bytes = _algorithmic_bytes(info, wl, B)
+    dom = max(prof.items(), key=lambda kv: kv[1][0])[0] if prof else None
+    roof = None
+    if dom in stage_bytes:
+        avg_ms = prof[dom][0] / prof[dom][1]
+        ach = stage_bytes[dom] / (avg_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(ach / hbm, 4), "peak_kind": "of " + peak_kind,
+                "traffic": _traffic_record(dom, args.workload),
+                "algorithmic_bytes_per_launch": stage_bytes[dom], "avg_launch_ms": round(avg_ms, 4)}
+    ms_per_step = total_ms / args.steps
+    step_gbs = step_bytes / (ms_per_step * 1e-3) / 1e9
+    value = ws * B * args.steps / (total_ms * 1e-3)
+    out = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64 (f32)", "data": "synthetic",
+        "config": {"workload": args.workload, "n_unknowns": ctx.nunk, "n_basis": ctx.N,
+                   "rhs_per_step": B, "grid": list(info["grid_n"]), "padded": list(info["pad"]),
+                   "order": info["order"], "near_nnz": info["near_nnz"], "freq_hz": freq,
+                   "formulation": wl["formulation"], "l2": "flushed between steps (512 MiB write)",
+                   "path": "plane-fused" if ctx.matvec_path(F32) == 0 else "generic",
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "roofline": roof,
+        "step_roofline": {"algorithmic_bytes": step_bytes, "achieved_gbs": round(step_gbs, 1),
+                          "frac": round(step_gbs / hbm, 4)},
+        "stages_ms": {k: [round(v[0] / args.steps, 4), v[1]] for k, v in prof.items()},
+        "e2e": {"value": round(ws * B * e2e_steps / e2e_s, 2), "unit": UNIT,
+                "h2d_bytes_per_step": int(x_np.nbytes), "d2h_bytes_per_step": int(x_np.nbytes)},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "setup_s": round(setup_s, 3),
+        "first_call_ms_incl_kernel_generation": round(first_ms, 3),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(wl, args.cpu_rows)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+class OracleSample:
+    """The FP64 oracle (direct grid summation) on sampled rows of one matvec of the workload."""
+
+    def __init__(self, wl, rows):
+        from oracle import operator as op
+        from synth import random_complex
+        self.op = op
+        self.wl = wl
+        nb = len(wl["tri"]) * 3 // 2
+        self.rows = (np.arange(rows) * 997 + 13) % nb
+        self.prob = op.setup(wl["xyz"], wl["tri"], wl["order"], wl["grid_n"], radius=wl["radius"],
+                             near_rows=self.rows)
+        self.x = random_complex(self.prob["N"] * (2 if wl["formulation"] == "pmchwt" else 1), seed=5)
+
+    def run(self, rows):
+        """Time the oracle on the given subset of sampled basis rows; returns (output rows, seconds)."""
+        wl, op = self.wl, self.op
+        t0 = time.perf_counter()
+        if wl["formulation"] == "pmchwt":
+            op.matvec_pmchwt(self.prob, wl["freq"], self.x, wl["eps_out"], wl["eps_in"], rows=rows)
+            nout = 2 * len(rows)
+        else:
+            op.matvec_efie(self.prob, wl["freq"], self.x, wl["eps_out"], rows=rows)
+            nout = len(rows)
+        return nout, time.perf_counter() - t0
+
+
+def cpu_baseline(wl, rows):
+    s = OracleSample(wl, rows)
+    nout, dt = s.run(s.rows)
+    nunk = len(s.x)
+    return {"value": nout / nunk / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "%d of %d output rows of one matvec (%s) by direct grid summation, %.1f s, numpy "
+                      "default threading; value = rows/s divided by rows per matvec" % (nout, nunk, wl["name"], dt)}
+
+
+def run_reference(args):
+    ws, rank = _dist()
+    if rank != 0:
+        return
+    from synth import workloads
+    wl = workloads.WORKLOADS[args.workload]()
+    samp = OracleSample(wl, max(1, args.steps))      # warm-up: oracle setup (not timed)
+    nunk = len(samp.x)
+    rates, t_all = [], 0.0
+    for k in range(args.steps):
+        nout, dt = samp.run(samp.rows[k:k + 1])      # one basis row per step
+        rates.append(nout / nunk / dt)
+        t_all += dt
+    value = float(np.median(rates))
+    sample = ("one basis row (%d output rows) of one matvec per step (%s), direct grid summation, numpy "
+              "default threading; value = median rows/s divided by %d rows per matvec"
+              % (2 if wl["formulation"] == "pmchwt" else 1, wl["name"], nunk))
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(1e3 * t_all / max(1, args.steps), 1), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "c128 (f64)", "data": "synthetic", "impl": "reference",
+           "config": {"workload": args.workload},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="dielectric_sphere_61440")
+    ap.add_argument("--nrhs", type=int, default=None)
+    ap.add_argument("--cpu-rows", type=int, default=32)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

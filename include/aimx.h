@@ -151,6 +151,25 @@ int aimx_matvec(aimx_ctx* ctx, double freq, int nrhs, const void* x, void* y,
 int aimx_matvec_host(aimx_ctx* ctx, double freq, int nrhs, const void* x, void* y,
                      int precision, void* stream);
 
+/* Select the FP32 matvec implementation: 0 = automatic (the plane-fused
+ * path whenever the grid is padded to exactly twice a power-of-two size per
+ * axis, else the generic path), 1 = always the generic path.  Both compute the
+ * same product; FP64 always uses the generic path. */
+int aimx_set_path(aimx_ctx* ctx, int path);
+
+/* 0 if aimx_matvec at this precision runs the plane-fused path, 1 if generic. */
+int aimx_matvec_path(const aimx_ctx* ctx, int precision);
+
+/* ------------------------------------------------------------------ profiling
+ * Per-stage timing with CUDA events recorded on the stream each stage is
+ * launched on (the paper's per-phase accounting, Table II, at kernel level).
+ * aimx_profile_read synchronises on the recorded events, writes the summed
+ * milliseconds and launch counts of up to max_stages stages, resets them and
+ * returns the number of stages the library defines. */
+int aimx_profile(aimx_ctx* ctx, int enable);
+int aimx_profile_read(aimx_ctx* ctx, double* ms, int64_t* launches, int max_stages);
+const char* aimx_profile_stage_name(int stage);
+
 /* ------------------------------------------------------------------ export (tests) */
 
 /* Copy setup products to host arrays (any pointer may be NULL to skip it).

@@ -64,6 +64,11 @@ _SIGS = [
     ("aimx_matvec_host", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     ("aimx_export_setup", ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 7),
+    ("aimx_set_path", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("aimx_matvec_path", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("aimx_profile", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("aimx_profile_read", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    ("aimx_profile_stage_name", ctypes.c_char_p, [ctypes.c_int]),
 ]
 
 
@@ -185,6 +190,33 @@ class Context:
         self._check(self._lib.aimx_matvec_host(self._ctx, float(freq), x.shape[0], _ptr(x), _ptr(y), prec,
                                                _stream_handle(stream)))
         return y
+
+    def matvec_host_ptr(self, freq, nrhs, x_ptr, y_ptr, precision=F32, stream=None):
+        """aimx_matvec_host on raw host addresses (e.g. pinned torch tensors)."""
+        self._check(self._lib.aimx_matvec_host(self._ctx, float(freq), int(nrhs), ctypes.c_void_p(x_ptr),
+                                               ctypes.c_void_p(y_ptr), int(precision), _stream_handle(stream)))
+
+    def set_path(self, path):
+        """0 = automatic (plane-fused FP32 path when supported), 1 = generic path."""
+        self._check(self._lib.aimx_set_path(self._ctx, int(path)))
+
+    def matvec_path(self, precision=F32):
+        return self._check(self._lib.aimx_matvec_path(self._ctx, int(precision)))
+
+    # ---------------------------------------------------------------- profiling
+    def profile(self, enable=True):
+        self._check(self._lib.aimx_profile(self._ctx, 1 if enable else 0))
+
+    def profile_read(self):
+        """{stage name: (milliseconds, launches)} since the last read (synchronises)."""
+        ms = np.zeros(32)
+        cnt = np.zeros(32, dtype=np.int64)
+        n = self._check(self._lib.aimx_profile_read(self._ctx, _ptr(ms), _ptr(cnt), 32))
+        out = {}
+        for k in range(n):
+            if cnt[k]:
+                out[self._lib.aimx_profile_stage_name(k).decode()] = (float(ms[k]), int(cnt[k]))
+        return out
 
     # ---------------------------------------------------------------- export
     def export_setup(self):

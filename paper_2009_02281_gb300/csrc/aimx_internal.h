@@ -55,6 +55,36 @@ struct PrecData {
     size_t grid_elems = 0; // complex elements allocated
 };
 
+// Per-stage CUDA-event timing (enabled by aimx_profile).
+enum Stage {
+    ST_KERNELGEN = 0,
+    ST_TRANSPOSE,
+    ST_GATHER,
+    ST_XY_FWD,
+    ST_ZPASS,
+    ST_XY_INV,
+    ST_FINAL,
+    ST_G_PROJECT,
+    ST_G_FFT,
+    ST_G_MIX,
+    ST_G_INTERP,
+    ST_SOLVE_BLAS,
+    ST_COUNT
+};
+
+struct ProfRec {
+    int stage;
+    cudaEvent_t a, b;
+};
+
+struct Profiler {
+    bool on = false;
+    std::vector<ProfRec> recs;
+    std::vector<cudaEvent_t> pool;
+    double ms[ST_COUNT] = {};
+    int64_t count[ST_COUNT] = {};
+};
+
 }  // namespace aimx
 
 struct aimx_ctx {
@@ -111,6 +141,18 @@ struct aimx_ctx {
     void* d_stage = nullptr;
     size_t stage_bytes = 0;
 
+    // fused FP32 path work buffers
+    float* d_xT = nullptr;         // [nunk][B] complex, internal order
+    float* d_G = nullptr;          // [B][F][Nz][Ny][Nx] complex (projected grid)
+    float* d_S = nullptr;          // [B][F][Nz][4][Ny][Nx] complex (xy spectra, parity blocks)
+    float* d_part = nullptr;       // [B][F/4][P][N] complex (per-plane interpolation partials)
+    int fused_cap = 0;             // RHS capacity of the buffers above
+    int max_plane_bases = 0;
+    int* d_plane = nullptr;        // [2][Nz] plane_lo then plane_hi
+    int path = 0;                  // 0 = automatic, 1 = force the generic FFT path
+
+    aimx::Profiler prof;
+
     int64_t device_bytes = 0;
     std::string last_error;
 };
@@ -153,6 +195,20 @@ template <>
 inline PrecData<double>& prec<double>(aimx_ctx* ctx) {
     return ctx->f64;
 }
+
+// profiling scope: records CUDA events around a stage on stream s when enabled
+struct StageScope {
+    aimx_ctx* ctx;
+    int stage;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr, b = nullptr;
+    StageScope(aimx_ctx* c, int st, cudaStream_t str);
+    ~StageScope();
+};
+
+// fused.cu
+bool fused_supported(const aimx_ctx* ctx);
+void matvec_fused(aimx_ctx* ctx, double freq, int nrhs, const float* x, float* y, cudaStream_t s);
 
 // matvec.cu
 template <class T>

@@ -36,10 +36,46 @@ static void free_all(aimx_ctx* c) {
                     c->d_anc,     c->d_perm,    c->d_row_ptr,  c->d_cols,   c->d_node_ptr,
                     c->d_node_w,  c->d_node_x,  c->d_diag,     c->f32.w,    c->f32.na,   c->f32.np,
                     c->f32.nk,    c->f32.spec,  c->f32.grid,   c->f64.w,    c->f64.na,   c->f64.np,
-                    c->f64.nk,    c->f64.spec,  c->f64.grid,   c->d_kgen,   c->d_stage};
+                    c->f64.nk,    c->f64.spec,  c->f64.grid,   c->d_kgen,   c->d_stage,
+                    c->d_xT,      c->d_G,       c->d_S,        c->d_part,   c->d_plane};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    for (auto& r : c->prof.recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : c->prof.pool) cudaEventDestroy(e);
+    c->prof.recs.clear();
+    c->prof.pool.clear();
 }
+
+static cudaEvent_t pool_event(aimx_ctx* ctx) {
+    if (!ctx->prof.pool.empty()) {
+        cudaEvent_t e = ctx->prof.pool.back();
+        ctx->prof.pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    AIMX_CUDA_TRY(cudaEventCreate(&e));
+    return e;
+}
+
+StageScope::StageScope(aimx_ctx* c, int st, cudaStream_t str) : ctx(c), stage(st), s(str) {
+    if (!ctx->prof.on) return;
+    a = pool_event(ctx);
+    b = pool_event(ctx);
+    AIMX_CUDA_TRY(cudaEventRecord(a, s));
+}
+
+StageScope::~StageScope() {
+    if (!a) return;
+    if (cudaEventRecord(b, s) == cudaSuccess) ctx->prof.recs.push_back(ProfRec{stage, a, b});
+}
+
+static const char* kStageNames[ST_COUNT] = {
+    "kernel_spectra", "transpose_x", "gather_projection", "xy_fft_forward", "z_fft_mix_inverse",
+    "xy_fft_inverse_interp", "near_final", "generic_projection", "generic_fft", "generic_mix",
+    "generic_interp_near", "solver_vector_ops"};
 
 }  // namespace aimx
 
@@ -120,7 +156,9 @@ int aimx_matvec(aimx_ctx* ctx, double freq, int nrhs, const void* x, void* y, in
     if (precision != AIMX_F32 && precision != AIMX_F64) return fail(ctx, Error{AIMX_E_ARG, "bad precision"});
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     try {
-        if (precision == AIMX_F32)
+        if (precision == AIMX_F32 && ctx->path == 0 && fused_supported(ctx))
+            matvec_fused(ctx, freq, nrhs, (const float*)x, (float*)y, s);
+        else if (precision == AIMX_F32)
             matvec_generic<float>(ctx, freq, nrhs, (const float*)x, (float*)y, s);
         else
             matvec_generic<double>(ctx, freq, nrhs, (const double*)x, (double*)y, s);
@@ -153,6 +191,52 @@ int aimx_matvec_host(aimx_ctx* ctx, double freq, int nrhs, const void* x, void* 
         return fail(ctx, e);
     }
     return AIMX_OK;
+}
+
+int aimx_set_path(aimx_ctx* ctx, int path) {
+    if (!ctx || path < 0 || path > 1) return AIMX_E_ARG;
+    ctx->path = path;
+    return AIMX_OK;
+}
+
+int aimx_matvec_path(const aimx_ctx* ctx, int precision) {
+    if (!ctx) return AIMX_E_ARG;
+    return (precision == AIMX_F32 && ctx->path == 0 && fused_supported(ctx)) ? 0 : 1;
+}
+
+int aimx_profile(aimx_ctx* ctx, int enable) {
+    if (!ctx) return AIMX_E_ARG;
+    ctx->prof.on = enable != 0;
+    return AIMX_OK;
+}
+
+const char* aimx_profile_stage_name(int stage) {
+    return (stage >= 0 && stage < ST_COUNT) ? kStageNames[stage] : "";
+}
+
+int aimx_profile_read(aimx_ctx* ctx, double* ms, int64_t* launches, int max_stages) {
+    if (!ctx || max_stages < 0) return AIMX_E_ARG;
+    try {
+        for (auto& r : ctx->prof.recs) {
+            AIMX_CUDA_TRY(cudaEventSynchronize(r.b));
+            float t = 0.f;
+            AIMX_CUDA_TRY(cudaEventElapsedTime(&t, r.a, r.b));
+            ctx->prof.ms[r.stage] += t;
+            ctx->prof.count[r.stage] += 1;
+            ctx->prof.pool.push_back(r.a);
+            ctx->prof.pool.push_back(r.b);
+        }
+        ctx->prof.recs.clear();
+        for (int k = 0; k < max_stages && k < ST_COUNT; ++k) {
+            if (ms) ms[k] = ctx->prof.ms[k];
+            if (launches) launches[k] = ctx->prof.count[k];
+            ctx->prof.ms[k] = 0.0;
+            ctx->prof.count[k] = 0;
+        }
+    } catch (const Error& e) {
+        return fail(ctx, e);
+    }
+    return ST_COUNT;
 }
 
 int aimx_export_setup(const aimx_ctx* ctx, int32_t* anchors, double* weights, int64_t* row_ptr,

@@ -26,7 +26,7 @@ static std::mutex g_tw_mutex;
 static void init_twiddles() {
     std::lock_guard<std::mutex> lock(g_tw_mutex);
     if (g_tw64) return;
-    const int H = kTwiddleLen / 2;
+    const int H = kTwiddleLen;   // full circle: e^{-2 pi i k / 4096}, k < 4096
     std::vector<double2> t64(H);
     std::vector<float2> t32(H);
     for (int k = 0; k < H; ++k) {

@@ -1,0 +1,493 @@
+// FP32 AIMx matvec, plane-fused path for grids padded to exactly twice their
+// size (M_a = 2 N_a, N_a a power of two).
+//
+// The zero-padded transform of a field that is non-zero only on the first
+// N_a nodes of each axis splits by output parity p_a (k_a = 2 k'_a + p_a)
+// into N-point transforms of the field twisted by e^{-2 pi i p_a n_a / M_a};
+// the inverse recombines the parity classes with the conjugate twist, and
+// only the N_a outputs on the grid are formed.  Pass structure:
+//
+//   k_transpose_x : x[b][n] -> xT[i][b] (internal basis order, RHS fastest)
+//   k_gather      : projection P, node-major gather (no atomics) -> G[b][f][z][y][x]
+//   k_xy_fwd      : per z plane: 4 parity classes (px, py), 2-D N-point FFT
+//                   -> S[b][f][z][q][ky'][kx']
+//   k_zpass       : per (kx', ky', q) column tile: zero-padded M_z FFT along z,
+//                   per-point kernel multiply (Eq. LAIMx / KAIMx grid term),
+//                   inverse, z < N_z kept -> S in place
+//   k_xy_inv      : per z plane and field group: inverse 2-D FFT of the four
+//                   parity classes, untwist, sum -> output plane in shared
+//                   memory -> interpolation W = P^T partial per basis and slot
+//   k_final       : per 32 bases: sum partials + near correction (BSR-free CSR
+//                   rows, RHS vectorised) -> y
+//
+// Every sum has a fixed order, so results are bitwise reproducible.
+
+#include <algorithm>
+
+#include "aimx_internal.h"
+#include "cplx.cuh"
+#include "fftreg.cuh"
+
+namespace aimx {
+
+static inline bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+constexpr int kThreads = 256;
+constexpr int kTX = 8;     // kx' columns per z-pass block
+constexpr int kRG = 8;     // RHS per z-pass block (kernel spectra reuse)
+constexpr int kFinalRows = 32;
+constexpr int kFinalB = 64;
+
+bool fused_supported(const aimx_ctx* ctx) {
+    for (int a = 0; a < 3; ++a) {
+        if (!pow2(ctx->n[a]) || ctx->M[a] != 2 * ctx->n[a] || ctx->n[a] < 2) return false;
+    }
+    const int Nx = ctx->n[0], Ny = ctx->n[1], Nz = ctx->n[2];
+    if ((size_t)Nx * Ny * sizeof(float2) > 40 * 1024) return false;
+    if (Nx < kTX) return false;
+    if (Nx > 4096 || Ny > 4096 || 2 * Nz > 4096) return false;
+    if ((size_t)ctx->F * kTX * (2 * Nz + 1) * sizeof(float2) > 96 * 1024) return false;
+    if (kTX * 2 * Nz > 4 * kThreads) return false;
+    int mpb = 0;
+    for (int z = 0; z < Nz; ++z) mpb = std::max(mpb, ctx->plane_hi[z] - ctx->plane_lo[z]);
+    if ((size_t)mpb * sizeof(float2) > 64 * 1024) return false;
+    return true;
+}
+
+__device__ inline float2 twist(const float2* __restrict__ tw, int p, int n, int M) {
+    if (!p) return make_float2(1.f, 0.f);
+    return __ldg(tw + (size_t)n * (kTwiddleLen / M));
+}
+
+// ------------------------------------------------------------------ K0
+__global__ void k_transpose_x(const float2* __restrict__ x, const int* __restrict__ perm, float2* xT,
+                              int N, int nunk, int B) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)nunk * B) return;
+    int b = (int)(t % B);
+    int r = (int)(t / B);
+    int blk = r / N, i = r - blk * N;
+    xT[t] = x[(int64_t)b * nunk + blk * N + perm[i]];
+}
+
+// ------------------------------------------------------------------ K1
+__global__ void k_gather(const float4* __restrict__ w, const int* __restrict__ node_ptr,
+                         const int* __restrict__ node_w, const float2* __restrict__ xT, float2* G,
+                         int B, int F, int N, int U, int64_t NG) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= NG * B) return;
+    int64_t g = t % NG;
+    int b = (int)(t / NG);
+    float2 acc[8];
+#pragma unroll
+    for (int f = 0; f < 8; ++f) acc[f] = make_float2(0.f, 0.f);
+    const int e1 = node_ptr[g + 1];
+    for (int e = node_ptr[g]; e < e1; ++e) {
+        int wi = node_w[e];
+        float4 wv = __ldg(w + wi);
+        int i = wi / U;
+        float2 xj = __ldg(xT + (int64_t)i * B + b);
+        rfma(acc[0], wv.x, xj);
+        rfma(acc[1], wv.y, xj);
+        rfma(acc[2], wv.z, xj);
+        rfma(acc[3], wv.w, xj);
+        if (F == 8) {
+            float2 xm = __ldg(xT + (int64_t)(N + i) * B + b);
+            rfma(acc[4], wv.x, xm);
+            rfma(acc[5], wv.y, xm);
+            rfma(acc[6], wv.z, xm);
+            rfma(acc[7], wv.w, xm);
+        }
+    }
+    float2* out = G + (int64_t)b * F * NG + g;
+#pragma unroll
+    for (int f = 0; f < 8; ++f)
+        if (f < F) out[f * NG] = acc[f];
+}
+
+// ------------------------------------------------------------------ K2
+// Shared-memory planes use a row pitch of Nx + 1 complex so that transforms of
+// adjacent rows touch different banks.
+__global__ void __launch_bounds__(kThreads) k_xy_fwd(const float2* __restrict__ G, float2* S, int F, int Nx,
+                                                     int Ny, int Nz, const float2* __restrict__ tw) {
+    extern __shared__ float2 sm[];
+    const int NP = Nx * Ny;
+    const int pitch = Nx + 1;
+    float2* P = sm;                 // natural plane, pitch Nx
+    float2* W = sm + NP;            // work plane, pitch Nx + 1
+    const int z = blockIdx.x, f = blockIdx.y, b = blockIdx.z;
+    const int64_t plane = ((int64_t)(b * F + f) * Nz + z);
+    const float2* src = G + plane * NP;
+    for (int i = threadIdx.x; i < NP; i += blockDim.x) P[i] = src[i];
+    __syncthreads();
+    const int Mx = 2 * Nx, My = 2 * Ny;
+    for (int q = 0; q < 4; ++q) {
+        const int px = q & 1, py = q >> 1;
+        // twisted input, digit-reversed along x for the DIT row transform
+        for (int i = threadIdx.x; i < NP; i += blockDim.x) {
+            int y = i / Nx, x = i - y * Nx;
+            float2 v = P[i];
+            if (px) v = v * twist(tw, 1, x, Mx);
+            if (py) v = v * twist(tw, 1, y, My);
+            W[y * pitch + dit_pos(x, Nx)] = v;
+        }
+        __syncthreads();
+        fft_dit<false>(W, Ny, pitch, 1, Nx, tw);     // rows: natural kx' out
+        fft_dif<false>(W, Nx, 1, pitch, Ny, tw);     // columns: ky' at dif_pos
+        float2* dst = S + (plane * 4 + q) * NP;
+        for (int i = threadIdx.x; i < NP; i += blockDim.x) {
+            int ky = i / Nx, kx = i - ky * Nx;
+            dst[i] = W[dif_pos(ky, Ny) * pitch + kx];
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ K3
+// spectra layout: [nspec][Oz][Oy][Ox] complex, octant 0..M/2; fold and odd signs applied here
+__global__ void __launch_bounds__(kThreads) k_zpass(float2* S, const float2* __restrict__ spec, int F, int Nx,
+                                                    int Ny, int Nz, int B, const float2* __restrict__ tw) {
+    extern __shared__ float2 sm[];
+    const int Mz = 2 * Nz, Mx = 2 * Nx, My = 2 * Ny;
+    const int lp = Mz + 1;          // line pitch
+    const int NP = Nx * Ny;
+    const int kx0 = blockIdx.x * kTX;
+    const int kyp = blockIdx.y;
+    const int q = blockIdx.z & 3;
+    const int b0 = (blockIdx.z >> 2) * kRG;
+    const int px = q & 1, py = q >> 1;
+    const int nlines = F * kTX;
+    const int Ox = Mx / 2 + 1, Oy = My / 2 + 1, Oz = Mz / 2 + 1;
+    const int64_t OT = (int64_t)Ox * Oy * Oz;
+    const int ky = 2 * kyp + py;
+    const int oy = ky <= My / 2 ? ky : My - ky;
+    const float sy = ky > My / 2 ? -1.f : 1.f;
+    // mix points owned by this thread: (c, kz), at most 4 per thread (kTX * Mz <= 4 * kThreads)
+    constexpr int KP = 4;
+    const int ns = F == 4 ? 2 : 7;
+    float2 sp[KP][7];
+    const int npts = kTX * Mz;
+#pragma unroll
+    for (int k = 0; k < KP; ++k) {
+        int pt = threadIdx.x + k * blockDim.x;
+        if (pt < npts) {
+            int c = pt % kTX, kz = pt / kTX;
+            int kx = 2 * (kx0 + c) + px;
+            int ox = kx <= Mx / 2 ? kx : Mx - kx;
+            int oz = kz <= Mz / 2 ? kz : Mz - kz;
+            int64_t oi = ((int64_t)oz * Oy + oy) * Ox + ox;
+#pragma unroll
+            for (int s = 0; s < 7; ++s) sp[k][s] = s < ns ? __ldg(spec + s * OT + oi) : make_float2(0.f, 0.f);
+            if (F == 8) {
+                if (kx > Mx / 2) sp[k][4] = -sp[k][4];
+                sp[k][5] = sy * sp[k][5];
+                if (kz > Mz / 2) sp[k][6] = -sp[k][6];
+            }
+        }
+    }
+    for (int bb = 0; bb < kRG; ++bb) {
+        const int b = b0 + bb;
+        if (b >= B) break;
+        // load z < Nz of F * kTX columns (digit-reversed slots), zero the padding
+        for (int idx = threadIdx.x; idx < nlines * Mz; idx += blockDim.x) {
+            int c = idx % kTX;
+            int rest = idx / kTX;
+            int z = rest % Mz;
+            int f = rest / Mz;
+            float2 v = make_float2(0.f, 0.f);
+            if (z < Nz) v = S[((((int64_t)b * F + f) * Nz + z) * 4 + q) * NP + (int64_t)kyp * Nx + kx0 + c];
+            sm[(f * kTX + c) * lp + dit_pos(z, Mz)] = v;
+        }
+        __syncthreads();
+        fft_dit<false>(sm, nlines, lp, 1, Mz, tw);
+#pragma unroll
+        for (int k = 0; k < KP; ++k) {
+            int pt = threadIdx.x + k * blockDim.x;
+            if (pt < npts) {
+                int c = pt % kTX, kz = pt / kTX;
+                float2* g = sm + c * lp + kz;
+                const int fs = kTX * lp;  // field stride
+                if (F == 4) {
+                    g[0] = sp[k][0] * g[0];
+                    g[fs] = sp[k][0] * g[fs];
+                    g[2 * fs] = sp[k][0] * g[2 * fs];
+                    g[3 * fs] = sp[k][1] * g[3 * fs];
+                } else {
+                    float2 jx = g[0], jy = g[fs], jz = g[2 * fs], rj = g[3 * fs];
+                    float2 mx = g[4 * fs], my = g[5 * fs], mz = g[6 * fs], rm = g[7 * fs];
+                    float2 s1 = sp[k][0], s2 = sp[k][1], s3 = sp[k][2], s4 = sp[k][3];
+                    float2 vx = sp[k][4], vy = sp[k][5], vz = sp[k][6];
+                    g[0] = s1 * jx + (vy * mz - vz * my);
+                    g[fs] = s1 * jy + (vz * mx - vx * mz);
+                    g[2 * fs] = s1 * jz + (vx * my - vy * mx);
+                    g[3 * fs] = s2 * rj;
+                    g[4 * fs] = s3 * mx - (vy * jz - vz * jy);
+                    g[5 * fs] = s3 * my - (vz * jx - vx * jz);
+                    g[6 * fs] = s3 * mz - (vx * jy - vy * jx);
+                    g[7 * fs] = s4 * rm;
+                }
+            }
+        }
+        __syncthreads();
+        fft_dif<true>(sm, nlines, lp, 1, Mz, tw);
+        for (int idx = threadIdx.x; idx < nlines * Nz; idx += blockDim.x) {
+            int c = idx % kTX;
+            int rest = idx / kTX;
+            int z = rest % Nz;
+            int f = rest / Nz;
+            S[((((int64_t)b * F + f) * Nz + z) * 4 + q) * NP + (int64_t)kyp * Nx + kx0 + c] =
+                sm[(f * kTX + c) * lp + dif_pos(z, Mz)];
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ K4
+__global__ void __launch_bounds__(kThreads) k_xy_inv(const float2* __restrict__ S, const float* __restrict__ w,
+                                                     const int* __restrict__ anc, const int* __restrict__ plane_lo,
+                                                     const int* __restrict__ plane_hi, float2* part, int F, int Nx,
+                                                     int Ny, int Nz, int N, int P, const float2* __restrict__ tw) {
+    extern __shared__ float2 sm[];
+    const int NP = Nx * Ny;
+    const int pitch = Nx + 1;
+    float2* O = sm;                     // output plane, pitch Nx
+    float2* W = sm + NP;                // work plane, pitch Nx + 1
+    float2* acc = sm + NP + Ny * pitch;
+    const int z = blockIdx.x, grp = blockIdx.y, b = blockIdx.z;
+    const int G = F / 4;
+    const int lo = plane_lo[z], hi = plane_hi[z];
+    const int nb = hi - lo;
+    const int Mx = 2 * Nx, My = 2 * Ny;
+    const int U = P * P * P;
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) acc[k] = make_float2(0.f, 0.f);
+    for (int fl = 0; fl < 4; ++fl) {
+        const int f = grp * 4 + fl;
+        const int64_t plane = ((int64_t)(b * F + f) * Nz + z);
+        for (int q = 0; q < 4; ++q) {
+            const int px = q & 1, py = q >> 1;
+            const float2* src = S + (plane * 4 + q) * NP;
+            for (int i = threadIdx.x; i < NP; i += blockDim.x) {
+                int ky = i / Nx, kx = i - ky * Nx;
+                W[ky * pitch + kx] = src[i];
+            }
+            __syncthreads();
+            fft_dif<true>(W, Nx, 1, pitch, Ny, tw);   // columns: y at dif_pos
+            fft_dif<true>(W, Ny, pitch, 1, Nx, tw);   // rows: x at dif_pos
+            for (int i = threadIdx.x; i < NP; i += blockDim.x) {
+                int y = i / Nx, x = i - y * Nx;
+                float2 v = W[dif_pos(y, Ny) * pitch + dif_pos(x, Nx)];
+                if (px) v = v * conj(twist(tw, 1, x, Mx));
+                if (py) v = v * conj(twist(tw, 1, y, My));
+                O[i] = q == 0 ? v : O[i] + v;
+            }
+            __syncthreads();
+        }
+        // interpolation partial of field f for the bases touching this plane
+        for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+            int i = lo + k;
+            int sx = anc[3 * i], sy = anc[3 * i + 1], sz = anc[3 * i + 2];
+            int slot = z - sz;
+            const float* wi = w + ((int64_t)i * U + slot * P * P) * 4 + fl;
+            float2 s = make_float2(0.f, 0.f);
+            for (int uy = 0; uy < P; ++uy)
+                for (int ux = 0; ux < P; ++ux) rfma(s, __ldg(wi + (uy * P + ux) * 4), O[(sy + uy) * Nx + sx + ux]);
+            acc[k] = acc[k] + s;
+        }
+        __syncthreads();
+    }
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+        int i = lo + k;
+        int slot = z - anc[3 * i + 2];
+        part[(((int64_t)b * G + grp) * P + slot) * N + i] = acc[k];
+    }
+}
+
+// ------------------------------------------------------------------ K5
+struct NearC {
+    float2 c[6];
+};
+
+__global__ void __launch_bounds__(kThreads) k_final(const float2* __restrict__ part, const float2* __restrict__ xT,
+                                                    const int* __restrict__ row_ptr, const int* __restrict__ cols,
+                                                    const float* __restrict__ na, const float* __restrict__ np,
+                                                    const float* __restrict__ nk, const int* __restrict__ perm,
+                                                    float2* y, NearC nc, int F, int N, int nunk, int P, int B) {
+    __shared__ float2 accE[kFinalRows][kFinalB];
+    __shared__ float2 accH[kFinalRows][kFinalB];
+    const int G = F / 4;
+    const int i0 = blockIdx.x * kFinalRows;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int bc = 0; bc < B; bc += kFinalB) {
+        const int nbc = min(kFinalB, B - bc);
+        // partial sums over slots
+        for (int idx = threadIdx.x; idx < G * nbc * kFinalRows; idx += blockDim.x) {
+            int r = idx % kFinalRows;
+            int rest = idx / kFinalRows;
+            int bl = rest % nbc;
+            int g = rest / nbc;
+            int i = i0 + r;
+            float2 s = make_float2(0.f, 0.f);
+            if (i < N)
+                for (int sl = 0; sl < P; ++sl) s = s + part[(((int64_t)(bc + bl) * G + g) * P + sl) * N + i];
+            if (g == 0)
+                accE[r][bl] = s;
+            else
+                accH[r][bl] = s;
+        }
+        __syncthreads();
+        for (int r = warp; r < kFinalRows; r += nwarps) {
+            int i = i0 + r;
+            if (i >= N) continue;
+            float2 aJ[2], pJ[2], kJ[2], aM[2], pM[2], kM[2];
+            for (int h = 0; h < 2; ++h) aJ[h] = pJ[h] = kJ[h] = aM[h] = pM[h] = kM[h] = make_float2(0.f, 0.f);
+            const int e1 = row_ptr[i + 1];
+            for (int e = row_ptr[i]; e < e1; ++e) {
+                int j = cols[e];
+                float va = __ldg(na + e), vp = __ldg(np + e);
+                float vk = F == 8 ? __ldg(nk + e) : 0.f;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    int bl = lane + 32 * h;
+                    if (bl < nbc) {
+                        float2 xj = __ldg(xT + (int64_t)j * B + bc + bl);
+                        rfma(aJ[h], va, xj);
+                        rfma(pJ[h], vp, xj);
+                        if (F == 8) {
+                            float2 xm = __ldg(xT + (int64_t)(N + j) * B + bc + bl);
+                            rfma(kJ[h], vk, xj);
+                            rfma(aM[h], va, xm);
+                            rfma(pM[h], vp, xm);
+                            rfma(kM[h], vk, xm);
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                int bl = lane + 32 * h;
+                if (bl < nbc) {
+                    float2 e = accE[r][bl] + nc.c[0] * aJ[h] + nc.c[1] * pJ[h];
+                    if (F == 8) {
+                        e = e + nc.c[2] * kM[h];
+                        float2 hh = accH[r][bl] + nc.c[3] * kJ[h] + nc.c[4] * aM[h] + nc.c[5] * pM[h];
+                        y[(int64_t)(bc + bl) * nunk + N + perm[i]] = hh;
+                    }
+                    y[(int64_t)(bc + bl) * nunk + perm[i]] = e;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ host driver
+
+static void ensure_fused_buffers(aimx_ctx* ctx, int B) {
+    if (ctx->fused_cap >= B) return;
+    const int64_t NG = (int64_t)ctx->n[0] * ctx->n[1] * ctx->n[2];
+    const int F = ctx->F;
+    if (ctx->d_xT) dev_free(ctx, ctx->d_xT);
+    if (ctx->d_G) dev_free(ctx, ctx->d_G);
+    if (ctx->d_S) dev_free(ctx, ctx->d_S);
+    if (ctx->d_part) dev_free(ctx, ctx->d_part);
+    ctx->d_xT = ctx->d_G = ctx->d_S = ctx->d_part = nullptr;
+    ctx->fused_cap = 0;
+    ctx->d_xT = (float*)dev_alloc(ctx, sizeof(float2) * (size_t)ctx->nunk * B);
+    ctx->d_G = (float*)dev_alloc(ctx, sizeof(float2) * (size_t)B * F * NG);
+    ctx->d_S = (float*)dev_alloc(ctx, sizeof(float2) * (size_t)B * F * NG * 4);
+    ctx->d_part = (float*)dev_alloc(ctx, sizeof(float2) * (size_t)B * (F / 4) * ctx->P * ctx->N);
+    ctx->fused_cap = B;
+}
+
+static int* d_plane_lo(aimx_ctx* ctx);
+
+void matvec_fused(aimx_ctx* ctx, double freq, int nrhs, const float* x, float* y, cudaStream_t s) {
+    {
+        StageScope sc(ctx, ST_KERNELGEN, s);
+        ensure_spectra<float>(ctx, freq, s);
+    }
+    Coefs cf = near_coefs(ctx, freq);
+    NearC nc;
+    for (int k = 0; k < 6; ++k) nc.c[k] = make_float2((float)cf.near[k].x, (float)cf.near[k].y);
+    const int Nx = ctx->n[0], Ny = ctx->n[1], Nz = ctx->n[2];
+    const int64_t NG = (int64_t)Nx * Ny * Nz;
+    const int F = ctx->F, N = ctx->N, nunk = ctx->nunk, P = ctx->P, U = ctx->U;
+    const int NP = Nx * Ny;
+    // RHS per pass bounded by an 8 GiB work-buffer budget
+    const size_t per_rhs = sizeof(float2) * ((size_t)nunk + (size_t)F * NG * 5 + (size_t)(F / 4) * P * N);
+    const int cap = (int)std::max<size_t>(1, std::min<size_t>(nrhs, ((size_t)8 << 30) / per_rhs));
+    ensure_fused_buffers(ctx, cap);
+    const float2* tw = twiddles32();
+    int* plo = d_plane_lo(ctx);
+    int* phi = plo + Nz;
+    for (int b0 = 0; b0 < nrhs; b0 += cap) {
+        const int B = std::min(cap, nrhs - b0);
+        const float2* xb = reinterpret_cast<const float2*>(x) + (int64_t)b0 * nunk;
+        float2* yb = reinterpret_cast<float2*>(y) + (int64_t)b0 * nunk;
+        float2* xT = reinterpret_cast<float2*>(ctx->d_xT);
+        float2* G = reinterpret_cast<float2*>(ctx->d_G);
+        float2* S = reinterpret_cast<float2*>(ctx->d_S);
+        float2* part = reinterpret_cast<float2*>(ctx->d_part);
+        {
+            StageScope sc(ctx, ST_TRANSPOSE, s);
+            int64_t tot = (int64_t)nunk * B;
+            k_transpose_x<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(xb, ctx->d_perm, xT, N, nunk, B);
+            AIMX_CUDA_TRY(cudaGetLastError());
+        }
+        {
+            StageScope sc(ctx, ST_GATHER, s);
+            int64_t tot = NG * B;
+            k_gather<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
+                reinterpret_cast<const float4*>(ctx->f32.w), ctx->d_node_ptr, ctx->d_node_w, xT, G, B, F, N, U, NG);
+            AIMX_CUDA_TRY(cudaGetLastError());
+        }
+        {
+            StageScope sc(ctx, ST_XY_FWD, s);
+            size_t sm = ((size_t)NP + (size_t)Ny * (Nx + 1)) * sizeof(float2);
+            AIMX_CUDA_TRY(cudaFuncSetAttribute(k_xy_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            k_xy_fwd<<<dim3(Nz, F, B), kThreads, sm, s>>>(G, S, F, Nx, Ny, Nz, tw);
+            AIMX_CUDA_TRY(cudaGetLastError());
+        }
+        {
+            StageScope sc(ctx, ST_ZPASS, s);
+            size_t sm = (size_t)F * kTX * (2 * Nz + 1) * sizeof(float2);
+            AIMX_CUDA_TRY(cudaFuncSetAttribute(k_zpass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            dim3 grid(Nx / kTX, Ny, 4 * ((B + kRG - 1) / kRG));
+            k_zpass<<<grid, kThreads, sm, s>>>(S, reinterpret_cast<const float2*>(ctx->f32.spec), F, Nx, Ny, Nz, B,
+                                               tw);
+            AIMX_CUDA_TRY(cudaGetLastError());
+        }
+        {
+            StageScope sc(ctx, ST_XY_INV, s);
+            size_t sm = ((size_t)NP + (size_t)Ny * (Nx + 1) + ctx->max_plane_bases) * sizeof(float2);
+            AIMX_CUDA_TRY(cudaFuncSetAttribute(k_xy_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            k_xy_inv<<<dim3(Nz, F / 4, B), kThreads, sm, s>>>(S, ctx->f32.w, ctx->d_anc, plo, phi, part, F, Nx, Ny,
+                                                              Nz, N, P, tw);
+            AIMX_CUDA_TRY(cudaGetLastError());
+        }
+        {
+            StageScope sc(ctx, ST_FINAL, s);
+            k_final<<<(N + kFinalRows - 1) / kFinalRows, kThreads, 0, s>>>(
+                part, xT, ctx->d_row_ptr, ctx->d_cols, ctx->f32.na, ctx->f32.np, ctx->f32.nk, ctx->d_perm, yb, nc, F,
+                N, nunk, P, B);
+            AIMX_CUDA_TRY(cudaGetLastError());
+        }
+    }
+}
+
+// plane ranges on the device (uploaded lazily)
+static int* d_plane_lo(aimx_ctx* ctx) {
+    static_assert(sizeof(int) == 4, "int");
+    if (!ctx->d_plane) {
+        std::vector<int> v(ctx->plane_lo);
+        v.insert(v.end(), ctx->plane_hi.begin(), ctx->plane_hi.end());
+        ctx->d_plane = (int*)dev_alloc(ctx, sizeof(int) * v.size());
+        AIMX_CUDA_TRY(cudaMemcpy(ctx->d_plane, v.data(), sizeof(int) * v.size(), cudaMemcpyHostToDevice));
+        int mpb = 0;
+        for (size_t z = 0; z < ctx->plane_lo.size(); ++z) mpb = std::max(mpb, ctx->plane_hi[z] - ctx->plane_lo[z]);
+        ctx->max_plane_bases = mpb;
+    }
+    return ctx->d_plane;
+}
+
+}  // namespace aimx

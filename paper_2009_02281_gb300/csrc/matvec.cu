@@ -189,6 +189,7 @@ void matvec_generic(aimx_ctx* ctx, double freq, int nrhs, const T* x, T* y, cuda
     const int64_t NG = (int64_t)ctx->n[0] * ctx->n[1] * ctx->n[2];
     for (int b0 = 0; b0 < nrhs; b0 += chunk) {
         int nb = std::min(chunk, nrhs - b0);
+        StageScope sc0(ctx, ST_G_PROJECT, s);
         AIMX_CUDA_TRY(cudaMemsetAsync(grid, 0, sizeof(C) * per_rhs * nb, s));
         int64_t tot = NG * nb;
         k_project<T><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
