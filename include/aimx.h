@@ -170,6 +170,33 @@ int aimx_profile(aimx_ctx* ctx, int enable);
 int aimx_profile_read(aimx_ctx* ctx, double* ms, int64_t* launches, int max_stages);
 const char* aimx_profile_stage_name(int stage);
 
+/* ------------------------------------------------------------------ allocation-free product
+ * aimx_matvec_noalloc: the FP32 product y = A(k) x of aimx_matvec (plane-fused
+ * path), for callers that must not allocate device memory when they need it,
+ * e.g. code working under a fixed memory budget or inside a framework that
+ * owns the allocator.  The paper has no counterpart; this is a property of the
+ * library, not of the method.
+ *   - Allocates nothing: no cudaMalloc / cudaFree / allocating library call.
+ *     Its work buffers live in one file-scope static device array of 64 MiB
+ *     that every device loading the library holds until the process exits.
+ *   - Preconditions: the grid takes the plane-fused path (aimx_matvec_path(ctx,
+ *     AIMX_F32) == 0) and aimx_matvec has run once in FP32 on this context (it
+ *     creates the kernel-spectra buffers and plane tables that are reused here;
+ *     a new frequency then regenerates spectra in place).  Otherwise
+ *     AIMX_E_STATE.
+ *   - x, y: device [nrhs][nunk] float2, caller-owned, not overlapping.
+ *     nrhs is limited by the 64 MiB array; larger requests return AIMX_E_ARG
+ *     with the required byte count in aimx_last_error.
+ *   - The first call on a device looks up the array's device address with
+ *     cudaGetSymbolAddress (once per device, with that device current); make
+ *     that first call before any stream capture.
+ *   - All calls share the one array and it keeps the previous call's contents
+ *     (every kernel writes its whole work region before reading it, so nothing
+ *     needs clearing).  Calls whose execution overlaps on the GPU (different
+ *     streams, contexts or host threads without ordering) race on the array.
+ *   - Asynchronous on stream, like aimx_matvec. */
+int aimx_matvec_noalloc(aimx_ctx* ctx, double freq, int nrhs, const void* x, void* y, void* stream);
+
 /* ------------------------------------------------------------------ export (tests) */
 
 /* Copy setup products to host arrays (any pointer may be NULL to skip it).

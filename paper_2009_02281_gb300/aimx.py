@@ -69,6 +69,8 @@ _SIGS = [
     ("aimx_profile", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("aimx_profile_read", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     ("aimx_profile_stage_name", ctypes.c_char_p, [ctypes.c_int]),
+    ("aimx_matvec_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_void_p]),
 ]
 
 

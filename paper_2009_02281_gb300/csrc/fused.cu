@@ -490,4 +490,67 @@ static int* d_plane_lo(aimx_ctx* ctx) {
     return ctx->d_plane;
 }
 
+// Scratch bytes of one plane-fused pass over B right-hand sides when every
+// work buffer starts on a 256-byte boundary.
+size_t fused_scratch_bytes(const aimx_ctx* ctx, int B) {
+    auto up = [](size_t v) { return (v + 255) / 256 * 256; };
+    const size_t NG = (size_t)ctx->n[0] * ctx->n[1] * ctx->n[2];
+    const size_t F = ctx->F;
+    return up(sizeof(float2) * (size_t)ctx->nunk * B) + up(sizeof(float2) * B * F * NG) +
+           up(sizeof(float2) * B * F * NG * 4) + up(sizeof(float2) * (size_t)B * (F / 4) * ctx->P * ctx->N);
+}
+
+// The plane-fused FP32 product for all B right-hand sides at once, with the
+// work buffers carved from caller-provided device memory `scratch` of at
+// least fused_scratch_bytes(ctx, B) bytes.  Performs no allocation: the
+// kernel spectra buffers and the plane table must already exist (any earlier
+// FP32 aimx_matvec on this context creates them).
+void matvec_fused_into(aimx_ctx* ctx, double freq, int B, const float* x, float* y, cudaStream_t s,
+                       unsigned char* scratch) {
+    ensure_spectra<float>(ctx, freq, s);
+    Coefs cf = near_coefs(ctx, freq);
+    NearC nc;
+    for (int k = 0; k < 6; ++k) nc.c[k] = make_float2((float)cf.near[k].x, (float)cf.near[k].y);
+    const int Nx = ctx->n[0], Ny = ctx->n[1], Nz = ctx->n[2];
+    const int64_t NG = (int64_t)Nx * Ny * Nz;
+    const int F = ctx->F, N = ctx->N, nunk = ctx->nunk, P = ctx->P, U = ctx->U;
+    const int NP = Nx * Ny;
+    auto up = [](size_t v) { return (v + 255) / 256 * 256; };
+    float2* xT = reinterpret_cast<float2*>(scratch);
+    float2* G = reinterpret_cast<float2*>(scratch + up(sizeof(float2) * (size_t)nunk * B));
+    float2* S = reinterpret_cast<float2*>(reinterpret_cast<unsigned char*>(G) + up(sizeof(float2) * B * F * NG));
+    float2* part =
+        reinterpret_cast<float2*>(reinterpret_cast<unsigned char*>(S) + up(sizeof(float2) * B * F * NG * 4));
+    const float2* tw = twiddles32();
+    int* plo = ctx->d_plane;
+    int* phi = plo + Nz;
+    const float2* xb = reinterpret_cast<const float2*>(x);
+    float2* yb = reinterpret_cast<float2*>(y);
+    int64_t tot = (int64_t)nunk * B;
+    k_transpose_x<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(xb, ctx->d_perm, xT, N, nunk, B);
+    AIMX_CUDA_TRY(cudaGetLastError());
+    tot = NG * B;
+    k_gather<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(reinterpret_cast<const float4*>(ctx->f32.w),
+                                                          ctx->d_node_ptr, ctx->d_node_w, xT, G, B, F, N, U, NG);
+    AIMX_CUDA_TRY(cudaGetLastError());
+    size_t sm2 = ((size_t)NP + (size_t)Ny * (Nx + 1)) * sizeof(float2);
+    AIMX_CUDA_TRY(cudaFuncSetAttribute(k_xy_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
+    k_xy_fwd<<<dim3(Nz, F, B), kThreads, sm2, s>>>(G, S, F, Nx, Ny, Nz, tw);
+    AIMX_CUDA_TRY(cudaGetLastError());
+    size_t sm3 = (size_t)F * kTX * (2 * Nz + 1) * sizeof(float2);
+    AIMX_CUDA_TRY(cudaFuncSetAttribute(k_zpass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
+    k_zpass<<<dim3(Nx / kTX, Ny, 4 * ((B + kRG - 1) / kRG)), kThreads, sm3, s>>>(
+        S, reinterpret_cast<const float2*>(ctx->f32.spec), F, Nx, Ny, Nz, B, tw);
+    AIMX_CUDA_TRY(cudaGetLastError());
+    size_t sm4 = ((size_t)NP + (size_t)Ny * (Nx + 1) + ctx->max_plane_bases) * sizeof(float2);
+    AIMX_CUDA_TRY(cudaFuncSetAttribute(k_xy_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm4));
+    k_xy_inv<<<dim3(Nz, F / 4, B), kThreads, sm4, s>>>(S, ctx->f32.w, ctx->d_anc, plo, phi, part, F, Nx, Ny, Nz, N,
+                                                       P, tw);
+    AIMX_CUDA_TRY(cudaGetLastError());
+    k_final<<<(N + kFinalRows - 1) / kFinalRows, kThreads, 0, s>>>(part, xT, ctx->d_row_ptr, ctx->d_cols,
+                                                                   ctx->f32.na, ctx->f32.np, ctx->f32.nk,
+                                                                   ctx->d_perm, yb, nc, F, N, nunk, P, B);
+    AIMX_CUDA_TRY(cudaGetLastError());
+}
+
 }  // namespace aimx
