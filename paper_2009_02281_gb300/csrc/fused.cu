@@ -27,6 +27,7 @@
 #include "aimx_internal.h"
 #include "cplx.cuh"
 #include "fftreg.cuh"
+#include "regfft.cuh"
 
 namespace aimx {
 
@@ -380,7 +381,368 @@ __global__ void __launch_bounds__(kThreads) k_final(const float2* __restrict__ p
     }
 }
 
+// ------------------------------------------------------------------ register-FFT kernels
+// Square planes Nx = Ny = N <= 64 and Nz <= 64: every line transform runs in
+// one thread's registers; shared memory only carries the transposes.
+
+// K2 (register form): thread (px, r) transforms row r for parity px, then
+// column r for both y parities; output block q = px + 2 py.
+template <int N>
+__global__ void __launch_bounds__(2 * N) k_xy_fwd_reg(const float2* __restrict__ G, float2* S, int F, int Nz) {
+    extern __shared__ float2 sm[];
+    constexpr int PITCH = N + 1;
+    const int z = blockIdx.x, f = blockIdx.y, b = blockIdx.z;
+    const int px = threadIdx.x / N, r = threadIdx.x - px * N;
+    float2* pl = sm + px * N * PITCH;
+    const int64_t plane = ((int64_t)(b * F + f) * Nz + z);
+    const float2* src = G + plane * N * N + (int64_t)r * N;
+    float2 v[N];
+#pragma unroll
+    for (int x = 0; x < N; x += 2) {
+        float4 t = __ldg(reinterpret_cast<const float4*>(src + x));
+        v[x] = make_float2(t.x, t.y);
+        v[x + 1] = make_float2(t.z, t.w);
+    }
+    if (px) {
+#pragma unroll
+        for (int x = 1; x < N; ++x) v[x] = v[x] * twc<false>(x, 2 * N);
+    }
+    reg_fft<N, false>(v);
+#pragma unroll
+    for (int k = 0; k < N; ++k) pl[r * PITCH + k] = v[k];
+    __syncthreads();
+#pragma unroll 1
+    for (int py = 0; py < 2; ++py) {
+#pragma unroll
+        for (int y = 0; y < N; ++y) {
+            float2 c = pl[y * PITCH + r];
+            if (py && y) c = c * twc<false>(y, 2 * N);
+            v[y] = c;
+        }
+        reg_fft<N, false>(v);
+        float2* dst = S + (plane * 4 + (px + 2 * py)) * N * N + r;
+#pragma unroll
+        for (int ky = 0; ky < N; ++ky) dst[ky * N] = v[ky];
+    }
+}
+
+// K3 (register form): thread pair (pz = 0, 1) per (field, column) computes the
+// even / odd halves of the zero-padded 2 NZ transform, shared memory carries
+// the per-point mix across fields and the final even + odd sum.
+template <int NZ, int F>
+__global__ void __launch_bounds__(2 * F * 8) k_zpass_reg(float2* S, const float2* __restrict__ spec, int Nx, int Ny,
+                                                          int B) {
+    extern __shared__ float2 sm[];
+    constexpr int TC = 8;
+    constexpr int MZ = 2 * NZ;
+    constexpr int LP = MZ + 1;       // line pitch (kz, all parities)
+    const int Mx = 2 * Nx, My = 2 * Ny;
+    const int NP = Nx * Ny;
+    const int kx0 = blockIdx.x * TC, kyp = blockIdx.y;
+    const int q = blockIdx.z & 3, b = blockIdx.z >> 2;
+    const int px = q & 1, py = q >> 1;
+    const int c = threadIdx.x % TC;
+    const int f = (threadIdx.x / TC) % F;
+    const int pz = threadIdx.x / (TC * F);
+    const int64_t zs = 4 * (int64_t)NP;
+    const int64_t base = (((int64_t)b * F + f) * NZ * 4 + q) * NP + (int64_t)kyp * Nx + kx0 + c;
+    float2* line = sm + (f * TC + c) * LP;
+    float2 v[NZ];
+#pragma unroll
+    for (int z = 0; z < NZ; ++z) v[z] = S[base + z * zs];
+    if (pz) {
+#pragma unroll
+        for (int z = 1; z < NZ; ++z) v[z] = v[z] * twc<false>(z, MZ);
+    }
+    reg_fft<NZ, false>(v);
+#pragma unroll
+    for (int k = 0; k < NZ; ++k) line[2 * k + pz] = v[k];     // spectral index kz = 2k + pz
+    __syncthreads();
+    // mix at (column, kz)
+    const int Ox = Mx / 2 + 1, Oy = My / 2 + 1, Oz = MZ / 2 + 1;
+    const int64_t OT = (int64_t)Ox * Oy * Oz;
+    const int ky = 2 * kyp + py;
+    const int oy = ky <= My / 2 ? ky : My - ky;
+    for (int pt = threadIdx.x; pt < TC * MZ; pt += blockDim.x) {
+        const int cc = pt % TC, kz = pt / TC;
+        const int kx = 2 * (kx0 + cc) + px;
+        const int ox = kx <= Mx / 2 ? kx : Mx - kx;
+        const int oz = kz <= MZ / 2 ? kz : MZ - kz;
+        const int64_t oi = ((int64_t)oz * Oy + oy) * Ox + ox;
+        float2* g = sm + cc * LP + kz;
+        constexpr int fs = TC * LP;
+        if (F == 4) {
+            const float2 s1 = __ldg(spec + oi), s2 = __ldg(spec + OT + oi);
+            g[0] = s1 * g[0];
+            g[fs] = s1 * g[fs];
+            g[2 * fs] = s1 * g[2 * fs];
+            g[3 * fs] = s2 * g[3 * fs];
+        } else {
+            const float2 s1 = __ldg(spec + oi), s2 = __ldg(spec + OT + oi), s3 = __ldg(spec + 2 * OT + oi),
+                         s4 = __ldg(spec + 3 * OT + oi);
+            float2 vx = __ldg(spec + 4 * OT + oi), vy = __ldg(spec + 5 * OT + oi), vz = __ldg(spec + 6 * OT + oi);
+            if (kx > Mx / 2) vx = -vx;
+            if (ky > My / 2) vy = -vy;
+            if (kz > MZ / 2) vz = -vz;
+            float2 jx = g[0], jy = g[fs], jz = g[2 * fs], rj = g[3 * fs];
+            float2 mx = g[4 * fs], my = g[5 * fs], mz = g[6 * fs], rm = g[7 * fs];
+            g[0] = s1 * jx + (vy * mz - vz * my);
+            g[fs] = s1 * jy + (vz * mx - vx * mz);
+            g[2 * fs] = s1 * jz + (vx * my - vy * mx);
+            g[3 * fs] = s2 * rj;
+            g[4 * fs] = s3 * mx - (vy * jz - vz * jy);
+            g[5 * fs] = s3 * my - (vz * jx - vx * jz);
+            g[6 * fs] = s3 * mz - (vx * jy - vy * jx);
+            g[7 * fs] = s4 * rm;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NZ; ++k) v[k] = line[2 * k + pz];
+    reg_fft<NZ, true>(v);
+    if (pz) {
+#pragma unroll
+        for (int z = 1; z < NZ; ++z) v[z] = v[z] * twc<true>(z, MZ);
+    }
+    __syncthreads();
+    if (pz) {
+#pragma unroll
+        for (int z = 0; z < NZ; ++z) line[z] = v[z];
+    }
+    __syncthreads();
+    if (!pz) {
+#pragma unroll
+        for (int z = 0; z < NZ; ++z) S[base + z * zs] = v[z] + line[z];
+    }
+}
+
+// K4 (register form): inverse of K2 plus the interpolation partials.
+template <int N>
+__global__ void __launch_bounds__(2 * N) k_xy_inv_reg(const float2* __restrict__ S, const float* __restrict__ w,
+                                                      const int* __restrict__ anc, const int* __restrict__ plane_lo,
+                                                      const int* __restrict__ plane_hi, float2* part, int F, int Nz,
+                                                      int Ntot, int P) {
+    extern __shared__ float2 sm[];
+    constexpr int PITCH = N + 1;
+    float2* acc = sm + 2 * N * PITCH;
+    const int z = blockIdx.x, grp = blockIdx.y, b = blockIdx.z;
+    const int px = threadIdx.x / N, r = threadIdx.x - px * N;
+    float2* pl = sm + px * N * PITCH;
+    float2* O = sm;                       // parity-0 plane doubles as the output plane
+    const int G = F / 4;
+    const int lo = plane_lo[z], hi = plane_hi[z];
+    const int nb = hi - lo;
+    const int U = P * P * P;
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) acc[k] = make_float2(0.f, 0.f);
+    float2 v[N];
+#pragma unroll 1
+    for (int fl = 0; fl < 4; ++fl) {
+        const int f = grp * 4 + fl;
+        const int64_t plane = ((int64_t)(b * F + f) * Nz + z);
+        // columns kx' = r of both y parities -> plane px (sum over py)
+#pragma unroll 1
+        for (int py = 0; py < 2; ++py) {
+            const float2* src = S + (plane * 4 + (px + 2 * py)) * N * N + r;
+#pragma unroll
+            for (int ky = 0; ky < N; ++ky) v[ky] = __ldg(src + ky * N);
+            reg_fft<N, true>(v);
+            if (py) {
+#pragma unroll
+                for (int y = 0; y < N; ++y) pl[y * PITCH + r] = pl[y * PITCH + r] + (y ? v[y] * twc<true>(y, 2 * N) : v[y]);
+            } else {
+#pragma unroll
+                for (int y = 0; y < N; ++y) pl[y * PITCH + r] = v[y];
+            }
+        }
+        __syncthreads();
+        // rows y = r of plane px, untwisted in x; parity 1 is added into parity 0's row
+#pragma unroll
+        for (int x = 0; x < N; ++x) v[x] = pl[r * PITCH + x];
+        reg_fft<N, true>(v);
+        if (px) {
+#pragma unroll
+            for (int x = 1; x < N; ++x) v[x] = v[x] * twc<true>(x, 2 * N);
+        } else {
+#pragma unroll
+            for (int x = 0; x < N; ++x) O[r * PITCH + x] = v[x];
+        }
+        __syncthreads();
+        if (px) {
+#pragma unroll
+            for (int x = 0; x < N; ++x) O[r * PITCH + x] = O[r * PITCH + x] + v[x];
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+            const int i = lo + k;
+            const int sx = anc[3 * i], sy = anc[3 * i + 1], sz = anc[3 * i + 2];
+            const int slot = z - sz;
+            const float* wi = w + ((int64_t)i * U + slot * P * P) * 4 + fl;
+            float2 s = make_float2(0.f, 0.f);
+            for (int uy = 0; uy < P; ++uy)
+                for (int ux = 0; ux < P; ++ux) rfma(s, __ldg(wi + (uy * P + ux) * 4), O[(sy + uy) * PITCH + sx + ux]);
+            acc[k] = acc[k] + s;
+        }
+        __syncthreads();
+    }
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+        const int i = lo + k;
+        const int slot = z - anc[3 * i + 2];
+        part[(((int64_t)b * G + grp) * P + slot) * Ntot + i] = acc[k];
+    }
+}
+
 // ------------------------------------------------------------------ host driver
+
+static bool reg_path(const aimx_ctx* ctx) {
+    const int N = ctx->n[0];
+    if (ctx->n[1] != N) return false;
+    if (N != 8 && N != 16 && N != 32 && N != 64) return false;
+    const int Nz = ctx->n[2];
+    if (Nz != 8 && Nz != 16 && Nz != 32 && Nz != 64) return false;
+    return (size_t)(2 * N * (N + 1) + ctx->max_plane_bases) * sizeof(float2) <= 200 * 1024;
+}
+
+static void ensure_const_twiddles() {
+    static bool done[64] = {};
+    int dev = 0;
+    AIMX_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev >= 0 && dev < 64 && done[dev]) return;
+    std::vector<float2> t(4096);
+    for (int k = 0; k < 4096; ++k) {
+        double a = -2.0 * kPi * (double)k / 4096.0;
+        t[k] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+    AIMX_CUDA_TRY(cudaMemcpyToSymbol(c_tw4096, t.data(), sizeof(float2) * 4096));
+    if (dev >= 0 && dev < 64) done[dev] = true;
+}
+
+template <class K>
+static void set_smem(K kernel, size_t bytes) {
+    AIMX_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+}
+
+template <int N>
+static void launch_xy_fwd_reg(const aimx_ctx* ctx, const float2* G, float2* S, int B, cudaStream_t s) {
+    size_t sm = 2 * (size_t)N * (N + 1) * sizeof(float2);
+    set_smem(k_xy_fwd_reg<N>, sm);
+    k_xy_fwd_reg<N><<<dim3(ctx->n[2], ctx->F, B), 2 * N, sm, s>>>(G, S, ctx->F, ctx->n[2]);
+}
+
+template <int N>
+static void launch_xy_inv_reg(const aimx_ctx* ctx, const float2* S, const int* plo, const int* phi, float2* part,
+                              int B, cudaStream_t s) {
+    size_t sm = (2 * (size_t)N * (N + 1) + ctx->max_plane_bases) * sizeof(float2);
+    set_smem(k_xy_inv_reg<N>, sm);
+    k_xy_inv_reg<N><<<dim3(ctx->n[2], ctx->F / 4, B), 2 * N, sm, s>>>(S, ctx->f32.w, ctx->d_anc, plo, phi, part,
+                                                                      ctx->F, ctx->n[2], ctx->N, ctx->P);
+}
+
+template <int NZ, int F>
+static void launch_zpass_reg(const aimx_ctx* ctx, float2* S, int B, cudaStream_t s) {
+    size_t sm = (size_t)F * 8 * (2 * NZ + 1) * sizeof(float2);
+    set_smem(k_zpass_reg<NZ, F>, sm);
+    k_zpass_reg<NZ, F><<<dim3(ctx->n[0] / 8, ctx->n[1], 4 * B), 2 * F * 8, sm, s>>>(
+        S, reinterpret_cast<const float2*>(ctx->f32.spec), ctx->n[0], ctx->n[1], B);
+}
+
+struct FusedBufs {
+    float2 *xT, *G, *S, *part;
+};
+
+// One plane-fused pass over B right-hand sides; `timed` wraps each stage in a
+// profiling scope (off for the allocation-free entry point).
+static void run_fused(aimx_ctx* ctx, const NearC& nc, int B, const float2* xb, float2* yb, cudaStream_t s,
+                      const FusedBufs& fb, bool timed) {
+    const int Nx = ctx->n[0], Ny = ctx->n[1], Nz = ctx->n[2];
+    const int64_t NG = (int64_t)Nx * Ny * Nz;
+    const int F = ctx->F, N = ctx->N, nunk = ctx->nunk, P = ctx->P, U = ctx->U;
+    const int NP = Nx * Ny;
+    const float2* tw = twiddles32();
+    const int* plo = ctx->d_plane;
+    const int* phi = plo + Nz;
+    const bool reg = reg_path(ctx);
+    auto scope = [&](int st) { return timed ? new StageScope(ctx, st, s) : nullptr; };
+    StageScope* sc = scope(ST_TRANSPOSE);
+    int64_t tot = (int64_t)nunk * B;
+    k_transpose_x<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(xb, ctx->d_perm, fb.xT, N, nunk, B);
+    AIMX_CUDA_TRY(cudaGetLastError());
+    delete sc;
+    sc = scope(ST_GATHER);
+    tot = NG * B;
+    k_gather<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(reinterpret_cast<const float4*>(ctx->f32.w),
+                                                          ctx->d_node_ptr, ctx->d_node_w, fb.xT, fb.G, B, F, N, U, NG);
+    AIMX_CUDA_TRY(cudaGetLastError());
+    delete sc;
+    sc = scope(ST_XY_FWD);
+    if (reg) {
+        switch (Nx) {
+            case 8: launch_xy_fwd_reg<8>(ctx, fb.G, fb.S, B, s); break;
+            case 16: launch_xy_fwd_reg<16>(ctx, fb.G, fb.S, B, s); break;
+            case 32: launch_xy_fwd_reg<32>(ctx, fb.G, fb.S, B, s); break;
+            default: launch_xy_fwd_reg<64>(ctx, fb.G, fb.S, B, s); break;
+        }
+    } else {
+        size_t sm = ((size_t)NP + (size_t)Ny * (Nx + 1)) * sizeof(float2);
+        set_smem(k_xy_fwd, sm);
+        k_xy_fwd<<<dim3(Nz, F, B), kThreads, sm, s>>>(fb.G, fb.S, F, Nx, Ny, Nz, tw);
+    }
+    AIMX_CUDA_TRY(cudaGetLastError());
+    delete sc;
+    sc = scope(ST_ZPASS);
+    if (reg) {
+        if (F == 4) {
+            switch (Nz) {
+                case 8: launch_zpass_reg<8, 4>(ctx, fb.S, B, s); break;
+                case 16: launch_zpass_reg<16, 4>(ctx, fb.S, B, s); break;
+                case 32: launch_zpass_reg<32, 4>(ctx, fb.S, B, s); break;
+                default: launch_zpass_reg<64, 4>(ctx, fb.S, B, s); break;
+            }
+        } else {
+            switch (Nz) {
+                case 8: launch_zpass_reg<8, 8>(ctx, fb.S, B, s); break;
+                case 16: launch_zpass_reg<16, 8>(ctx, fb.S, B, s); break;
+                case 32: launch_zpass_reg<32, 8>(ctx, fb.S, B, s); break;
+                default: launch_zpass_reg<64, 8>(ctx, fb.S, B, s); break;
+            }
+        }
+    } else {
+        size_t sm = (size_t)F * kTX * (2 * Nz + 1) * sizeof(float2);
+        set_smem(k_zpass, sm);
+        k_zpass<<<dim3(Nx / kTX, Ny, 4 * ((B + kRG - 1) / kRG)), kThreads, sm, s>>>(
+            fb.S, reinterpret_cast<const float2*>(ctx->f32.spec), F, Nx, Ny, Nz, B, tw);
+    }
+    AIMX_CUDA_TRY(cudaGetLastError());
+    delete sc;
+    sc = scope(ST_XY_INV);
+    if (reg) {
+        switch (Nx) {
+            case 8: launch_xy_inv_reg<8>(ctx, fb.S, plo, phi, fb.part, B, s); break;
+            case 16: launch_xy_inv_reg<16>(ctx, fb.S, plo, phi, fb.part, B, s); break;
+            case 32: launch_xy_inv_reg<32>(ctx, fb.S, plo, phi, fb.part, B, s); break;
+            default: launch_xy_inv_reg<64>(ctx, fb.S, plo, phi, fb.part, B, s); break;
+        }
+    } else {
+        size_t sm = ((size_t)NP + (size_t)Ny * (Nx + 1) + ctx->max_plane_bases) * sizeof(float2);
+        set_smem(k_xy_inv, sm);
+        k_xy_inv<<<dim3(Nz, F / 4, B), kThreads, sm, s>>>(fb.S, ctx->f32.w, ctx->d_anc, plo, phi, fb.part, F, Nx, Ny,
+                                                          Nz, N, P, tw);
+    }
+    AIMX_CUDA_TRY(cudaGetLastError());
+    delete sc;
+    sc = scope(ST_FINAL);
+    k_final<<<(N + kFinalRows - 1) / kFinalRows, kThreads, 0, s>>>(fb.part, fb.xT, ctx->d_row_ptr, ctx->d_cols,
+                                                                   ctx->f32.na, ctx->f32.np, ctx->f32.nk, ctx->d_perm,
+                                                                   yb, nc, F, N, nunk, P, B);
+    AIMX_CUDA_TRY(cudaGetLastError());
+    delete sc;
+}
+
+static NearC near_c(const aimx_ctx* ctx, double freq) {
+    Coefs cf = near_coefs(ctx, freq);
+    NearC nc;
+    for (int k = 0; k < 6; ++k) nc.c[k] = make_float2((float)cf.near[k].x, (float)cf.near[k].y);
+    return nc;
+}
 
 static void ensure_fused_buffers(aimx_ctx* ctx, int B) {
     if (ctx->fused_cap >= B) return;
@@ -399,95 +761,40 @@ static void ensure_fused_buffers(aimx_ctx* ctx, int B) {
     ctx->fused_cap = B;
 }
 
-static int* d_plane_lo(aimx_ctx* ctx);
+// plane ranges on the device (uploaded on the first fused call)
+static void ensure_plane_table(aimx_ctx* ctx) {
+    if (ctx->d_plane) return;
+    std::vector<int> v(ctx->plane_lo);
+    v.insert(v.end(), ctx->plane_hi.begin(), ctx->plane_hi.end());
+    ctx->d_plane = (int*)dev_alloc(ctx, sizeof(int) * v.size());
+    AIMX_CUDA_TRY(cudaMemcpy(ctx->d_plane, v.data(), sizeof(int) * v.size(), cudaMemcpyHostToDevice));
+    int mpb = 0;
+    for (size_t z = 0; z < ctx->plane_lo.size(); ++z) mpb = std::max(mpb, ctx->plane_hi[z] - ctx->plane_lo[z]);
+    ctx->max_plane_bases = mpb;
+}
 
 void matvec_fused(aimx_ctx* ctx, double freq, int nrhs, const float* x, float* y, cudaStream_t s) {
     {
         StageScope sc(ctx, ST_KERNELGEN, s);
         ensure_spectra<float>(ctx, freq, s);
     }
-    Coefs cf = near_coefs(ctx, freq);
-    NearC nc;
-    for (int k = 0; k < 6; ++k) nc.c[k] = make_float2((float)cf.near[k].x, (float)cf.near[k].y);
-    const int Nx = ctx->n[0], Ny = ctx->n[1], Nz = ctx->n[2];
-    const int64_t NG = (int64_t)Nx * Ny * Nz;
-    const int F = ctx->F, N = ctx->N, nunk = ctx->nunk, P = ctx->P, U = ctx->U;
-    const int NP = Nx * Ny;
+    ensure_plane_table(ctx);
+    ensure_const_twiddles();
+    const NearC nc = near_c(ctx, freq);
+    const int64_t NG = (int64_t)ctx->n[0] * ctx->n[1] * ctx->n[2];
+    const int F = ctx->F;
     // RHS per pass bounded by an 8 GiB work-buffer budget
-    const size_t per_rhs = sizeof(float2) * ((size_t)nunk + (size_t)F * NG * 5 + (size_t)(F / 4) * P * N);
+    const size_t per_rhs =
+        sizeof(float2) * ((size_t)ctx->nunk + (size_t)F * NG * 5 + (size_t)(F / 4) * ctx->P * ctx->N);
     const int cap = (int)std::max<size_t>(1, std::min<size_t>(nrhs, ((size_t)8 << 30) / per_rhs));
     ensure_fused_buffers(ctx, cap);
-    const float2* tw = twiddles32();
-    int* plo = d_plane_lo(ctx);
-    int* phi = plo + Nz;
+    FusedBufs fb{reinterpret_cast<float2*>(ctx->d_xT), reinterpret_cast<float2*>(ctx->d_G),
+                 reinterpret_cast<float2*>(ctx->d_S), reinterpret_cast<float2*>(ctx->d_part)};
     for (int b0 = 0; b0 < nrhs; b0 += cap) {
         const int B = std::min(cap, nrhs - b0);
-        const float2* xb = reinterpret_cast<const float2*>(x) + (int64_t)b0 * nunk;
-        float2* yb = reinterpret_cast<float2*>(y) + (int64_t)b0 * nunk;
-        float2* xT = reinterpret_cast<float2*>(ctx->d_xT);
-        float2* G = reinterpret_cast<float2*>(ctx->d_G);
-        float2* S = reinterpret_cast<float2*>(ctx->d_S);
-        float2* part = reinterpret_cast<float2*>(ctx->d_part);
-        {
-            StageScope sc(ctx, ST_TRANSPOSE, s);
-            int64_t tot = (int64_t)nunk * B;
-            k_transpose_x<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(xb, ctx->d_perm, xT, N, nunk, B);
-            AIMX_CUDA_TRY(cudaGetLastError());
-        }
-        {
-            StageScope sc(ctx, ST_GATHER, s);
-            int64_t tot = NG * B;
-            k_gather<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
-                reinterpret_cast<const float4*>(ctx->f32.w), ctx->d_node_ptr, ctx->d_node_w, xT, G, B, F, N, U, NG);
-            AIMX_CUDA_TRY(cudaGetLastError());
-        }
-        {
-            StageScope sc(ctx, ST_XY_FWD, s);
-            size_t sm = ((size_t)NP + (size_t)Ny * (Nx + 1)) * sizeof(float2);
-            AIMX_CUDA_TRY(cudaFuncSetAttribute(k_xy_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-            k_xy_fwd<<<dim3(Nz, F, B), kThreads, sm, s>>>(G, S, F, Nx, Ny, Nz, tw);
-            AIMX_CUDA_TRY(cudaGetLastError());
-        }
-        {
-            StageScope sc(ctx, ST_ZPASS, s);
-            size_t sm = (size_t)F * kTX * (2 * Nz + 1) * sizeof(float2);
-            AIMX_CUDA_TRY(cudaFuncSetAttribute(k_zpass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-            dim3 grid(Nx / kTX, Ny, 4 * ((B + kRG - 1) / kRG));
-            k_zpass<<<grid, kThreads, sm, s>>>(S, reinterpret_cast<const float2*>(ctx->f32.spec), F, Nx, Ny, Nz, B,
-                                               tw);
-            AIMX_CUDA_TRY(cudaGetLastError());
-        }
-        {
-            StageScope sc(ctx, ST_XY_INV, s);
-            size_t sm = ((size_t)NP + (size_t)Ny * (Nx + 1) + ctx->max_plane_bases) * sizeof(float2);
-            AIMX_CUDA_TRY(cudaFuncSetAttribute(k_xy_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-            k_xy_inv<<<dim3(Nz, F / 4, B), kThreads, sm, s>>>(S, ctx->f32.w, ctx->d_anc, plo, phi, part, F, Nx, Ny,
-                                                              Nz, N, P, tw);
-            AIMX_CUDA_TRY(cudaGetLastError());
-        }
-        {
-            StageScope sc(ctx, ST_FINAL, s);
-            k_final<<<(N + kFinalRows - 1) / kFinalRows, kThreads, 0, s>>>(
-                part, xT, ctx->d_row_ptr, ctx->d_cols, ctx->f32.na, ctx->f32.np, ctx->f32.nk, ctx->d_perm, yb, nc, F,
-                N, nunk, P, B);
-            AIMX_CUDA_TRY(cudaGetLastError());
-        }
+        run_fused(ctx, nc, B, reinterpret_cast<const float2*>(x) + (int64_t)b0 * ctx->nunk,
+                  reinterpret_cast<float2*>(y) + (int64_t)b0 * ctx->nunk, s, fb, true);
     }
-}
-
-// plane ranges on the device (uploaded lazily)
-static int* d_plane_lo(aimx_ctx* ctx) {
-    static_assert(sizeof(int) == 4, "int");
-    if (!ctx->d_plane) {
-        std::vector<int> v(ctx->plane_lo);
-        v.insert(v.end(), ctx->plane_hi.begin(), ctx->plane_hi.end());
-        ctx->d_plane = (int*)dev_alloc(ctx, sizeof(int) * v.size());
-        AIMX_CUDA_TRY(cudaMemcpy(ctx->d_plane, v.data(), sizeof(int) * v.size(), cudaMemcpyHostToDevice));
-        int mpb = 0;
-        for (size_t z = 0; z < ctx->plane_lo.size(); ++z) mpb = std::max(mpb, ctx->plane_hi[z] - ctx->plane_lo[z]);
-        ctx->max_plane_bases = mpb;
-    }
-    return ctx->d_plane;
 }
 
 // Scratch bytes of one plane-fused pass over B right-hand sides when every
@@ -503,54 +810,21 @@ size_t fused_scratch_bytes(const aimx_ctx* ctx, int B) {
 // The plane-fused FP32 product for all B right-hand sides at once, with the
 // work buffers carved from caller-provided device memory `scratch` of at
 // least fused_scratch_bytes(ctx, B) bytes.  Performs no allocation: the
-// kernel spectra buffers and the plane table must already exist (any earlier
-// FP32 aimx_matvec on this context creates them).
+// kernel spectra buffers, the plane table and the constant twiddles must
+// already exist (any earlier FP32 aimx_matvec on this context creates them).
 void matvec_fused_into(aimx_ctx* ctx, double freq, int B, const float* x, float* y, cudaStream_t s,
                        unsigned char* scratch) {
     ensure_spectra<float>(ctx, freq, s);
-    Coefs cf = near_coefs(ctx, freq);
-    NearC nc;
-    for (int k = 0; k < 6; ++k) nc.c[k] = make_float2((float)cf.near[k].x, (float)cf.near[k].y);
-    const int Nx = ctx->n[0], Ny = ctx->n[1], Nz = ctx->n[2];
-    const int64_t NG = (int64_t)Nx * Ny * Nz;
-    const int F = ctx->F, N = ctx->N, nunk = ctx->nunk, P = ctx->P, U = ctx->U;
-    const int NP = Nx * Ny;
+    const NearC nc = near_c(ctx, freq);
+    const size_t NG = (size_t)ctx->n[0] * ctx->n[1] * ctx->n[2];
+    const size_t F = ctx->F;
     auto up = [](size_t v) { return (v + 255) / 256 * 256; };
-    float2* xT = reinterpret_cast<float2*>(scratch);
-    float2* G = reinterpret_cast<float2*>(scratch + up(sizeof(float2) * (size_t)nunk * B));
-    float2* S = reinterpret_cast<float2*>(reinterpret_cast<unsigned char*>(G) + up(sizeof(float2) * B * F * NG));
-    float2* part =
-        reinterpret_cast<float2*>(reinterpret_cast<unsigned char*>(S) + up(sizeof(float2) * B * F * NG * 4));
-    const float2* tw = twiddles32();
-    int* plo = ctx->d_plane;
-    int* phi = plo + Nz;
-    const float2* xb = reinterpret_cast<const float2*>(x);
-    float2* yb = reinterpret_cast<float2*>(y);
-    int64_t tot = (int64_t)nunk * B;
-    k_transpose_x<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(xb, ctx->d_perm, xT, N, nunk, B);
-    AIMX_CUDA_TRY(cudaGetLastError());
-    tot = NG * B;
-    k_gather<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(reinterpret_cast<const float4*>(ctx->f32.w),
-                                                          ctx->d_node_ptr, ctx->d_node_w, xT, G, B, F, N, U, NG);
-    AIMX_CUDA_TRY(cudaGetLastError());
-    size_t sm2 = ((size_t)NP + (size_t)Ny * (Nx + 1)) * sizeof(float2);
-    AIMX_CUDA_TRY(cudaFuncSetAttribute(k_xy_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
-    k_xy_fwd<<<dim3(Nz, F, B), kThreads, sm2, s>>>(G, S, F, Nx, Ny, Nz, tw);
-    AIMX_CUDA_TRY(cudaGetLastError());
-    size_t sm3 = (size_t)F * kTX * (2 * Nz + 1) * sizeof(float2);
-    AIMX_CUDA_TRY(cudaFuncSetAttribute(k_zpass, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
-    k_zpass<<<dim3(Nx / kTX, Ny, 4 * ((B + kRG - 1) / kRG)), kThreads, sm3, s>>>(
-        S, reinterpret_cast<const float2*>(ctx->f32.spec), F, Nx, Ny, Nz, B, tw);
-    AIMX_CUDA_TRY(cudaGetLastError());
-    size_t sm4 = ((size_t)NP + (size_t)Ny * (Nx + 1) + ctx->max_plane_bases) * sizeof(float2);
-    AIMX_CUDA_TRY(cudaFuncSetAttribute(k_xy_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm4));
-    k_xy_inv<<<dim3(Nz, F / 4, B), kThreads, sm4, s>>>(S, ctx->f32.w, ctx->d_anc, plo, phi, part, F, Nx, Ny, Nz, N,
-                                                       P, tw);
-    AIMX_CUDA_TRY(cudaGetLastError());
-    k_final<<<(N + kFinalRows - 1) / kFinalRows, kThreads, 0, s>>>(part, xT, ctx->d_row_ptr, ctx->d_cols,
-                                                                   ctx->f32.na, ctx->f32.np, ctx->f32.nk,
-                                                                   ctx->d_perm, yb, nc, F, N, nunk, P, B);
-    AIMX_CUDA_TRY(cudaGetLastError());
+    FusedBufs fb;
+    fb.xT = reinterpret_cast<float2*>(scratch);
+    fb.G = reinterpret_cast<float2*>(scratch + up(sizeof(float2) * (size_t)ctx->nunk * B));
+    fb.S = reinterpret_cast<float2*>(reinterpret_cast<unsigned char*>(fb.G) + up(sizeof(float2) * B * F * NG));
+    fb.part = reinterpret_cast<float2*>(reinterpret_cast<unsigned char*>(fb.S) + up(sizeof(float2) * B * F * NG * 4));
+    run_fused(ctx, nc, B, reinterpret_cast<const float2*>(x), reinterpret_cast<float2*>(y), s, fb, false);
 }
 
 }  // namespace aimx
