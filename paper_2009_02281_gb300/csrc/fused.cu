@@ -430,12 +430,13 @@ __global__ void __launch_bounds__(2 * N) k_xy_fwd_reg(const float2* __restrict__
 // even / odd halves of the zero-padded 2 NZ transform, shared memory carries
 // the per-point mix across fields and the final even + odd sum.
 template <int NZ, int F>
-__global__ void __launch_bounds__(2 * F * 8) k_zpass_reg(float2* S, const float2* __restrict__ spec, int Nx, int Ny,
-                                                          int B) {
+__global__ void __launch_bounds__(2 * F * 8, 3) k_zpass_reg(float2* S, const float2* __restrict__ spec, int Nx,
+                                                             int Ny, int B) {
     extern __shared__ float2 sm[];
     constexpr int TC = 8;
     constexpr int MZ = 2 * NZ;
-    constexpr int LP = MZ + 1;       // line pitch (kz, all parities)
+    constexpr int LP = MZ + 2;       // line pitch: adjacent columns 2 banks apart
+    constexpr int FS = TC * LP + 1;  // field stride: adjacent fields 1 bank apart
     const int Mx = 2 * Nx, My = 2 * Ny;
     const int NP = Nx * Ny;
     const int kx0 = blockIdx.x * TC, kyp = blockIdx.y;
@@ -446,7 +447,7 @@ __global__ void __launch_bounds__(2 * F * 8) k_zpass_reg(float2* S, const float2
     const int pz = threadIdx.x / (TC * F);
     const int64_t zs = 4 * (int64_t)NP;
     const int64_t base = (((int64_t)b * F + f) * NZ * 4 + q) * NP + (int64_t)kyp * Nx + kx0 + c;
-    float2* line = sm + (f * TC + c) * LP;
+    float2* line = sm + f * FS + c * LP;
     float2 v[NZ];
 #pragma unroll
     for (int z = 0; z < NZ; ++z) v[z] = S[base + z * zs];
@@ -470,7 +471,7 @@ __global__ void __launch_bounds__(2 * F * 8) k_zpass_reg(float2* S, const float2
         const int oz = kz <= MZ / 2 ? kz : MZ - kz;
         const int64_t oi = ((int64_t)oz * Oy + oy) * Ox + ox;
         float2* g = sm + cc * LP + kz;
-        constexpr int fs = TC * LP;
+        constexpr int fs = FS;
         if (F == 4) {
             const float2 s1 = __ldg(spec + oi), s2 = __ldg(spec + OT + oi);
             g[0] = s1 * g[0];
@@ -621,6 +622,16 @@ static void set_smem(K kernel, size_t bytes) {
     AIMX_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
 }
 
+static int num_sms() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        AIMX_CUDA_TRY(cudaGetDevice(&dev));
+        AIMX_CUDA_TRY(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+    }
+    return n;
+}
+
 template <int N>
 static void launch_xy_fwd_reg(const aimx_ctx* ctx, const float2* G, float2* S, int B, cudaStream_t s) {
     size_t sm = 2 * (size_t)N * (N + 1) * sizeof(float2);
@@ -639,9 +650,10 @@ static void launch_xy_inv_reg(const aimx_ctx* ctx, const float2* S, const int* p
 
 template <int NZ, int F>
 static void launch_zpass_reg(const aimx_ctx* ctx, float2* S, int B, cudaStream_t s) {
-    size_t sm = (size_t)F * 8 * (2 * NZ + 1) * sizeof(float2);
+    constexpr int TC = 8, LP = 2 * NZ + 2, FS = TC * LP + 1;
+    size_t sm = (size_t)F * FS * sizeof(float2);
     set_smem(k_zpass_reg<NZ, F>, sm);
-    k_zpass_reg<NZ, F><<<dim3(ctx->n[0] / 8, ctx->n[1], 4 * B), 2 * F * 8, sm, s>>>(
+    k_zpass_reg<NZ, F><<<dim3(ctx->n[0] / TC, ctx->n[1], 4 * B), 2 * F * TC, sm, s>>>(
         S, reinterpret_cast<const float2*>(ctx->f32.spec), ctx->n[0], ctx->n[1], B);
 }
 
