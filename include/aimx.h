@@ -151,6 +151,63 @@ int aimx_matvec(aimx_ctx* ctx, double freq, int nrhs, const void* x, void* y,
 int aimx_matvec_host(aimx_ctx* ctx, double freq, int nrhs, const void* x, void* y,
                      int precision, void* stream);
 
+/* ------------------------------------------------------------------ solve and sweep */
+
+#define AIMX_PRECOND_DIAG 0   /* inverse of the static self block per basis (diagonal of L_s, Sec. III-A-2) */
+#define AIMX_PRECOND_NONE 1
+
+typedef struct {
+    double tol;               /* target relative true residual |b - A x| / |b| (0 = 1e-6)            */
+    int32_t restart;          /* Krylov vectors per cycle (0 = 50)                                    */
+    int32_t max_iter;         /* total inner iterations per right-hand side (0 = 1000)                */
+    int32_t max_refine;       /* FP64 refinement cycles (0 = max_iter / restart + 10)                 */
+    int32_t inner_precision;  /* AIMX_F32 (default) or AIMX_F64 products inside a cycle              */
+    int32_t precond;          /* AIMX_PRECOND_DIAG (default) or AIMX_PRECOND_NONE                     */
+    int32_t use_x0;           /* 1: x holds an initial guess on entry                                 */
+} aimx_solve_opts;
+
+typedef struct {
+    int32_t iterations;       /* inner GMRES iterations used                                          */
+    int32_t refinements;      /* FP64 refinement cycles used                                          */
+    double rel_residual;      /* final |b - A x| / |b| from the FP64 product                         */
+    int32_t status;           /* AIMX_OK or AIMX_E_NOCONV                                             */
+} aimx_solve_stats;
+
+/* Solve A(k) x = b for nrhs right-hand sides in lockstep (the iterative GMRES
+ * solve of Sec. V): cycles of right-preconditioned GMRES(restart) with FP64
+ * Krylov vectors (classical Gram-Schmidt applied twice) and FP32 (or FP64)
+ * AIMx products, each cycle started from the FP64 true residual b - A x
+ * (iterative refinement).  b, x: device [nrhs][nunk] complex128 (double2),
+ * caller-owned; stats: host array [nrhs] or NULL.  Returns AIMX_E_NOCONV (> 0)
+ * when any right-hand side misses tol.  Synchronises stream. */
+int aimx_solve(aimx_ctx* ctx, double freq, int nrhs, const void* b, void* x, const aimx_solve_opts* opts,
+               aimx_solve_stats* stats, void* stream);
+
+/* Plane-wave right-hand sides (Eq. EFIEdis / CFIEdis excitation): for wave w
+ * with unit propagation direction dirs[w] and polarisation pols[w] (host
+ * [nwave][3] doubles, E0 = 1 V/m, background medium), b[w] = <f_m, E_inc>,
+ * and for AIMX_PMCHWT additionally eta0 <f_m, H_inc> in the second half.
+ * b: device [nwave][nunk] complex128.  Synchronises stream. */
+int aimx_rhs_planewave(aimx_ctx* ctx, double freq, int nwave, const double* dirs, const double* pols, void* b,
+                       void* stream);
+
+/* Far-zone electric field r e^{jkr} E(rhat) of the solved surface currents in
+ * the background medium for ndir unit directions (host [ndir][3]); x: device
+ * [nrhs][nunk] complex128; E: host [nrhs][ndir][3] complex128 (interleaved).
+ * RCS = 4 pi |E|^2 / |E0|^2.  Synchronises stream. */
+int aimx_farfield(aimx_ctx* ctx, double freq, int nrhs, const void* x, int ndir, const double* dirs, double* E,
+                  void* stream);
+
+/* Frequency sweep (Sec. V-A, Discussion: T = T_s + N T_d): for every
+ * frequency, plane-wave right-hand sides, then aimx_solve, reusing the
+ * frequency-independent near matrices built once by aimx_setup; only the grid
+ * kernel spectra and the preconditioner coefficients change per frequency.
+ * X: device [nf][nwave][nunk] complex128; stats: host [nf][nwave] or NULL.
+ * warm_start = 1 starts each frequency from the previous solution.  Returns
+ * AIMX_E_NOCONV if any system missed tol.  Synchronises stream. */
+int aimx_sweep(aimx_ctx* ctx, int nf, const double* freqs, int nwave, const double* dirs, const double* pols, void* X,
+               const aimx_solve_opts* opts, int warm_start, aimx_solve_stats* stats, void* stream);
+
 /* Select the FP32 matvec implementation: 0 = automatic (the plane-fused
  * path whenever the grid is padded to exactly twice a power-of-two size per
  * axis, else the generic path), 1 = always the generic path.  Both compute the

@@ -71,7 +71,40 @@ _SIGS = [
     ("aimx_profile_stage_name", ctypes.c_char_p, [ctypes.c_int]),
     ("aimx_matvec_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
                                            ctypes.c_void_p, ctypes.c_void_p]),
+    ("aimx_solve", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("aimx_rhs_planewave", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("aimx_farfield", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("aimx_sweep", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                  ctypes.c_void_p]),
 ]
+
+PRECOND_DIAG = 0
+PRECOND_NONE = 1
+
+
+class _SolveOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int32), ("max_iter", ctypes.c_int32),
+                ("max_refine", ctypes.c_int32), ("inner_precision", ctypes.c_int32), ("precond", ctypes.c_int32),
+                ("use_x0", ctypes.c_int32)]
+
+
+class _SolveStats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("refinements", ctypes.c_int32), ("rel_residual", ctypes.c_double),
+                ("status", ctypes.c_int32)]
+
+
+def _opts(tol, restart, max_iter, inner_precision, precond, use_x0=0, max_refine=0):
+    return _SolveOpts(float(tol), int(restart), int(max_iter), int(max_refine), int(inner_precision), int(precond),
+                      int(use_x0))
+
+
+def _stats_list(arr):
+    return [dict(iterations=s.iterations, refinements=s.refinements, rel_residual=s.rel_residual, status=s.status)
+            for s in arr]
 
 
 def lib_path():
@@ -197,6 +230,58 @@ class Context:
         """aimx_matvec_host on raw host addresses (e.g. pinned torch tensors)."""
         self._check(self._lib.aimx_matvec_host(self._ctx, float(freq), int(nrhs), ctypes.c_void_p(x_ptr),
                                                ctypes.c_void_p(y_ptr), int(precision), _stream_handle(stream)))
+
+    # ---------------------------------------------------------------- solve / sweep / excitation
+    def rhs_planewave(self, freq, dirs, pols, stream=None):
+        """Plane-wave right-hand sides as a CUDA complex128 tensor [nwave, nunk]."""
+        import torch
+        d = np.ascontiguousarray(np.atleast_2d(dirs), dtype=np.float64)
+        p = np.ascontiguousarray(np.atleast_2d(pols), dtype=np.float64)
+        b = torch.empty((len(d), self.nunk), dtype=torch.complex128, device="cuda")
+        self._check(self._lib.aimx_rhs_planewave(self._ctx, float(freq), len(d), _ptr(d), _ptr(p),
+                                                 ctypes.c_void_p(b.data_ptr()), _stream_handle(stream)))
+        return b
+
+    def solve(self, freq, b, x0=None, tol=1e-6, restart=50, max_iter=1000, inner_precision=F32,
+              precond=PRECOND_DIAG, max_refine=0, stream=None):
+        """Solve A x = b for CUDA complex128 b [nrhs, nunk]; returns (x, stats, status)."""
+        import torch
+        if b.dim() == 1:
+            b = b.unsqueeze(0)
+        b = b.contiguous()
+        x = x0.clone().contiguous() if x0 is not None else torch.empty_like(b)
+        st = (_SolveStats * b.shape[0])()
+        o = _opts(tol, restart, max_iter, inner_precision, precond, 1 if x0 is not None else 0, max_refine)
+        rc = self._check(self._lib.aimx_solve(self._ctx, float(freq), b.shape[0], ctypes.c_void_p(b.data_ptr()),
+                                              ctypes.c_void_p(x.data_ptr()), ctypes.byref(o), st,
+                                              _stream_handle(stream)))
+        return x, _stats_list(st), rc
+
+    def farfield(self, freq, x, dirs, stream=None):
+        """Far-zone E (r e^{jkr} E) [nrhs, ndir, 3] for CUDA complex128 currents x [nrhs, nunk]."""
+        if x.dim() == 1:
+            x = x.unsqueeze(0)
+        x = x.contiguous()
+        d = np.ascontiguousarray(np.atleast_2d(dirs), dtype=np.float64)
+        E = np.zeros((x.shape[0], len(d), 3), dtype=np.complex128)
+        self._check(self._lib.aimx_farfield(self._ctx, float(freq), x.shape[0], ctypes.c_void_p(x.data_ptr()), len(d),
+                                            _ptr(d), _ptr(E), _stream_handle(stream)))
+        return E
+
+    def sweep(self, freqs, dirs, pols, tol=1e-6, restart=50, max_iter=1000, inner_precision=F32,
+              precond=PRECOND_DIAG, warm_start=True, stream=None):
+        """Solve the plane-wave problems at every frequency; returns (X [nf, nwave, nunk], stats, status)."""
+        import torch
+        f = np.ascontiguousarray(freqs, dtype=np.float64)
+        d = np.ascontiguousarray(np.atleast_2d(dirs), dtype=np.float64)
+        p = np.ascontiguousarray(np.atleast_2d(pols), dtype=np.float64)
+        X = torch.empty((len(f), len(d), self.nunk), dtype=torch.complex128, device="cuda")
+        st = (_SolveStats * (len(f) * len(d)))()
+        o = _opts(tol, restart, max_iter, inner_precision, precond)
+        rc = self._check(self._lib.aimx_sweep(self._ctx, len(f), _ptr(f), len(d), _ptr(d), _ptr(p),
+                                              ctypes.c_void_p(X.data_ptr()), ctypes.byref(o), 1 if warm_start else 0,
+                                              st, _stream_handle(stream)))
+        return X, _stats_list(st), rc
 
     def set_path(self, path):
         """0 = automatic (plane-fused FP32 path when supported), 1 = generic path."""

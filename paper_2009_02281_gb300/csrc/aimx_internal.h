@@ -129,6 +129,7 @@ struct aimx_ctx {
     int* d_node_w = nullptr;       // [N*U] weight row index i*U+u
     int* d_node_x = nullptr;       // [N*U] caller basis index of that entry
     double* d_diag = nullptr;      // [N][3] static self terms L^A_s, L^Phi_s, K_s
+    double* d_q5 = nullptr;        // [25][4] 5 x 5 collapsed Gauss-Legendre rule (l1, l2, l3, w)
 
     aimx::PrecData<float> f32;
     aimx::PrecData<double> f64;

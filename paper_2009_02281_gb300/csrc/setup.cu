@@ -571,6 +571,7 @@ void setup_context(aimx_ctx* ctx, const aimx_mesh* mesh, const aimx_material* ma
     triangle_rule(5, qn);
     AIMX_CUDA_TRY(cudaMemcpyToSymbol(c_qproj, qp.data(), qp.size() * sizeof(double)));
     AIMX_CUDA_TRY(cudaMemcpyToSymbol(c_qnear, qn.data(), qn.size() * sizeof(double)));
+    ctx->d_q5 = upload(ctx, qn);
     const int nq_proj = (int)qp.size() / 4, nq_near = (int)qn.size() / 4;
 
     GeomView gv{ctx->d_xyz, ctx->d_tri, ctx->d_area, ctx->d_btri, ctx->d_bfree, ctx->d_blen};

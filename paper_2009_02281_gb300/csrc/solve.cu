@@ -1,0 +1,714 @@
+// Iterative solve, right-hand sides and far field.
+//
+// aimx_solve: restarted GMRES with right preconditioning (the paper solves
+// Eq. EFIEAIMx / CFIEAIMx with GMRES to a relative residual, Sec. V), run in
+// lockstep over all right-hand sides.  Krylov vectors, Gram-Schmidt (CGS2)
+// and Givens rotations are FP64; the inner products A v use the FP32 AIMx
+// matvec (or FP64 on request) inside an FP64 iterative-refinement loop whose
+// true residual b - A x comes from the FP64 matvec.  Preconditioner: the
+// inverse of the per-basis static self block (the diagonal of L_s,
+// Sec. III-A-2), i.e. a scalar per unknown for the EFIE and a 2x2 (J, M)
+// block per basis for the two-region form.
+//
+// aimx_rhs_planewave: <f_m, E_inc> (and eta0 <f_m, H_inc>) by the collapsed
+// Gauss-Legendre rule (5 x 5 points) on each RWG triangle.
+// aimx_farfield: radiation integrals of the surface currents by the same rule.
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <vector>
+
+#include "aimx_internal.h"
+#include "cplx.cuh"
+
+namespace aimx {
+
+using cd = std::complex<double>;
+
+// ------------------------------------------------------------------ vector kernels (FP64, RHS-major)
+
+__global__ void k_dots(const double2* __restrict__ V, const double2* __restrict__ w, double2* h, int nunk,
+                       int64_t vstride, int ldh, int nvec) {
+    // h[b * ldh + i] = sum_n conj(V[b][i][n]) w[b][n]; grid (nvec, nrhs)
+    const int i = blockIdx.x, b = blockIdx.y;
+    const double2* v = V + b * vstride + (int64_t)i * nunk;
+    const double2* x = w + (int64_t)b * nunk;
+    double re = 0.0, im = 0.0;
+    for (int n = threadIdx.x; n < nunk; n += blockDim.x) {
+        double2 a = v[n], c = x[n];
+        re += a.x * c.x + a.y * c.y;
+        im += a.x * c.y - a.y * c.x;
+    }
+    __shared__ double sr[32], si[32];
+    for (int o = 16; o > 0; o >>= 1) {
+        re += __shfl_down_sync(0xffffffffu, re, o);
+        im += __shfl_down_sync(0xffffffffu, im, o);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        sr[wid] = re;
+        si[wid] = im;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+        re = lane < nw ? sr[lane] : 0.0;
+        im = lane < nw ? si[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) {
+            re += __shfl_down_sync(0xffffffffu, re, o);
+            im += __shfl_down_sync(0xffffffffu, im, o);
+        }
+        if (lane == 0) h[b * ldh + i] = make_double2(re, im);
+    }
+    (void)nvec;
+}
+
+// w[b] -= sum_{i < nvec} h[b][i] V[b][i]
+__global__ void k_subtract(const double2* __restrict__ V, double2* w, const double2* __restrict__ h, int nunk,
+                           int64_t vstride, int ldh, int nvec, int nrhs) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)nunk * nrhs) return;
+    const int b = (int)(t / nunk), n = (int)(t % nunk);
+    double2 acc = w[t];
+    const double2* v = V + b * vstride + n;
+    for (int i = 0; i < nvec; ++i) acc = acc - h[b * ldh + i] * v[(int64_t)i * nunk];
+    w[t] = acc;
+}
+
+// y[b] = sum_{i < nvec} c[b][i] V[b][i]
+__global__ void k_combine(const double2* __restrict__ V, const double2* __restrict__ c, double2* y, int nunk,
+                          int64_t vstride, int ldc, int nvec, int nrhs) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)nunk * nrhs) return;
+    const int b = (int)(t / nunk), n = (int)(t % nunk);
+    double2 acc = make_double2(0, 0);
+    const double2* v = V + b * vstride + n;
+    for (int i = 0; i < nvec; ++i) acc = acc + c[b * ldc + i] * v[(int64_t)i * nunk];
+    y[t] = acc;
+}
+
+__global__ void k_norms(const double2* __restrict__ w, double* out, int nunk, int64_t stride) {
+    const int b = blockIdx.x;
+    const double2* x = w + b * stride;
+    double s = 0.0;
+    for (int n = threadIdx.x; n < nunk; n += blockDim.x) s += x[n].x * x[n].x + x[n].y * x[n].y;
+    __shared__ double sh[32];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) out[b] = sqrt(s);
+    }
+}
+
+// dst[b] = src[b] * scale[b] (scale[b] real); zero when scale[b] == 0
+__global__ void k_scale(const double2* __restrict__ src, double2* dst, const double* __restrict__ scale, int nunk,
+                        int64_t sstride, int64_t dstride, int nrhs) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)nunk * nrhs) return;
+    const int b = (int)(t / nunk), n = (int)(t % nunk);
+    dst[b * dstride + n] = scale[b] * src[b * sstride + n];
+}
+
+// r = b - y
+__global__ void k_residual(const double2* __restrict__ bv, const double2* __restrict__ y, double2* r, int64_t n) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t < n) r[t] = bv[t] - y[t];
+}
+
+// x += d on active RHS
+__global__ void k_add_masked(double2* x, const double2* __restrict__ d, const int* __restrict__ active, int nunk,
+                             int nrhs) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)nunk * nrhs) return;
+    if (active[t / nunk]) x[t] = x[t] + d[t];
+}
+
+// Preconditioner application z = M v (M: per-basis 1x1 or 2x2 inverse block), cast to FP32 or kept FP64.
+template <class T>
+__global__ void k_precond(const double2* __restrict__ v, cplx_t<T>* z, const double2* __restrict__ minv, int N,
+                          int nunk, int nrhs, int form, int64_t vstride) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)N * nrhs) return;
+    const int b = (int)(t / N), i = (int)(t % N);
+    const double2* vb = v + (int64_t)b * vstride;
+    cplx_t<T>* zb = z + (int64_t)b * nunk;
+    if (form == AIMX_EFIE) {
+        double2 r = minv[i] * vb[i];
+        zb[i] = mk((T)r.x, (T)r.y);
+    } else {
+        const double2* m = minv + 4 * (int64_t)i;
+        double2 a = vb[i], c = vb[N + i];
+        double2 r0 = m[0] * a + m[1] * c, r1 = m[2] * a + m[3] * c;
+        zb[i] = mk((T)r0.x, (T)r0.y);
+        zb[N + i] = mk((T)r1.x, (T)r1.y);
+    }
+}
+
+// in-place preconditioner on an FP64 vector (for the solution update)
+__global__ void k_precond_inplace(double2* v, const double2* __restrict__ minv, int N, int nunk, int nrhs, int form) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)N * nrhs) return;
+    const int b = (int)(t / N), i = (int)(t % N);
+    double2* vb = v + (int64_t)b * nunk;
+    if (form == AIMX_EFIE) {
+        vb[i] = minv[i] * vb[i];
+    } else {
+        const double2* m = minv + 4 * (int64_t)i;
+        double2 a = vb[i], c = vb[N + i];
+        vb[i] = m[0] * a + m[1] * c;
+        vb[N + i] = m[2] * a + m[3] * c;
+    }
+}
+
+__global__ void k_f32_to_f64(const float2* __restrict__ a, double2* b, int64_t n) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t < n) b[t] = make_double2(a[t].x, a[t].y);
+}
+
+// inverse of the static self block of every basis (internal -> caller order)
+__global__ void k_build_precond(const double* __restrict__ diag, const int* __restrict__ perm, double2* minv, int N,
+                                int form, double2 aA, double2 aP, double2 aK, double2 bK, double2 bA, double2 bP) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double la = diag[3 * i], lp = diag[3 * i + 1], kk = diag[3 * i + 2];
+    const int o = perm[i];
+    if (form == AIMX_EFIE) {
+        double2 d = la * aA + lp * aP;
+        double den = d.x * d.x + d.y * d.y;
+        minv[o] = den > 0 ? make_double2(d.x / den, -d.y / den) : make_double2(1.0, 0.0);
+    } else {
+        double2 a = la * aA + lp * aP, b = kk * aK, c = kk * bK, d = la * bA + lp * bP;
+        double2 det = a * d - b * c;
+        double den = det.x * det.x + det.y * det.y;
+        double2 inv = den > 0 ? make_double2(det.x / den, -det.y / den) : make_double2(1.0, 0.0);
+        double2* m = minv + 4 * (int64_t)o;
+        m[0] = d * inv;
+        m[1] = -(b * inv);
+        m[2] = -(c * inv);
+        m[3] = a * inv;
+    }
+}
+
+static inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+struct SolveWork {
+    double2* V = nullptr;      // [nrhs][m+1][nunk]
+    double2* w = nullptr;      // [nrhs][nunk]
+    double2* r = nullptr;      // [nrhs][nunk]
+    double2* d = nullptr;      // [nrhs][nunk]
+    void* z = nullptr;         // [nrhs][nunk] FP32 or FP64 matvec input
+    void* az = nullptr;        // [nrhs][nunk] matvec output
+    double2* h = nullptr;      // [nrhs][m+1]
+    double* nrm = nullptr;     // [nrhs]
+    int* active = nullptr;     // [nrhs]
+    double2* minv = nullptr;   // [4N]
+};
+
+static void matvec_any(aimx_ctx* ctx, double freq, int nrhs, const void* x, void* y, int prec, cudaStream_t s) {
+    if (prec == AIMX_F32) {
+        if (ctx->path == 0 && fused_supported(ctx))
+            matvec_fused(ctx, freq, nrhs, (const float*)x, (float*)y, s);
+        else
+            matvec_generic<float>(ctx, freq, nrhs, (const float*)x, (float*)y, s);
+    } else {
+        matvec_generic<double>(ctx, freq, nrhs, (const double*)x, (double*)y, s);
+    }
+}
+
+// Givens-based least squares on the host for one RHS.
+struct HostGmres {
+    std::vector<cd> H;   // (m+1) x m column-major
+    std::vector<cd> cs, sn, g;
+    int m;
+    void reset(int m_, double beta) {
+        m = m_;
+        H.assign((size_t)(m + 1) * m, 0.0);
+        cs.assign(m, 0.0);
+        sn.assign(m, 0.0);
+        g.assign(m + 1, 0.0);
+        g[0] = beta;
+    }
+    // add column j (h has j+2 entries); returns |residual estimate|
+    double add_column(int j, const cd* h) {
+        for (int i = 0; i <= j + 1; ++i) H[(size_t)j * (m + 1) + i] = h[i];
+        cd* col = &H[(size_t)j * (m + 1)];
+        for (int i = 0; i < j; ++i) {
+            cd t = std::conj(cs[i]) * col[i] + std::conj(sn[i]) * col[i + 1];
+            col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+            col[i] = t;
+        }
+        double a = std::abs(col[j]), b = std::abs(col[j + 1]);
+        double r = std::hypot(a, b);
+        if (r == 0.0) {
+            cs[j] = 1.0;
+            sn[j] = 0.0;
+        } else {
+            cs[j] = col[j] / r;
+            sn[j] = col[j + 1] / r;
+        }
+        col[j] = r;
+        col[j + 1] = 0.0;
+        cd gj = g[j];
+        g[j] = std::conj(cs[j]) * gj;
+        g[j + 1] = -sn[j] * gj;
+        return std::abs(g[j + 1]);
+    }
+    std::vector<cd> solve(int k) {  // upper-triangular solve of size k
+        std::vector<cd> y(k);
+        for (int i = k - 1; i >= 0; --i) {
+            cd s = g[i];
+            for (int l = i + 1; l < k; ++l) s -= H[(size_t)l * (m + 1) + i] * y[l];
+            y[i] = s / H[(size_t)i * (m + 1) + i];
+        }
+        return y;
+    }
+};
+
+}  // namespace aimx
+
+using namespace aimx;
+
+extern "C" int aimx_solve(aimx_ctx* ctx, double freq, int nrhs, const void* bdev, void* xdev,
+                          const aimx_solve_opts* opts_in, aimx_solve_stats* stats, void* stream) {
+    if (!ctx) return AIMX_E_ARG;
+    if (!bdev || !xdev || nrhs <= 0 || !(freq > 0)) {
+        ctx->last_error = "aimx_solve: bad argument";
+        return AIMX_E_ARG;
+    }
+    aimx_solve_opts o;
+    if (opts_in)
+        o = *opts_in;
+    else
+        std::memset(&o, 0, sizeof(o));
+    if (!(o.tol > 0)) o.tol = 1e-6;
+    if (o.restart <= 0) o.restart = 50;
+    if (o.max_iter <= 0) o.max_iter = 1000;
+    if (o.max_refine <= 0) o.max_refine = o.max_iter / o.restart + 10;
+    if (o.inner_precision != AIMX_F64) o.inner_precision = AIMX_F32;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int N = ctx->N, nunk = ctx->nunk, m = o.restart;
+    const int64_t nv = (int64_t)nunk * nrhs;
+    const int64_t vstride = (int64_t)(m + 1) * nunk;
+    SolveWork W;
+    double2* h2 = nullptr;
+    std::vector<void*> allocs;
+    auto alloc = [&](size_t bytes) {
+        void* p = dev_alloc(ctx, bytes);
+        allocs.push_back(p);
+        return p;
+    };
+    int rc = AIMX_OK;
+    try {
+        W.V = (double2*)alloc(sizeof(double2) * (size_t)nrhs * (m + 1) * nunk);
+        W.w = (double2*)alloc(sizeof(double2) * nv);
+        W.r = (double2*)alloc(sizeof(double2) * nv);
+        W.d = (double2*)alloc(sizeof(double2) * nv);
+        W.z = alloc(sizeof(double2) * nv);
+        W.az = alloc(sizeof(double2) * nv);
+        W.h = (double2*)alloc(sizeof(double2) * (size_t)nrhs * (m + 1));
+        h2 = (double2*)alloc(sizeof(double2) * (size_t)nrhs * (m + 1));
+        W.nrm = (double*)alloc(sizeof(double) * nrhs);
+        W.active = (int*)alloc(sizeof(int) * nrhs);
+        W.minv = (double2*)alloc(sizeof(double2) * 4 * (size_t)N);
+        double* dscale = (double*)alloc(sizeof(double) * nrhs);
+        const double2* b = (const double2*)bdev;
+        double2* x = (double2*)xdev;
+        Coefs cf = near_coefs(ctx, freq);
+        if (o.precond == AIMX_PRECOND_NONE) {
+            std::vector<double2> one(4 * (size_t)N, make_double2(0, 0));
+            for (int i = 0; i < N; ++i) {
+                if (ctx->form == AIMX_EFIE) {
+                    one[i] = make_double2(1, 0);
+                } else {
+                    one[4 * i] = make_double2(1, 0);
+                    one[4 * i + 3] = make_double2(1, 0);
+                }
+            }
+            AIMX_CUDA_TRY(cudaMemcpyAsync(W.minv, one.data(), sizeof(double2) * one.size(), cudaMemcpyHostToDevice, s));
+            AIMX_CUDA_TRY(cudaStreamSynchronize(s));
+        } else {
+            k_build_precond<<<nblk(N), 256, 0, s>>>(ctx->d_diag, ctx->d_perm, W.minv, N, ctx->form, cf.near[0],
+                                                     cf.near[1], cf.near[2], cf.near[3], cf.near[4], cf.near[5]);
+            AIMX_CUDA_TRY(cudaGetLastError());
+        }
+        std::vector<double> bnorm(nrhs), rnorm(nrhs), hn(nrhs);
+        k_norms<<<nrhs, 256, 0, s>>>(b, W.nrm, nunk, nunk);
+        AIMX_CUDA_TRY(cudaMemcpyAsync(bnorm.data(), W.nrm, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+        if (!o.use_x0) AIMX_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double2) * nv, s));
+        AIMX_CUDA_TRY(cudaStreamSynchronize(s));
+        std::vector<int> iters(nrhs, 0), refs(nrhs, 0), act(nrhs, 1);
+        std::vector<double> relres(nrhs, 1.0);
+        auto true_residual = [&]() {
+            matvec_generic<double>(ctx, freq, nrhs, (const double*)x, (double*)W.w, s);
+            k_residual<<<nblk(nv), 256, 0, s>>>(b, W.w, W.r, nv);
+            k_norms<<<nrhs, 256, 0, s>>>(W.r, W.nrm, nunk, nunk);
+            AIMX_CUDA_TRY(cudaMemcpyAsync(rnorm.data(), W.nrm, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+            AIMX_CUDA_TRY(cudaStreamSynchronize(s));
+            for (int k = 0; k < nrhs; ++k) relres[k] = bnorm[k] > 0 ? rnorm[k] / bnorm[k] : 0.0;
+        };
+        true_residual();
+        std::vector<HostGmres> hg(nrhs);
+        std::vector<double2> hb1((size_t)nrhs * (m + 1)), hb2((size_t)nrhs * (m + 1));
+        std::vector<double> scale(nrhs);
+        std::vector<double2> coef((size_t)nrhs * (m + 1));
+        for (int ref = 0; ref < o.max_refine; ++ref) {
+            int nact = 0;
+            for (int k = 0; k < nrhs; ++k) {
+                act[k] = (relres[k] > o.tol && iters[k] < o.max_iter && std::isfinite(relres[k])) ? 1 : 0;
+                nact += act[k];
+            }
+            if (!nact) break;
+            AIMX_CUDA_TRY(cudaMemcpyAsync(W.active, act.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, s));
+            std::vector<double> eta(nrhs);
+            std::vector<int> done(nrhs), kused(nrhs, 0);
+            for (int k = 0; k < nrhs; ++k) {
+                // inner target |r - A d| <= eta |r|: a fraction of what the outer tolerance needs,
+                // floored at what the inner precision can deliver
+                double want = 0.3 * o.tol * bnorm[k] / std::max(rnorm[k], 1e-300);
+                eta[k] = std::max(want, o.inner_precision == AIMX_F32 ? 3e-6 : 1e-13);
+                hg[k].reset(m, rnorm[k]);
+                scale[k] = act[k] && rnorm[k] > 0 ? 1.0 / rnorm[k] : 0.0;
+                done[k] = !act[k];
+            }
+            // v_0 = r / |r|
+            AIMX_CUDA_TRY(cudaMemcpyAsync(dscale, scale.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
+            k_scale<<<nblk(nv), 256, 0, s>>>(W.r, W.V, dscale, nunk, nunk, vstride, nrhs);
+            int jlast = 0;
+            for (int j = 0; j < m; ++j) {
+                // w = A M v_j
+                const double2* vj = W.V + (int64_t)j * nunk;
+                if (o.inner_precision == AIMX_F32) {
+                    k_precond<float><<<nblk((int64_t)N * nrhs), 256, 0, s>>>(vj, (float2*)W.z, W.minv, N, nunk,
+                                                                               nrhs, ctx->form, vstride);
+                    matvec_any(ctx, freq, nrhs, W.z, W.az, AIMX_F32, s);
+                    k_f32_to_f64<<<nblk(nv), 256, 0, s>>>((const float2*)W.az, W.w, nv);
+                } else {
+                    k_precond<double><<<nblk((int64_t)N * nrhs), 256, 0, s>>>(vj, (double2*)W.z, W.minv, N, nunk,
+                                                                                nrhs, ctx->form, vstride);
+                    matvec_any(ctx, freq, nrhs, W.z, W.w, AIMX_F64, s);
+                }
+                // CGS2 against v_0 .. v_j
+                dim3 gd(j + 1, nrhs);
+                k_dots<<<gd, 256, 0, s>>>(W.V, W.w, W.h, nunk, vstride, m + 1, j + 1);
+                k_subtract<<<nblk(nv), 256, 0, s>>>(W.V, W.w, W.h, nunk, vstride, m + 1, j + 1, nrhs);
+                k_dots<<<gd, 256, 0, s>>>(W.V, W.w, h2, nunk, vstride, m + 1, j + 1);
+                k_subtract<<<nblk(nv), 256, 0, s>>>(W.V, W.w, h2, nunk, vstride, m + 1, j + 1, nrhs);
+                k_norms<<<nrhs, 256, 0, s>>>(W.w, W.nrm, nunk, nunk);
+                AIMX_CUDA_TRY(cudaGetLastError());
+                AIMX_CUDA_TRY(cudaMemcpyAsync(hb1.data(), W.h, sizeof(double2) * hb1.size(), cudaMemcpyDeviceToHost, s));
+                AIMX_CUDA_TRY(cudaMemcpyAsync(hb2.data(), h2, sizeof(double2) * hb2.size(), cudaMemcpyDeviceToHost, s));
+                AIMX_CUDA_TRY(cudaMemcpyAsync(hn.data(), W.nrm, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+                AIMX_CUDA_TRY(cudaStreamSynchronize(s));
+                jlast = j + 1;
+                int ndone = 0;
+                for (int k = 0; k < nrhs; ++k) {
+                    if (!done[k]) {
+                        std::vector<cd> col(j + 2);
+                        for (int i = 0; i <= j; ++i) {
+                            double2 a = hb1[(size_t)k * (m + 1) + i], c = hb2[(size_t)k * (m + 1) + i];
+                            col[i] = cd(a.x + c.x, a.y + c.y);
+                        }
+                        col[j + 1] = hn[k];
+                        double est = hg[k].add_column(j, col.data());
+                        kused[k] = j + 1;
+                        if (est <= eta[k] * rnorm[k] || hn[k] <= 1e-14 * rnorm[k] || !std::isfinite(est)) done[k] = 1;
+                    }
+                    scale[k] = (!done[k] && hn[k] > 0) ? 1.0 / hn[k] : 0.0;
+                    ndone += done[k];
+                }
+                if (ndone == nrhs || j + 1 == m) break;
+                AIMX_CUDA_TRY(cudaMemcpyAsync(dscale, scale.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
+                k_scale<<<nblk(nv), 256, 0, s>>>(W.w, W.V + (int64_t)(j + 1) * nunk, dscale, nunk, nunk, vstride, nrhs);
+            }
+            // d = M V y, x += d
+            std::fill(coef.begin(), coef.end(), make_double2(0, 0));
+            for (int k = 0; k < nrhs; ++k) {
+                if (!act[k] || kused[k] == 0) continue;
+                std::vector<cd> y = hg[k].solve(kused[k]);
+                for (int i = 0; i < kused[k]; ++i) coef[(size_t)k * (m + 1) + i] = make_double2(y[i].real(), y[i].imag());
+                iters[k] += kused[k];
+                refs[k] += 1;
+            }
+            AIMX_CUDA_TRY(cudaMemcpyAsync(W.h, coef.data(), sizeof(double2) * coef.size(), cudaMemcpyHostToDevice, s));
+            k_combine<<<nblk(nv), 256, 0, s>>>(W.V, W.h, W.d, nunk, vstride, m + 1, jlast, nrhs);
+            k_precond_inplace<<<nblk((int64_t)N * nrhs), 256, 0, s>>>(W.d, W.minv, N, nunk, nrhs, ctx->form);
+            k_add_masked<<<nblk(nv), 256, 0, s>>>(x, W.d, W.active, nunk, nrhs);
+            AIMX_CUDA_TRY(cudaGetLastError());
+            true_residual();
+        }
+        bool allok = true;
+        for (int k = 0; k < nrhs; ++k) {
+            bool ok = relres[k] <= o.tol;
+            allok = allok && ok;
+            if (stats) {
+                stats[k].iterations = iters[k];
+                stats[k].refinements = refs[k];
+                stats[k].rel_residual = relres[k];
+                stats[k].status = ok ? AIMX_OK : AIMX_E_NOCONV;
+            }
+        }
+        if (!allok) rc = AIMX_E_NOCONV;
+    } catch (const Error& e) {
+        ctx->last_error = e.msg;
+        rc = e.code;
+    }
+    for (void* p : allocs) dev_free(ctx, p);
+    return rc;
+}
+
+// ------------------------------------------------------------------ right-hand sides and far field
+
+namespace aimx {
+
+struct Wave {
+    double d[3];
+    double p[3];
+};
+
+// b[w][perm i] = <f_i, E_inc,w>; PMCHWT also b[w][N + perm i] = eta0 <f_i, H_inc,w>
+__global__ void k_rhs_planewave(const double* __restrict__ xyz, const int* __restrict__ tri,
+                                const double* __restrict__ area, const int* __restrict__ btri,
+                                const int* __restrict__ bfree, const double* __restrict__ blen,
+                                const int* __restrict__ perm, const double* __restrict__ q5, const Wave* __restrict__ waves,
+                                int nwave, int N, int nunk, int form, double k, double inv_eta, double2* out) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)N * nwave) return;
+    const int i = (int)(t % N), wv = (int)(t / N);
+    const Wave W = waves[wv];
+    double2 ve = make_double2(0, 0), vh = make_double2(0, 0);
+    const double h[3] = {inv_eta * (W.d[1] * W.p[2] - W.d[2] * W.p[1]), inv_eta * (W.d[2] * W.p[0] - W.d[0] * W.p[2]),
+                         inv_eta * (W.d[0] * W.p[1] - W.d[1] * W.p[0])};
+    for (int side = 0; side < 2; ++side) {
+        const int tr = btri[2 * i + side];
+        const double sg = side == 0 ? 1.0 : -1.0;
+        const double A = area[tr];
+        const double c = blen[i] / (2.0 * A);
+        const double* pf = xyz + 3 * bfree[2 * i + side];
+        const double* v0 = xyz + 3 * tri[3 * tr];
+        const double* v1 = xyz + 3 * tri[3 * tr + 1];
+        const double* v2 = xyz + 3 * tri[3 * tr + 2];
+        for (int q = 0; q < 25; ++q) {
+            const double l1 = q5[4 * q], l2 = q5[4 * q + 1], l3 = q5[4 * q + 2], wq = q5[4 * q + 3] * A;
+            double r[3], f[3];
+            for (int a = 0; a < 3; ++a) {
+                r[a] = l1 * v0[a] + l2 * v1[a] + l3 * v2[a];
+                f[a] = sg * c * (r[a] - pf[a]);
+            }
+            double s_, c_;
+            sincos(k * (W.d[0] * r[0] + W.d[1] * r[1] + W.d[2] * r[2]), &s_, &c_);
+            const double2 ph = make_double2(c_, -s_);  // e^{-j k d.r}
+            const double fe = f[0] * W.p[0] + f[1] * W.p[1] + f[2] * W.p[2];
+            ve = ve + (wq * fe) * ph;
+            if (form == AIMX_PMCHWT) {
+                const double fh = f[0] * h[0] + f[1] * h[1] + f[2] * h[2];
+                vh = vh + (wq * fh) * ph;
+            }
+        }
+    }
+    double2* ob = out + (int64_t)wv * nunk;
+    ob[perm[i]] = ve;
+    if (form == AIMX_PMCHWT) ob[N + perm[i]] = kEta0 * vh;
+}
+
+// Radiation integrals IJ, IM [nrhs][ndir][3] = sum_i x_i int f_i e^{j k rhat.r'} dS'
+__global__ void k_radiation(const double* __restrict__ xyz, const int* __restrict__ tri, const double* __restrict__ area,
+                            const int* __restrict__ btri, const int* __restrict__ bfree, const double* __restrict__ blen,
+                            const int* __restrict__ perm, const double* __restrict__ q5, const double* __restrict__ dirs,
+                            const double2* __restrict__ x, int N, int nunk, int form, double k, double2* IJ, double2* IM) {
+    const int dir = blockIdx.x, b = blockIdx.y;
+    const double rh[3] = {dirs[3 * dir], dirs[3 * dir + 1], dirs[3 * dir + 2]};
+    double2 aJ[3] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0)};
+    double2 aM[3] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0)};
+    const double2* xb = x + (int64_t)b * nunk;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const double2 cj = xb[perm[i]];
+        const double2 cm = form == AIMX_PMCHWT ? kEta0 * xb[N + perm[i]] : make_double2(0, 0);
+        for (int side = 0; side < 2; ++side) {
+            const int tr = btri[2 * i + side];
+            const double sg = side == 0 ? 1.0 : -1.0;
+            const double A = area[tr];
+            const double c = blen[i] / (2.0 * A);
+            const double* pf = xyz + 3 * bfree[2 * i + side];
+            const double* v0 = xyz + 3 * tri[3 * tr];
+            const double* v1 = xyz + 3 * tri[3 * tr + 1];
+            const double* v2 = xyz + 3 * tri[3 * tr + 2];
+            for (int q = 0; q < 25; ++q) {
+                const double l1 = q5[4 * q], l2 = q5[4 * q + 1], l3 = q5[4 * q + 2], wq = q5[4 * q + 3] * A;
+                double r[3], f[3];
+                for (int a = 0; a < 3; ++a) {
+                    r[a] = l1 * v0[a] + l2 * v1[a] + l3 * v2[a];
+                    f[a] = sg * c * (r[a] - pf[a]) * wq;
+                }
+                double s_, c_;
+                sincos(k * (rh[0] * r[0] + rh[1] * r[1] + rh[2] * r[2]), &s_, &c_);
+                const double2 ph = make_double2(c_, s_);  // e^{+j k rhat.r'}
+                const double2 pj = cj * ph, pm = cm * ph;
+                for (int a = 0; a < 3; ++a) {
+                    aJ[a] = aJ[a] + f[a] * pj;
+                    aM[a] = aM[a] + f[a] * pm;
+                }
+            }
+        }
+    }
+    __shared__ double red[12][256];
+    for (int a = 0; a < 3; ++a) {
+        red[4 * a][threadIdx.x] = aJ[a].x;
+        red[4 * a + 1][threadIdx.x] = aJ[a].y;
+        red[4 * a + 2][threadIdx.x] = aM[a].x;
+        red[4 * a + 3][threadIdx.x] = aM[a].y;
+    }
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st)
+            for (int c = 0; c < 12; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const int ndir = gridDim.x;
+        for (int a = 0; a < 3; ++a) {
+            IJ[((int64_t)b * ndir + dir) * 3 + a] = make_double2(red[4 * a][0], red[4 * a + 1][0]);
+            IM[((int64_t)b * ndir + dir) * 3 + a] = make_double2(red[4 * a + 2][0], red[4 * a + 3][0]);
+        }
+    }
+}
+
+static double background_k(const aimx_ctx* ctx, double freq, double* eta1) {
+    const double w = 2.0 * kPi * freq;
+    const double mu = kMu0 * ctx->mu_out, eps = kEps0 * ctx->eps_out;
+    if (eta1) *eta1 = std::sqrt(mu / eps);
+    return w * std::sqrt(mu * eps);
+}
+
+}  // namespace aimx
+
+extern "C" int aimx_rhs_planewave(aimx_ctx* ctx, double freq, int nwave, const double* dirs, const double* pols,
+                                  void* b, void* stream) {
+    if (!ctx) return AIMX_E_ARG;
+    if (nwave <= 0 || !dirs || !pols || !b || !(freq > 0)) {
+        ctx->last_error = "aimx_rhs_planewave: bad argument";
+        return AIMX_E_ARG;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    try {
+        std::vector<Wave> wv(nwave);
+        for (int k = 0; k < nwave; ++k)
+            for (int a = 0; a < 3; ++a) {
+                wv[k].d[a] = dirs[3 * k + a];
+                wv[k].p[a] = pols[3 * k + a];
+            }
+        Wave* dw = (Wave*)dev_alloc(ctx, sizeof(Wave) * nwave);
+        AIMX_CUDA_TRY(cudaMemcpyAsync(dw, wv.data(), sizeof(Wave) * nwave, cudaMemcpyHostToDevice, s));
+        double eta1 = 0;
+        const double k = background_k(ctx, freq, &eta1);
+        const int64_t tot = (int64_t)ctx->N * nwave;
+        k_rhs_planewave<<<nblk(tot, 128), 128, 0, s>>>(ctx->d_xyz, ctx->d_tri, ctx->d_area, ctx->d_btri, ctx->d_bfree,
+                                                      ctx->d_blen, ctx->d_perm, ctx->d_q5, dw, nwave, ctx->N, ctx->nunk,
+                                                      ctx->form, k, 1.0 / eta1, (double2*)b);
+        AIMX_CUDA_TRY(cudaGetLastError());
+        AIMX_CUDA_TRY(cudaStreamSynchronize(s));
+        dev_free(ctx, dw);
+    } catch (const Error& e) {
+        ctx->last_error = e.msg;
+        return e.code;
+    }
+    return AIMX_OK;
+}
+
+extern "C" int aimx_farfield(aimx_ctx* ctx, double freq, int nrhs, const void* x, int ndir, const double* dirs,
+                             double* E, void* stream) {
+    if (!ctx) return AIMX_E_ARG;
+    if (nrhs <= 0 || ndir <= 0 || !x || !dirs || !E || !(freq > 0)) {
+        ctx->last_error = "aimx_farfield: bad argument";
+        return AIMX_E_ARG;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    try {
+        const double w = 2.0 * kPi * freq;
+        double eta1 = 0;
+        const double k = background_k(ctx, freq, &eta1);
+        const double mu = kMu0 * ctx->mu_out;
+        double* dd = (double*)dev_alloc(ctx, sizeof(double) * 3 * ndir);
+        double2* IJ = (double2*)dev_alloc(ctx, sizeof(double2) * 3 * (size_t)ndir * nrhs);
+        double2* IM = (double2*)dev_alloc(ctx, sizeof(double2) * 3 * (size_t)ndir * nrhs);
+        AIMX_CUDA_TRY(cudaMemcpyAsync(dd, dirs, sizeof(double) * 3 * ndir, cudaMemcpyHostToDevice, s));
+        k_radiation<<<dim3(ndir, nrhs), 256, 0, s>>>(ctx->d_xyz, ctx->d_tri, ctx->d_area, ctx->d_btri, ctx->d_bfree,
+                                                     ctx->d_blen, ctx->d_perm, ctx->d_q5, dd, (const double2*)x, ctx->N,
+                                                     ctx->nunk, ctx->form, k, IJ, IM);
+        AIMX_CUDA_TRY(cudaGetLastError());
+        std::vector<double2> hj(3 * (size_t)ndir * nrhs), hm(hj.size());
+        AIMX_CUDA_TRY(cudaMemcpyAsync(hj.data(), IJ, sizeof(double2) * hj.size(), cudaMemcpyDeviceToHost, s));
+        AIMX_CUDA_TRY(cudaMemcpyAsync(hm.data(), IM, sizeof(double2) * hm.size(), cudaMemcpyDeviceToHost, s));
+        AIMX_CUDA_TRY(cudaStreamSynchronize(s));
+        dev_free(ctx, dd);
+        dev_free(ctx, IJ);
+        dev_free(ctx, IM);
+        // E = -j w mu / (4 pi) (I_J - (rhat.I_J) rhat) + j k / (4 pi) rhat x I_M
+        for (int b = 0; b < nrhs; ++b)
+            for (int d = 0; d < ndir; ++d) {
+                const double* rh = dirs + 3 * d;
+                cd ij[3], im[3];
+                for (int a = 0; a < 3; ++a) {
+                    double2 v = hj[((size_t)b * ndir + d) * 3 + a], u = hm[((size_t)b * ndir + d) * 3 + a];
+                    ij[a] = cd(v.x, v.y);
+                    im[a] = cd(u.x, u.y);
+                }
+                cd dotp = rh[0] * ij[0] + rh[1] * ij[1] + rh[2] * ij[2];
+                cd cr[3] = {rh[1] * im[2] - rh[2] * im[1], rh[2] * im[0] - rh[0] * im[2], rh[0] * im[1] - rh[1] * im[0]};
+                for (int a = 0; a < 3; ++a) {
+                    cd e = cd(0, -w * mu / (4.0 * kPi)) * (ij[a] - dotp * rh[a]) + cd(0, k / (4.0 * kPi)) * cr[a];
+                    E[2 * (((size_t)b * ndir + d) * 3 + a)] = e.real();
+                    E[2 * (((size_t)b * ndir + d) * 3 + a) + 1] = e.imag();
+                }
+            }
+    } catch (const Error& e) {
+        ctx->last_error = e.msg;
+        return e.code;
+    }
+    return AIMX_OK;
+}
+
+extern "C" int aimx_sweep(aimx_ctx* ctx, int nf, const double* freqs, int nwave, const double* dirs,
+                          const double* pols, void* X, const aimx_solve_opts* opts, int warm_start,
+                          aimx_solve_stats* stats, void* stream) {
+    if (!ctx) return AIMX_E_ARG;
+    if (nf <= 0 || !freqs || nwave <= 0 || !X) {
+        ctx->last_error = "aimx_sweep: bad argument";
+        return AIMX_E_ARG;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const size_t per = sizeof(double2) * (size_t)nwave * ctx->nunk;
+    double2* bw = nullptr;
+    int worst = AIMX_OK;
+    try {
+        bw = (double2*)dev_alloc(ctx, per);
+        aimx_solve_opts o;
+        if (opts)
+            o = *opts;
+        else
+            std::memset(&o, 0, sizeof(o));
+        for (int f = 0; f < nf; ++f) {
+            int rc = aimx_rhs_planewave(ctx, freqs[f], nwave, dirs, pols, bw, stream);
+            if (rc < 0) throw Error{rc, ctx->last_error};
+            char* xf = (char*)X + per * f;
+            o.use_x0 = 0;
+            if (warm_start && f > 0) {
+                AIMX_CUDA_TRY(cudaMemcpyAsync(xf, (char*)X + per * (f - 1), per, cudaMemcpyDeviceToDevice, s));
+                o.use_x0 = 1;
+            }
+            rc = aimx_solve(ctx, freqs[f], nwave, bw, xf, &o, stats ? stats + (size_t)f * nwave : nullptr, stream);
+            if (rc < 0) throw Error{rc, ctx->last_error};
+            if (rc > 0) worst = rc;
+        }
+    } catch (const Error& e) {
+        if (bw) dev_free(ctx, bw);
+        ctx->last_error = e.msg;
+        return e.code;
+    }
+    dev_free(ctx, bw);
+    return worst;
+}
