@@ -430,7 +430,7 @@ __global__ void __launch_bounds__(2 * N) k_xy_fwd_reg(const float2* __restrict__
 // even / odd halves of the zero-padded 2 NZ transform, shared memory carries
 // the per-point mix across fields and the final even + odd sum.
 template <int NZ, int F>
-__global__ void __launch_bounds__(2 * F * 8, 3) k_zpass_reg(float2* S, const float2* __restrict__ spec, int Nx,
+__global__ void __launch_bounds__(2 * F * 8) k_zpass_reg(float2* S, const float2* __restrict__ spec, int Nx,
                                                              int Ny, int B) {
     extern __shared__ float2 sm[];
     constexpr int TC = 8;
