@@ -155,6 +155,9 @@ int aimx_matvec_host(aimx_ctx* ctx, double freq, int nrhs, const void* x, void* 
 
 #define AIMX_PRECOND_DIAG 0   /* inverse of the static self block per basis (diagonal of L_s, Sec. III-A-2) */
 #define AIMX_PRECOND_NONE 1
+#define AIMX_PRECOND_BLOCK 2  /* block Jacobi: bases grouped by 2x2x2 anchor cells (<= 32 per block); each block
+                                 is the full AIMx matrix block, static near part plus the grid-generated
+                                 frequency-dependent part (Sec. III-A-2), inverted in FP64, applied in FP32 */
 
 typedef struct {
     double tol;               /* target relative true residual |b - A x| / |b| (0 = 1e-6)            */
@@ -182,6 +185,12 @@ typedef struct {
  * when any right-hand side misses tol.  Synchronises stream. */
 int aimx_solve(aimx_ctx* ctx, double freq, int nrhs, const void* b, void* x, const aimx_solve_opts* opts,
                aimx_solve_stats* stats, void* stream);
+
+/* z = M v for the preconditioner `precond` (AIMX_PRECOND_*) at freq; v, z:
+ * device [nrhs][nunk] complex128, not overlapping.  The block preconditioner
+ * is assembled and inverted on the first call at a frequency and cached.
+ * Synchronises stream. */
+int aimx_precond_apply(aimx_ctx* ctx, double freq, int precond, int nrhs, const void* v, void* z, void* stream);
 
 /* Plane-wave right-hand sides (Eq. EFIEdis / CFIEdis excitation): for wave w
  * with unit propagation direction dirs[w] and polarisation pols[w] (host

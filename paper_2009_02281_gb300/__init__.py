@@ -4,4 +4,5 @@ The compute path is the CUDA library ``libaimx.so`` (sources in ``csrc/``, C ABI
 ``include/aimx.h``); ``aimx`` is its thin ctypes binding.
 """
 
-from .aimx import (AimxError, Context, EFIE, PMCHWT, F32, F64, PRECOND_DIAG, PRECOND_NONE, load)  # noqa: F401
+from .aimx import (AimxError, Context, EFIE, PMCHWT, F32, F64, PRECOND_DIAG, PRECOND_NONE, PRECOND_BLOCK,  # noqa: F401
+                   load)

@@ -80,10 +80,13 @@ _SIGS = [
     ("aimx_sweep", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                   ctypes.c_void_p]),
+    ("aimx_precond_apply", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
 ]
 
 PRECOND_DIAG = 0
 PRECOND_NONE = 1
+PRECOND_BLOCK = 2
 
 
 class _SolveOpts(ctypes.Structure):
@@ -256,6 +259,18 @@ class Context:
                                               ctypes.c_void_p(x.data_ptr()), ctypes.byref(o), st,
                                               _stream_handle(stream)))
         return x, _stats_list(st), rc
+
+    def precond_apply(self, freq, v, precond=PRECOND_BLOCK, stream=None):
+        """z = M v for CUDA complex128 v [nrhs, nunk]."""
+        import torch
+        if v.dim() == 1:
+            v = v.unsqueeze(0)
+        v = v.contiguous()
+        z = torch.empty_like(v)
+        self._check(self._lib.aimx_precond_apply(self._ctx, float(freq), int(precond), v.shape[0],
+                                                 ctypes.c_void_p(v.data_ptr()), ctypes.c_void_p(z.data_ptr()),
+                                                 _stream_handle(stream)))
+        return z
 
     def farfield(self, freq, x, dirs, stream=None):
         """Far-zone E (r e^{jkr} E) [nrhs, ndir, 3] for CUDA complex128 currents x [nrhs, nunk]."""

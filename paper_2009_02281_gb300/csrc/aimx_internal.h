@@ -20,6 +20,17 @@ constexpr double kEta0 = kMu0 * kC0;
 constexpr int kMaxQuad = 64;        // points of the largest triangle rule kept on the device
 constexpr int kTwiddleLen = 4096;   // largest power-of-two FFT length supported
 
+template <class T>
+struct Cplx;
+template <>
+struct Cplx<float> {
+    using type = float2;
+};
+template <>
+struct Cplx<double> {
+    using type = double2;
+};
+
 // Status carrier used inside the library (never crosses the ABI).
 struct Error {
     int code;
@@ -83,6 +94,16 @@ struct Profiler {
     std::vector<cudaEvent_t> pool;
     double ms[ST_COUNT] = {};
     int64_t count[ST_COUNT] = {};
+};
+
+// block-Jacobi preconditioner state (precond.cu)
+struct PrecondBlocks {
+    int nblk = 0, maxnb = 0, D = 0;   // blocks, bases per block (max), matrix order
+    int* d_ptr = nullptr;            // [nblk+1]
+    int* d_idx = nullptr;            // [N] internal basis ids grouped by block
+    double2* d_work = nullptr;       // [nblk][D][D] FP64 assembly / factorisation
+    float2* d_inv = nullptr;         // [nblk][D][D] FP32 inverse
+    double freq = -1.0;
 };
 
 }  // namespace aimx
@@ -153,6 +174,7 @@ struct aimx_ctx {
     int path = 0;                  // 0 = automatic, 1 = force the generic FFT path
 
     aimx::Profiler prof;
+    aimx::PrecondBlocks pc;
 
     int64_t device_bytes = 0;
     std::string last_error;
@@ -210,6 +232,12 @@ struct StageScope {
 // fused.cu
 bool fused_supported(const aimx_ctx* ctx);
 void matvec_fused(aimx_ctx* ctx, double freq, int nrhs, const float* x, float* y, cudaStream_t s);
+
+// precond.cu
+void precond_block_prepare(aimx_ctx* ctx, double freq, cudaStream_t s);
+template <class T>
+void precond_block_apply(aimx_ctx* ctx, const double2* v, int64_t vstride, typename Cplx<T>::type* z, int nrhs,
+                         cudaStream_t s);
 
 // matvec.cu
 template <class T>

@@ -2,18 +2,10 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "aimx_internal.h"
+
 namespace aimx {
 
-template <class T>
-struct Cplx;
-template <>
-struct Cplx<float> {
-    using type = float2;
-};
-template <>
-struct Cplx<double> {
-    using type = double2;
-};
 template <class T>
 using cplx_t = typename Cplx<T>::type;
 

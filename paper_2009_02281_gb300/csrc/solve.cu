@@ -319,7 +319,9 @@ extern "C" int aimx_solve(aimx_ctx* ctx, double freq, int nrhs, const void* bdev
         const double2* b = (const double2*)bdev;
         double2* x = (double2*)xdev;
         Coefs cf = near_coefs(ctx, freq);
-        if (o.precond == AIMX_PRECOND_NONE) {
+        const bool block = o.precond == AIMX_PRECOND_BLOCK;
+        if (block) precond_block_prepare(ctx, freq, s);
+        if (o.precond == AIMX_PRECOND_NONE || block) {
             std::vector<double2> one(4 * (size_t)N, make_double2(0, 0));
             for (int i = 0; i < N; ++i) {
                 if (ctx->form == AIMX_EFIE) {
@@ -383,13 +385,19 @@ extern "C" int aimx_solve(aimx_ctx* ctx, double freq, int nrhs, const void* bdev
                 // w = A M v_j
                 const double2* vj = W.V + (int64_t)j * nunk;
                 if (o.inner_precision == AIMX_F32) {
-                    k_precond<float><<<nblk((int64_t)N * nrhs), 256, 0, s>>>(vj, (float2*)W.z, W.minv, N, nunk,
-                                                                               nrhs, ctx->form, vstride);
+                    if (block)
+                        precond_block_apply<float>(ctx, vj, vstride, (float2*)W.z, nrhs, s);
+                    else
+                        k_precond<float><<<nblk((int64_t)N * nrhs), 256, 0, s>>>(vj, (float2*)W.z, W.minv, N, nunk,
+                                                                                   nrhs, ctx->form, vstride);
                     matvec_any(ctx, freq, nrhs, W.z, W.az, AIMX_F32, s);
                     k_f32_to_f64<<<nblk(nv), 256, 0, s>>>((const float2*)W.az, W.w, nv);
                 } else {
-                    k_precond<double><<<nblk((int64_t)N * nrhs), 256, 0, s>>>(vj, (double2*)W.z, W.minv, N, nunk,
-                                                                                nrhs, ctx->form, vstride);
+                    if (block)
+                        precond_block_apply<double>(ctx, vj, vstride, (double2*)W.z, nrhs, s);
+                    else
+                        k_precond<double><<<nblk((int64_t)N * nrhs), 256, 0, s>>>(vj, (double2*)W.z, W.minv, N,
+                                                                                    nunk, nrhs, ctx->form, vstride);
                     matvec_any(ctx, freq, nrhs, W.z, W.w, AIMX_F64, s);
                 }
                 // CGS2 against v_0 .. v_j
@@ -436,8 +444,13 @@ extern "C" int aimx_solve(aimx_ctx* ctx, double freq, int nrhs, const void* bdev
             }
             AIMX_CUDA_TRY(cudaMemcpyAsync(W.h, coef.data(), sizeof(double2) * coef.size(), cudaMemcpyHostToDevice, s));
             k_combine<<<nblk(nv), 256, 0, s>>>(W.V, W.h, W.d, nunk, vstride, m + 1, jlast, nrhs);
-            k_precond_inplace<<<nblk((int64_t)N * nrhs), 256, 0, s>>>(W.d, W.minv, N, nunk, nrhs, ctx->form);
-            k_add_masked<<<nblk(nv), 256, 0, s>>>(x, W.d, W.active, nunk, nrhs);
+            if (block) {
+                precond_block_apply<double>(ctx, W.d, nunk, (double2*)W.z, nrhs, s);
+                k_add_masked<<<nblk(nv), 256, 0, s>>>(x, (const double2*)W.z, W.active, nunk, nrhs);
+            } else {
+                k_precond_inplace<<<nblk((int64_t)N * nrhs), 256, 0, s>>>(W.d, W.minv, N, nunk, nrhs, ctx->form);
+                k_add_masked<<<nblk(nv), 256, 0, s>>>(x, W.d, W.active, nunk, nrhs);
+            }
             AIMX_CUDA_TRY(cudaGetLastError());
             true_residual();
         }
@@ -711,4 +724,49 @@ extern "C" int aimx_sweep(aimx_ctx* ctx, int nf, const double* freqs, int nwave,
     }
     dev_free(ctx, bw);
     return worst;
+}
+
+extern "C" int aimx_precond_apply(aimx_ctx* ctx, double freq, int precond, int nrhs, const void* v, void* z,
+                                  void* stream) {
+    if (!ctx) return AIMX_E_ARG;
+    if (nrhs <= 0 || !v || !z || !(freq > 0) || precond < 0 || precond > 2) {
+        ctx->last_error = "aimx_precond_apply: bad argument";
+        return AIMX_E_ARG;
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int N = ctx->N, nunk = ctx->nunk;
+    try {
+        if (precond == AIMX_PRECOND_BLOCK) {
+            precond_block_prepare(ctx, freq, s);
+            precond_block_apply<double>(ctx, (const double2*)v, nunk, (double2*)z, nrhs, s);
+        } else {
+            double2* minv = (double2*)dev_alloc(ctx, sizeof(double2) * 4 * (size_t)N);
+            if (precond == AIMX_PRECOND_NONE) {
+                std::vector<double2> one(4 * (size_t)N, make_double2(0, 0));
+                for (int i = 0; i < N; ++i) {
+                    if (ctx->form == AIMX_EFIE) {
+                        one[i] = make_double2(1, 0);
+                    } else {
+                        one[4 * i] = make_double2(1, 0);
+                        one[4 * i + 3] = make_double2(1, 0);
+                    }
+                }
+                AIMX_CUDA_TRY(cudaMemcpy(minv, one.data(), sizeof(double2) * one.size(), cudaMemcpyHostToDevice));
+            } else {
+                Coefs cf = near_coefs(ctx, freq);
+                k_build_precond<<<nblk(N), 256, 0, s>>>(ctx->d_diag, ctx->d_perm, minv, N, ctx->form, cf.near[0],
+                                                         cf.near[1], cf.near[2], cf.near[3], cf.near[4], cf.near[5]);
+            }
+            k_precond<double><<<nblk((int64_t)N * nrhs), 256, 0, s>>>((const double2*)v, (double2*)z, minv, N, nunk,
+                                                                        nrhs, ctx->form, nunk);
+            AIMX_CUDA_TRY(cudaGetLastError());
+            AIMX_CUDA_TRY(cudaStreamSynchronize(s));
+            dev_free(ctx, minv);
+        }
+        AIMX_CUDA_TRY(cudaStreamSynchronize(s));
+    } catch (const Error& e) {
+        ctx->last_error = e.msg;
+        return e.code;
+    }
+    return AIMX_OK;
 }
