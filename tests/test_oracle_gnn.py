@@ -1,0 +1,94 @@
+"""Pins for the FP64 reference of the learned preconditioner network.
+
+Gradients from explicit backpropagation are checked against central finite
+differences of the loss, for the scalar (EFIE) and 2x2-block (two-region)
+output forms; the preconditioner application is checked against an explicit
+dense matrix.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import gnn
+
+
+def _graph(N, seed):
+    rng = np.random.default_rng(seed)
+    rows, cols = [], []
+    for m in range(N):
+        nb = set([m] + list(rng.choice(N, size=4, replace=False)))
+        for n in sorted(nb):
+            rows.append(m)
+            cols.append(n)
+    rows, cols = np.array(rows), np.array(cols)
+    # make the pattern symmetric like the near relation
+    pairs = set(zip(rows, cols)) | set(zip(cols, rows))
+    pairs = sorted(pairs)
+    return np.array([p[0] for p in pairs]), np.array([p[1] for p in pairs])
+
+
+@pytest.mark.parametrize("K", [2, 8])
+def test_gradients_match_finite_differences(K):
+    rng = np.random.default_rng(3)
+    N = 12
+    rows, cols = _graph(N, 1)
+    width, layers = 6, 2
+    params = gnn.init_params(5, width=width, layers=layers, K=K)
+    for k in ("E", "F", "G", "f", "g"):
+        params[k] = 0.3 * rng.standard_normal(params[k].shape)
+    x = rng.standard_normal((N, 8))
+    e = rng.standard_normal((len(rows), 8))
+    nunk = N if K == 2 else 2 * N
+    if K == 2:
+        dinv = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    else:
+        dinv = rng.standard_normal((N, 2, 2)) + 1j * rng.standard_normal((N, 2, 2))
+    Y = rng.standard_normal((3, nunk)) + 1j * rng.standard_normal((3, nunk))
+    Z = rng.standard_normal((3, nunk)) + 1j * rng.standard_normal((3, nunk))
+    L, grads = gnn.loss_and_grads(params, x, e, rows, cols, dinv, Y, Z, K, layers)
+    h = 1e-6
+    for name in params:
+        flat = params[name].reshape(-1)
+        for idx in rng.choice(flat.size, size=min(4, flat.size), replace=False):
+            old = flat[idx]
+            flat[idx] = old + h
+            Lp, _ = gnn.loss_and_grads(params, x, e, rows, cols, dinv, Y, Z, K, layers)
+            flat[idx] = old - h
+            Lm, _ = gnn.loss_and_grads(params, x, e, rows, cols, dinv, Y, Z, K, layers)
+            flat[idx] = old
+            fd = (Lp - Lm) / (2 * h)
+            an = grads[name].reshape(-1)[idx]
+            assert an == pytest.approx(fd, rel=1e-5, abs=1e-9), (name, idx)
+
+
+@pytest.mark.parametrize("K", [2, 8])
+def test_apply_precond_dense(K):
+    rng = np.random.default_rng(7)
+    N = 9
+    rows, cols = _graph(N, 2)
+    nunk = N if K == 2 else 2 * N
+    o = rng.standard_normal((len(rows), K)) * (rows != cols)[:, None]
+    g = rng.standard_normal((N, K))
+    oc, gc = gnn.to_complex_blocks(o, g, K)
+    if K == 2:
+        dinv = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+        C = np.zeros((N, N), complex)
+        C[rows, cols] += oc
+        C[np.arange(N), np.arange(N)] += gc
+        M = np.diag(dinv) @ (np.eye(N) + C)
+    else:
+        dinv = rng.standard_normal((N, 2, 2)) + 1j * rng.standard_normal((N, 2, 2))
+        C = np.zeros((2 * N, 2 * N), complex)
+        Dm = np.zeros((2 * N, 2 * N), complex)
+        for k, (m, n) in enumerate(zip(rows, cols)):
+            for a in range(2):
+                for b in range(2):
+                    C[a * N + m, b * N + n] += oc[k, a, b]
+        for m in range(N):
+            for a in range(2):
+                for b in range(2):
+                    C[a * N + m, b * N + m] += gc[m, a, b]
+                    Dm[a * N + m, b * N + m] = dinv[m, a, b]
+        M = Dm @ (np.eye(2 * N) + C)
+    v = rng.standard_normal(nunk) + 1j * rng.standard_normal(nunk)
+    assert np.allclose(gnn.apply_precond(dinv, oc, gc, rows, cols, v, K), M @ v, rtol=1e-12, atol=1e-12)
