@@ -179,3 +179,96 @@ def init_params(seed, width=64, layers=4, nin=8, nedge=8, K=2):
         else:
             out[k] = np.zeros(shp)
     return out
+
+
+# ------------------------------------------------------------------ inputs of the network
+
+def _wavenumbers(freq, eps_out, eps_in, mu_in):
+    from .constants import C0
+    k_out = 2.0 * np.pi * freq * np.sqrt(eps_out) / C0
+    contrast = 1.0 if eps_in is None else np.sqrt(eps_in * mu_in / eps_out)
+    return k_out, contrast
+
+
+def features(prob, freq, eps_out=1.0, eps_in=None, mu_in=1.0):
+    """Node features x [N, 8] and edge features e [nnz, 8] on the near graph (caller order).
+
+    With h_bar the geometric mean of the grid spacings and k the exterior
+    wavenumber, every feature is dimensionless:
+
+      node m: l_m/h_bar, A+_m/h_bar^2, A-_m/h_bar^2, the offset of the basis
+              centre from the stencil's central node in cells (3), k h_bar,
+              the refractive contrast sqrt(eps_in mu_in / eps_out) (1 for a PEC body);
+      edge (m, n): (c_n - c_m)/h_bar (3), |c_n - c_m|/h_bar,
+              N^A_mn / sqrt|N^A_mm N^A_nn|, N^Phi_mn / sqrt|N^Phi_mm N^Phi_nn|,
+              h_bar N^K_mn / sqrt|N^A_mm N^A_nn|, k h_bar,
+    with N the precorrected static near matrices (Eq. LAIMx).  Returns
+    (x, e, rows, cols).
+    """
+    rwg, g = prob["rwg"], prob["grid"]
+    h = np.asarray(g["h"], dtype=np.float64)
+    hb = np.cbrt(h[0] * h[1] * h[2])
+    k, contrast = _wavenumbers(freq, eps_out, eps_in, mu_in)
+    N = prob["N"]
+    c = rwg["center"]
+    x = np.zeros((N, 8))
+    x[:, 0] = rwg["length"] / hb
+    x[:, 1] = rwg["area"][rwg["tp"]] / hb ** 2
+    x[:, 2] = rwg["area"][rwg["tm"]] / hb ** 2
+    x[:, 3:6] = (c - g["origin"]) / h - prob["anc"] - 0.5 * g["order"]
+    x[:, 6] = k * hb
+    x[:, 7] = contrast
+    near = prob["near"]
+    rows = near["rows"]
+    cols = prob["cols"]
+    dpos = rows == cols
+    dA = np.zeros(N)
+    dP = np.zeros(N)
+    dA[rows[dpos]] = np.abs(near["NA"][dpos])
+    dP[rows[dpos]] = np.abs(near["NP"][dpos])
+    tiny = 1e-300
+    sA = np.sqrt(np.maximum(dA[rows] * dA[cols], tiny))
+    sP = np.sqrt(np.maximum(dP[rows] * dP[cols], tiny))
+    e = np.zeros((len(rows), 8))
+    d = (c[cols] - c[rows]) / hb
+    e[:, 0:3] = d
+    e[:, 3] = np.sqrt((d * d).sum(1))
+    e[:, 4] = near["NA"] / sA
+    e[:, 5] = near["NP"] / sP
+    e[:, 6] = hb * near["NK"] / sA
+    e[:, 7] = k * hb
+    return x, e, rows, cols
+
+
+def diag_inverse(prob, freq, eps_out=1.0, eps_in=None, mu_in=1.0):
+    """D^{-1}: inverse of each basis' frequency-combined static self term (Sec. III-A-2).
+
+    EFIE: [N] complex, 1 / (j w mu (L^A_s - L^Phi_s / k^2)).  Two-region form:
+    [N, 2, 2], the inverse of [[sum_i j w mu_i <L_i>, 2 eta0 K_s], [-2 eta0 K_s,
+    eta0^2 sum_i j w eps_i <L_i>]] on the self pair (unknowns [J; M/eta0])."""
+    from .constants import MU0, EPS0, ETA0
+    near = prob["near"]
+    dpos = near["rows"] == prob["cols"]
+    la, lp, kk = near["LsA_diag"], near["LsP_diag"], near["LsK_diag"]
+    w = 2.0 * np.pi * freq
+    regs = [(MU0, EPS0 * eps_out)]
+    if eps_in is not None:
+        regs.append((MU0 * mu_in, EPS0 * eps_in))
+    order = near["rows"][dpos]
+    if eps_in is None:
+        mu, eps = regs[0]
+        k2 = w * w * mu * eps
+        d = 1j * w * mu * (la - lp / k2)
+        out = np.empty(prob["N"], dtype=np.complex128)
+        out[order] = 1.0 / d
+        return out
+    a = sum(1j * w * mu * (la - lp / (w * w * mu * eps)) for mu, eps in regs)
+    dd = sum(ETA0 ** 2 * 1j * w * eps * (la - lp / (w * w * mu * eps)) for mu, eps in regs)
+    b = 2.0 * ETA0 * kk
+    c = -2.0 * ETA0 * kk
+    blk = np.zeros((prob["N"], 2, 2), dtype=np.complex128)
+    blk[order, 0, 0] = a
+    blk[order, 0, 1] = b
+    blk[order, 1, 0] = c
+    blk[order, 1, 1] = dd
+    return np.linalg.inv(blk)

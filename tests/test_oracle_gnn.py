@@ -92,3 +92,60 @@ def test_apply_precond_dense(K):
         M = Dm @ (np.eye(2 * N) + C)
     v = rng.standard_normal(nunk) + 1j * rng.standard_normal(nunk)
     assert np.allclose(gnn.apply_precond(dinv, oc, gc, rows, cols, v, K), M @ v, rtol=1e-12, atol=1e-12)
+
+
+# ------------------------------------------------------------------ network inputs on a real mesh
+
+@pytest.fixture(scope="module")
+def sphere_prob():
+    from synth import icosphere
+    from oracle import operator as op
+    xyz, tri = icosphere(1)
+    return op.setup(xyz, tri, 2, (8, 8, 8)), xyz, tri
+
+
+def test_features_invariant_under_translation_and_scale(sphere_prob):
+    from oracle import operator as op
+    prob, xyz, tri = sphere_prob
+    f = 2.0e8
+    x0, e0, r0, c0 = gnn.features(prob, f)
+    g = prob["grid"]
+    s, t = 3.0, np.array([0.7, -1.1, 2.3])
+    prob2 = op.setup(xyz * s + t, tri, 2, (8, 8, 8), h=np.asarray(g["h"]) * s,
+                     origin=np.asarray(g["origin"]) * s + t)
+    x1, e1, r1, c1 = gnn.features(prob2, f / s)
+    assert np.array_equal(r0, r1) and np.array_equal(c0, c1)
+    assert np.allclose(x0, x1, atol=1e-9)
+    assert np.allclose(e0, e1, atol=1e-7)
+
+
+def test_edge_features_symmetry(sphere_prob):
+    prob, _, _ = sphere_prob
+    x, e, rows, cols = gnn.features(prob, 2.0e8)
+    pos = {(int(m), int(n)): i for i, (m, n) in enumerate(zip(rows, cols))}
+    tr = np.array([pos[(int(n), int(m))] for m, n in zip(rows, cols)])
+    assert np.allclose(e[tr, 0:3], -e[:, 0:3])
+    # distance and k h are exactly symmetric; the static near values only to quadrature accuracy
+    assert np.array_equal(e[tr, 3], e[:, 3]) and np.array_equal(e[tr, 7], e[:, 7])
+    assert np.allclose(e[tr, 4:6], e[:, 4:6], atol=1e-3)
+    assert np.allclose(e[tr, 6], e[:, 6], atol=2e-2)
+    diag = rows == cols
+    assert np.allclose(e[diag, 4:6], 1.0)
+    assert np.all(np.abs(x[:, 3:6]) <= 0.5 + 1e-12)
+
+
+def test_diag_inverse_matches_low_frequency_operator_diagonal(sphere_prob):
+    """At k h << 1 the AIMx self terms reduce to the static self terms (Eq. LAIMx)."""
+    from oracle import operator as op
+    prob, _, _ = sphere_prob
+    f = 3.0e6
+    d = 1.0 / gnn.diag_inverse(prob, f)
+    Z = op.dense_efie(prob, f)
+    assert np.allclose(d, np.diag(Z), rtol=2e-2)
+    N = prob["N"]
+    blk = np.linalg.inv(gnn.diag_inverse(prob, f, 1.0, 4.0))
+    Zp = op.dense_pmchwt(prob, f, 1.0, 4.0)
+    ref = np.stack([np.stack([np.diag(Zp[:N, :N]), np.diag(Zp[:N, N:])], -1),
+                    np.stack([np.diag(Zp[N:, :N]), np.diag(Zp[N:, N:])], -1)], -2)
+    scale = np.abs(ref).max(axis=(1, 2), keepdims=True)
+    assert np.allclose(blk / scale, ref / scale, atol=2e-2)
