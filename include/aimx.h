@@ -158,6 +158,10 @@ int aimx_matvec_host(aimx_ctx* ctx, double freq, int nrhs, const void* x, void* 
 #define AIMX_PRECOND_BLOCK 2  /* block Jacobi: bases grouped by 2x2x2 anchor cells (<= 32 per block); each block
                                  is the full AIMx matrix block, static near part plus the grid-generated
                                  frequency-dependent part (Sec. III-A-2), inverted in FP64, applied in FP32 */
+#define AIMX_PRECOND_LEARNED 3 /* M = D^{-1} (I + C): D as for AIMX_PRECOND_DIAG, C on the near graph predicted
+                                  by the network attached with aimx_gnn_attach (not in the paper; the learned
+                                  analogue of augmenting the diagonal of L_s with off-diagonal entries,
+                                  Sec. III-A-2).  Linear in the vector, so GMRES stays valid. */
 
 typedef struct {
     double tol;               /* target relative true residual |b - A x| / |b| (0 = 1e-6)            */
@@ -165,7 +169,7 @@ typedef struct {
     int32_t max_iter;         /* total inner iterations per right-hand side (0 = 1000)                */
     int32_t max_refine;       /* FP64 refinement cycles (0 = max_iter / restart + 10)                 */
     int32_t inner_precision;  /* AIMX_F32 (default) or AIMX_F64 products inside a cycle              */
-    int32_t precond;          /* AIMX_PRECOND_DIAG (default) or AIMX_PRECOND_NONE                     */
+    int32_t precond;          /* AIMX_PRECOND_DIAG (default), _NONE, _BLOCK or _LEARNED              */
     int32_t use_x0;           /* 1: x holds an initial guess on entry                                 */
 } aimx_solve_opts;
 
@@ -274,6 +278,83 @@ int aimx_matvec_noalloc(aimx_ctx* ctx, double freq, int nrhs, const void* x, voi
  * Synchronous. */
 int aimx_export_setup(const aimx_ctx* ctx, int32_t* anchors, double* weights,
                       int64_t* row_ptr, int32_t* cols, double* na, double* nphi, double* nk);
+
+/* ------------------------------------------------------------------------
+ * Learned near-field preconditioner (no counterpart in the paper, whose
+ * preconditioner is the diagonal of L_s, Sec. III-A-2).
+ *
+ * M = D^{-1} (I + C): D as for AIMX_PRECOND_DIAG, C on the near graph and its
+ * diagonal, predicted by a message-passing network of width 64 with `layers`
+ * layers.  Reversing an RWG function's orientation flips row and column n of
+ * the operator and C_mn -> s_m s_n C_mn; the network respects this exactly:
+ * its inputs are orientation invariant and each edge entry is a learned
+ * combination of 8 signed bases.  With h the geometric-mean grid spacing, k
+ * the exterior wavenumber and N the precorrected static near matrices
+ * (Eq. LAIMx):
+ *   bases b(m, n): eta^A = N^A_mn / sqrt|N^A_mm N^A_nn|, eta^Phi (same with N^Phi),
+ *           eta^K = h N^K_mn / sqrt|N^A_mm N^A_nn|, and the two-hop products
+ *           (XY)_mn = sum_j X_mj Y_jn / sqrt(deg_m deg_n) over the near pattern
+ *           for XY = AA, PP, AP, PA, KK (deg: off-diagonal near count, >= 1);
+ *   node features x_m: l/h, A+/h^2, A-/h^2, basis-centre offset from the
+ *           stencil centre in cells (3), k h, refractive contrast (1 for EFIE);
+ *   edge features e_mn: (c_n - c_m)/h (3), |c_n - c_m|/h, |eta^A|, |eta^Phi|,
+ *           eta^A eta^Phi, |eta^K|, |AA|, |PP|, |AP|, |PA|, |KK|, eta^A AA,
+ *           eta^Phi PP, k h.
+ * Network:
+ *   h0 = relu(A0 x + a0);  h_l = relu(D_l h_m + mean_{n != m} relu(B_l h_n + C_l e_mn + c_l) + d_l);
+ *   u_mn = relu(Ua h_m + Ub h_n + Uc e_mn + u);
+ *   C_mn[k] = sum_c (E u_mn + f)[8k + c] b_c(m, n) (n != m);  C_mm[k] = G h_m + g,
+ * K = 2 outputs (one complex entry, EFIE) or 8 (2x2 complex block, rows
+ * (E, H) x columns (J, M), real parts then imaginary parts; two-region form).
+ * Parameters are one FP32 vector in the order A0[64][8], a0[64], then per
+ * layer B[64][64], C[64][16], c[64], D[64][64], d[64], then Ua[64][64],
+ * Ub[64][64], Uc[64][16], u[64], E[8K][64], f[8K], G[K][64], g[K] (matrices
+ * row-major [out][in]).  The kernels use the parameters rounded to BF16 and
+ * accumulate in FP32.
+ *
+ * Training minimises the probe loss (1/P) sum_p |M y_p - z_p|^2 / |z_p|^2 over
+ * pairs y_p = A z_p supplied by the caller (e.g. from aimx_matvec), P = nprobe.
+ * ------------------------------------------------------------------------ */
+typedef struct aimx_gnn aimx_gnn;
+
+typedef struct {
+    double lr;      /* Adam step size (> 0)                              */
+    double beta1;   /* 0 = 0.9                                           */
+    double beta2;   /* 0 = 0.999                                         */
+    double eps;     /* 0 = 1e-8                                          */
+    double clip;    /* global gradient-norm clip (<= 0: none)            */
+} aimx_adam_opts;
+
+/* New network for `formulation` (AIMX_EFIE: K = 2, AIMX_PMCHWT: K = 8) with
+ * 1..8 layers; parameters start at zero.  The caller destroys it. */
+int aimx_gnn_create(int formulation, int layers, aimx_gnn** out);
+int aimx_gnn_destroy(aimx_gnn* net);
+int64_t aimx_gnn_num_params(const aimx_gnn* net);
+/* Host FP32 parameter vector (n = aimx_gnn_num_params) in / out.  Setting
+ * parameters resets the Adam state.  Synchronous. */
+int aimx_gnn_set_params(aimx_gnn* net, const float* host, int64_t n);
+int aimx_gnn_get_params(const aimx_gnn* net, float* host, int64_t n);
+/* Probe loss for the context at freq; Z, Y: device complex64 [nprobe][n_unknowns]
+ * (caller order), Y = A Z.  grad (host FP32 [num_params], may be NULL) receives
+ * the gradient.  Synchronous on `stream`.  AIMX_E_ARG if the network's K does
+ * not match the context's formulation. */
+int aimx_gnn_loss_grad(aimx_gnn* net, aimx_ctx* ctx, double freq, int nprobe, const void* Z, const void* Y,
+                       double* loss, float* grad, void* stream);
+/* One Adam step on the probe loss (loss before the step returned). */
+int aimx_gnn_train_step(aimx_gnn* net, aimx_ctx* ctx, double freq, int nprobe, const void* Z, const void* Y,
+                        const aimx_adam_opts* opt, double* loss, void* stream);
+/* Copy the network's current BF16 parameters into the context for
+ * AIMX_PRECOND_LEARNED (the network may be destroyed afterwards); NULL detaches.
+ * Solving with AIMX_PRECOND_LEARNED and nothing attached returns AIMX_E_STATE. */
+int aimx_gnn_attach(aimx_ctx* ctx, const aimx_gnn* net);
+/* Inspection (host outputs, any may be NULL): node features [N][8] by caller
+ * basis index; edge features [nnz][16], bases [nnz][8], rows[nnz], cols[nnz]
+ * (caller indices) in the context's internal near order; network outputs with
+ * `net`'s parameters at freq: o [nnz][K] in the same edge order (0 on the
+ * diagonal), g [N][K] by caller basis index. */
+int aimx_gnn_features(aimx_ctx* ctx, double freq, float* node, float* edge, float* basis, int32_t* rows,
+                      int32_t* cols);
+int aimx_gnn_outputs(aimx_ctx* ctx, const aimx_gnn* net, double freq, float* o, float* g);
 
 #ifdef __cplusplus
 }

@@ -82,11 +82,33 @@ _SIGS = [
                                   ctypes.c_void_p]),
     ("aimx_precond_apply", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("aimx_gnn_create", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
+    ("aimx_gnn_destroy", ctypes.c_int, [ctypes.c_void_p]),
+    ("aimx_gnn_num_params", ctypes.c_int64, [ctypes.c_void_p]),
+    ("aimx_gnn_set_params", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
+    ("aimx_gnn_get_params", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
+    ("aimx_gnn_loss_grad", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_int,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.c_void_p, ctypes.c_void_p]),
+    ("aimx_gnn_train_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_int,
+                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
+    ("aimx_gnn_attach", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("aimx_gnn_features", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("aimx_gnn_outputs", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
+                                        ctypes.c_void_p]),
 ]
 
 PRECOND_DIAG = 0
 PRECOND_NONE = 1
 PRECOND_BLOCK = 2
+PRECOND_LEARNED = 3
+
+
+class _AdamOpts(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
+                ("eps", ctypes.c_double), ("clip", ctypes.c_double)]
 
 
 class _SolveOpts(ctypes.Structure):
@@ -332,3 +354,134 @@ class Context:
         self._check(self._lib.aimx_export_setup(self._ctx, _ptr(anc), _ptr(w), _ptr(rp), _ptr(cols), _ptr(na),
                                                 _ptr(nphi), _ptr(nk)))
         return dict(anchors=anc, weights=w, row_ptr=rp, cols=cols, NA=na, NP=nphi, NK=nk)
+
+    # ---------------------------------------------------------------- learned preconditioner
+    def gnn_attach(self, net):
+        """Copy ``net``'s parameters into this context for PRECOND_LEARNED (None detaches)."""
+        self._check(self._lib.aimx_gnn_attach(self._ctx, net._net if net is not None else None))
+
+    def gnn_features(self, freq):
+        """(node [N,8] by basis, edge [nnz,16], basis [nnz,8], rows, cols) of the network inputs at freq."""
+        nnz = self.info["near_nnz"]
+        node = np.zeros((self.N, 8), dtype=np.float32)
+        edge = np.zeros((nnz, 16), dtype=np.float32)
+        basis = np.zeros((nnz, 8), dtype=np.float32)
+        rows = np.zeros(nnz, dtype=np.int32)
+        cols = np.zeros(nnz, dtype=np.int32)
+        self._check(self._lib.aimx_gnn_features(self._ctx, float(freq), _ptr(node), _ptr(edge), _ptr(basis),
+                                                _ptr(rows), _ptr(cols)))
+        return node, edge, basis, rows, cols
+
+    def gnn_outputs(self, net, freq):
+        """Network outputs (o [nnz,K] in gnn_features' edge order, g [N,K]) with ``net``'s parameters."""
+        K = net.K
+        o = np.zeros((self.info["near_nnz"], K), dtype=np.float32)
+        g = np.zeros((self.N, K), dtype=np.float32)
+        self._check(self._lib.aimx_gnn_outputs(self._ctx, net._net, float(freq), _ptr(o), _ptr(g)))
+        return o, g
+
+
+class Gnn:
+    """The learned near-field preconditioner network (see include/aimx.h)."""
+
+    def __init__(self, formulation=EFIE, layers=4):
+        self._lib = load()
+        h = ctypes.c_void_p()
+        rc = self._lib.aimx_gnn_create(int(formulation), int(layers), ctypes.byref(h))
+        if rc != 0:
+            raise AimxError(rc, "aimx_gnn_create")
+        self._net = h
+        self.K = 2 if formulation == EFIE else 8
+        self.layers = layers
+        self.n_params = int(self._lib.aimx_gnn_num_params(h))
+
+    def close(self):
+        if getattr(self, "_net", None):
+            self._lib.aimx_gnn_destroy(self._net)
+            self._net = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, ctx=None):
+        if rc != 0:
+            msg = self._lib.aimx_last_error(ctx._ctx).decode() if ctx is not None else ""
+            raise AimxError(rc, msg)
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        self._check(self._lib.aimx_gnn_set_params(self._net, _ptr(p), p.size))
+
+    def params(self):
+        p = np.zeros(self.n_params, dtype=np.float32)
+        self._check(self._lib.aimx_gnn_get_params(self._net, _ptr(p), p.size))
+        return p
+
+    def loss_grad(self, ctx, freq, Z, Y, want_grad=True, stream=None):
+        """Probe loss (and gradient) for device complex64 tensors Z, Y [P, n_unknowns]."""
+        loss = ctypes.c_double()
+        g = np.zeros(self.n_params, dtype=np.float32) if want_grad else None
+        self._check(self._lib.aimx_gnn_loss_grad(self._net, ctx._ctx, float(freq), Z.shape[0],
+                                                 ctypes.c_void_p(Z.data_ptr()), ctypes.c_void_p(Y.data_ptr()),
+                                                 ctypes.byref(loss), _ptr(g), _stream_handle(stream)), ctx)
+        return loss.value, g
+
+    def train_step(self, ctx, freq, Z, Y, lr=1e-3, clip=0.0, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+        loss = ctypes.c_double()
+        o = _AdamOpts(float(lr), float(beta1), float(beta2), float(eps), float(clip))
+        self._check(self._lib.aimx_gnn_train_step(self._net, ctx._ctx, float(freq), Z.shape[0],
+                                                  ctypes.c_void_p(Z.data_ptr()), ctypes.c_void_p(Y.data_ptr()),
+                                                  ctypes.byref(o), ctypes.byref(loss), _stream_handle(stream)), ctx)
+        return loss.value
+
+    def init_params(self, seed=0):
+        """He-initialised hidden layers, zero E, f, G, g (C = 0: the diagonal preconditioner)."""
+        rng = np.random.default_rng(seed)
+        p = np.zeros(self.n_params, dtype=np.float32)
+        off = 0
+
+        def take(rows, cols, he):
+            nonlocal off
+            n = rows * cols
+            if he:
+                p[off:off + n] = (rng.standard_normal(n) * np.sqrt(2.0 / cols)).astype(np.float32)
+            off += n
+
+        take(64, 8, True)            # A0
+        take(64, 1, False)           # a0
+        for _ in range(self.layers):
+            take(64, 64, True)       # B
+            take(64, 16, True)       # C
+            take(64, 1, False)       # c
+            take(64, 64, True)       # D
+            take(64, 1, False)       # d
+        take(64, 64, True)           # Ua
+        take(64, 64, True)           # Ub
+        take(64, 16, True)           # Uc
+        take(64, 1, False)           # u
+        assert off + self.K * (8 * 64 + 8 + 64 + 1) == self.n_params
+        self.set_params(p)
+        return p
+
+    def fit(self, samples, steps, nprobe=8, lr=1e-3, clip=1.0, seed=0, log=None):
+        """Adam on the probe loss, cycling over ``samples`` = [(Context, freq), ...].
+
+        Each step draws nprobe seeded complex Gaussian probes z on the device,
+        forms y = A z with the context's FP32 product, and takes one step."""
+        import torch
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(int(seed))
+        losses = []
+        for it in range(int(steps)):
+            ctx, freq = samples[it % len(samples)]
+            n = ctx.nunk
+            Z = torch.randn(nprobe, n, 2, device="cuda", generator=gen, dtype=torch.float32)
+            Z = torch.view_as_complex(Z).contiguous()
+            Y = ctx.matvec(freq, Z)
+            losses.append(self.train_step(ctx, freq, Z, Y, lr=lr, clip=clip))
+            if log is not None:
+                log(it, losses[-1])
+        return losses

@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of libaimx.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -106,6 +107,46 @@ struct PrecondBlocks {
     double freq = -1.0;
 };
 
+// parameter offsets of the learned-preconditioner network (gnn.cu)
+struct GnnLayout {
+    int K = 2, L = 4;
+    int64_t A0 = 0, a0 = 0, B[8] = {}, C[8] = {}, c[8] = {}, D[8] = {}, d[8] = {};
+    int64_t Ua = 0, Ub = 0, Uc = 0, u = 0, E = 0, f = 0, G = 0, g = 0, total = 0;
+};
+
+// per-context state of the learned preconditioner (gnn.cu)
+struct GnnGraph {
+    std::vector<void*> own;        // allocations below (freed together)
+    int* d_rows = nullptr;         // [nnz] internal row of each near entry
+    int* d_trans = nullptr;        // [nnz] position of (n, m) for entry (m, n)
+    int* d_colc = nullptr;         // [nnz] caller index of the column
+    int* d_dpos = nullptr;         // [N] position of the diagonal entry in each row
+    float* d_deginv = nullptr;     // [N] 1 / off-diagonal degree
+    float* d_x = nullptr;          // [N][8] node features
+    float* d_e = nullptr;          // [nnz][16] orientation-invariant edge features
+    float* d_basis = nullptr;      // [nnz][8] signed bases (static)
+    double* d_eta = nullptr;       // [nnz][3] normalised static near entries (static)
+    double* d_center = nullptr;    // [N][3] basis centres
+    double2* d_minv = nullptr;     // [N] or [N][2][2] D^{-1}, caller order
+    double* d_lossn = nullptr;     // [N] per-row loss terms
+    double feat_freq = -1.0, minv_freq = -1.0;
+    int K = 0, L = 0;              // shape the activation buffers were sized for
+    float* d_H = nullptr;          // [L+1][N][64]
+    float* d_P = nullptr;          // [L][N][64]
+    float* d_S = nullptr;          // [N][64]
+    float* d_Pa = nullptr;         // [N][64] Ua h_L
+    float* d_Pb = nullptr;         // [N][64] Ub h_L
+    float* d_o = nullptr;          // [nnz][K]
+    float* d_g = nullptr;          // [N][K]
+    const __nv_bfloat16* out_w = nullptr;  // weights that produced d_o / d_g
+    double out_freq = -1.0;
+    __nv_bfloat16* d_watt = nullptr;       // attached weights (aimx_gnn_attach)
+    int64_t att_np = 0;
+    int att_K = 0, att_L = 0;
+    void* d_vT = nullptr;          // transposed right-hand sides for the apply
+    size_t vT_bytes = 0;
+};
+
 }  // namespace aimx
 
 struct aimx_ctx {
@@ -175,6 +216,7 @@ struct aimx_ctx {
 
     aimx::Profiler prof;
     aimx::PrecondBlocks pc;
+    aimx::GnnGraph gnn;
 
     int64_t device_bytes = 0;
     std::string last_error;
@@ -238,6 +280,18 @@ void precond_block_prepare(aimx_ctx* ctx, double freq, cudaStream_t s);
 template <class T>
 void precond_block_apply(aimx_ctx* ctx, const double2* v, int64_t vstride, typename Cplx<T>::type* z, int nrhs,
                          cudaStream_t s);
+
+// gnn.cu (learned preconditioner)
+GnnLayout gnn_layout(int K, int L);
+void gnn_features(aimx_ctx* ctx, double freq, cudaStream_t s);
+void learned_prepare(aimx_ctx* ctx, double freq, cudaStream_t s);
+template <class T>
+void learned_apply(aimx_ctx* ctx, const double2* v, int64_t vstride, typename Cplx<T>::type* z, int nrhs,
+                   cudaStream_t s);
+void gnn_free(aimx_ctx* ctx);
+
+// solve.cu: inverse of the frequency-combined static self blocks (caller order)
+void build_diag_inverse(aimx_ctx* ctx, double freq, double2* minv, cudaStream_t s);
 
 // matvec.cu
 template <class T>

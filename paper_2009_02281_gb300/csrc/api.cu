@@ -46,6 +46,7 @@ static void free_all(aimx_ctx* c) {
         cudaEventDestroy(r.b);
     }
     for (auto e : c->prof.pool) cudaEventDestroy(e);
+    gnn_free(c);
     c->prof.recs.clear();
     c->prof.pool.clear();
 }

@@ -196,6 +196,13 @@ __global__ void k_build_precond(const double* __restrict__ diag, const int* __re
 
 static inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
+void build_diag_inverse(aimx_ctx* ctx, double freq, double2* minv, cudaStream_t s) {
+    Coefs cf = near_coefs(ctx, freq);
+    k_build_precond<<<nblk(ctx->N), 256, 0, s>>>(ctx->d_diag, ctx->d_perm, minv, ctx->N, ctx->form, cf.near[0],
+                                                 cf.near[1], cf.near[2], cf.near[3], cf.near[4], cf.near[5]);
+    AIMX_CUDA_TRY(cudaGetLastError());
+}
+
 struct SolveWork {
     double2* V = nullptr;      // [nrhs][m+1][nunk]
     double2* w = nullptr;      // [nrhs][nunk]
@@ -320,8 +327,10 @@ extern "C" int aimx_solve(aimx_ctx* ctx, double freq, int nrhs, const void* bdev
         double2* x = (double2*)xdev;
         Coefs cf = near_coefs(ctx, freq);
         const bool block = o.precond == AIMX_PRECOND_BLOCK;
+        const bool learned = o.precond == AIMX_PRECOND_LEARNED;
         if (block) precond_block_prepare(ctx, freq, s);
-        if (o.precond == AIMX_PRECOND_NONE || block) {
+        if (learned) learned_prepare(ctx, freq, s);
+        if (o.precond == AIMX_PRECOND_NONE || block || learned) {
             std::vector<double2> one(4 * (size_t)N, make_double2(0, 0));
             for (int i = 0; i < N; ++i) {
                 if (ctx->form == AIMX_EFIE) {
@@ -387,6 +396,8 @@ extern "C" int aimx_solve(aimx_ctx* ctx, double freq, int nrhs, const void* bdev
                 if (o.inner_precision == AIMX_F32) {
                     if (block)
                         precond_block_apply<float>(ctx, vj, vstride, (float2*)W.z, nrhs, s);
+                    else if (learned)
+                        learned_apply<float>(ctx, vj, vstride, (float2*)W.z, nrhs, s);
                     else
                         k_precond<float><<<nblk((int64_t)N * nrhs), 256, 0, s>>>(vj, (float2*)W.z, W.minv, N, nunk,
                                                                                    nrhs, ctx->form, vstride);
@@ -395,6 +406,8 @@ extern "C" int aimx_solve(aimx_ctx* ctx, double freq, int nrhs, const void* bdev
                 } else {
                     if (block)
                         precond_block_apply<double>(ctx, vj, vstride, (double2*)W.z, nrhs, s);
+                    else if (learned)
+                        learned_apply<double>(ctx, vj, vstride, (double2*)W.z, nrhs, s);
                     else
                         k_precond<double><<<nblk((int64_t)N * nrhs), 256, 0, s>>>(vj, (double2*)W.z, W.minv, N,
                                                                                     nunk, nrhs, ctx->form, vstride);
@@ -444,8 +457,11 @@ extern "C" int aimx_solve(aimx_ctx* ctx, double freq, int nrhs, const void* bdev
             }
             AIMX_CUDA_TRY(cudaMemcpyAsync(W.h, coef.data(), sizeof(double2) * coef.size(), cudaMemcpyHostToDevice, s));
             k_combine<<<nblk(nv), 256, 0, s>>>(W.V, W.h, W.d, nunk, vstride, m + 1, jlast, nrhs);
-            if (block) {
-                precond_block_apply<double>(ctx, W.d, nunk, (double2*)W.z, nrhs, s);
+            if (block || learned) {
+                if (block)
+                    precond_block_apply<double>(ctx, W.d, nunk, (double2*)W.z, nrhs, s);
+                else
+                    learned_apply<double>(ctx, W.d, nunk, (double2*)W.z, nrhs, s);
                 k_add_masked<<<nblk(nv), 256, 0, s>>>(x, (const double2*)W.z, W.active, nunk, nrhs);
             } else {
                 k_precond_inplace<<<nblk((int64_t)N * nrhs), 256, 0, s>>>(W.d, W.minv, N, nunk, nrhs, ctx->form);
@@ -729,7 +745,7 @@ extern "C" int aimx_sweep(aimx_ctx* ctx, int nf, const double* freqs, int nwave,
 extern "C" int aimx_precond_apply(aimx_ctx* ctx, double freq, int precond, int nrhs, const void* v, void* z,
                                   void* stream) {
     if (!ctx) return AIMX_E_ARG;
-    if (nrhs <= 0 || !v || !z || !(freq > 0) || precond < 0 || precond > 2) {
+    if (nrhs <= 0 || !v || !z || !(freq > 0) || precond < 0 || precond > AIMX_PRECOND_LEARNED) {
         ctx->last_error = "aimx_precond_apply: bad argument";
         return AIMX_E_ARG;
     }
@@ -739,6 +755,9 @@ extern "C" int aimx_precond_apply(aimx_ctx* ctx, double freq, int precond, int n
         if (precond == AIMX_PRECOND_BLOCK) {
             precond_block_prepare(ctx, freq, s);
             precond_block_apply<double>(ctx, (const double2*)v, nunk, (double2*)z, nrhs, s);
+        } else if (precond == AIMX_PRECOND_LEARNED) {
+            learned_prepare(ctx, freq, s);
+            learned_apply<double>(ctx, (const double2*)v, nunk, (double2*)z, nrhs, s);
         } else {
             double2* minv = (double2*)dev_alloc(ctx, sizeof(double2) * 4 * (size_t)N);
             if (precond == AIMX_PRECOND_NONE) {
