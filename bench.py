@@ -151,6 +151,50 @@ def _algorithmic_bytes(info, wl, B):
     return step, stages
 
 
+def measure_solves(ctx, wl, args):
+    """Batched GMRES solves of the workload's plane-wave right-hand sides (seeded
+    directions) to a true FP64 relative residual of args.solve_tol, with the
+    diagonal preconditioner and with the learned one trained on this context and
+    frequency (training reported as a one-time cost, like setup)."""
+    import torch
+    from synth import planewave_batch
+    from paper_2009_02281_gb300 import Gnn, PRECOND_DIAG, PRECOND_LEARNED
+    freq, B = wl["freq"], wl["nrhs"]
+    dirs, pols = planewave_batch(B, seed=0)
+    b = ctx.rhs_planewave(freq, dirs, pols)
+
+    def solve(pc):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        _, st, rc = ctx.solve(freq, b, tol=args.solve_tol, restart=100, max_iter=4000, precond=pc)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        it = [s["iterations"] for s in st]
+        ok = sum(1 for s in st if s["rel_residual"] <= args.solve_tol)
+        return {"solves_per_s": round(ok / dt, 3), "wall_s": round(dt, 3), "converged": ok, "rhs": B,
+                "iterations_mean": round(float(np.mean(it)), 1), "iterations_max": int(max(it)),
+                "max_rel_residual": max(s["rel_residual"] for s in st)}
+
+    out = {"tol": args.solve_tol, "restart": 100, "inner": "f32 products, f64 Arnoldi and refinement",
+           "diag": solve(PRECOND_DIAG)}
+    if args.gnn_steps > 0:
+        net = Gnn(ctx.info["formulation"])
+        net.init_params(0)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        losses = net.fit([(ctx, freq)], steps=args.gnn_steps, nprobe=8, lr=2e-3, clip=1.0, seed=1)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        ctx.gnn_attach(net)
+        net.close()
+        out["learned"] = solve(PRECOND_LEARNED)
+        out["learned_training"] = {"steps": args.gnn_steps, "probes_per_step": 8, "wall_s": round(dt, 2),
+                                   "ms_per_step": round(1e3 * dt / args.gnn_steps, 2),
+                                   "loss_first": round(losses[0], 4),
+                                   "loss_last": round(float(np.mean(losses[-20:])), 4)}
+    return out
+
+
 def run_ours(args):
     import torch
     ws, rank = _dist()
@@ -260,6 +304,8 @@ def run_ours(args):
         "setup_s": round(setup_s, 3),
         "first_call_ms_incl_kernel_generation": round(first_ms, 3),
     }
+    if not args.no_solves:
+        out["solves"] = measure_solves(ctx, wl, args)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl, args.cpu_rows)
     if rank == 0:
@@ -342,6 +388,9 @@ def main():
     ap.add_argument("--nrhs", type=int, default=None)
     ap.add_argument("--cpu-rows", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-solves", action="store_true", help="skip the batched solve measurement")
+    ap.add_argument("--solve-tol", type=float, default=1e-4)
+    ap.add_argument("--gnn-steps", type=int, default=600, help="training steps of the learned preconditioner")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

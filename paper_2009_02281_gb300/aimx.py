@@ -466,22 +466,26 @@ class Gnn:
         self.set_params(p)
         return p
 
-    def fit(self, samples, steps, nprobe=8, lr=1e-3, clip=1.0, seed=0, log=None):
+    def fit(self, samples, steps, nprobe=8, lr=1e-3, clip=1.0, seed=0, log=None, cosine=True):
         """Adam on the probe loss, cycling over ``samples`` = [(Context, freq), ...].
 
         Each step draws nprobe seeded complex Gaussian probes z on the device,
-        forms y = A z with the context's FP32 product, and takes one step."""
+        forms y = A z with the context's FP32 product, and takes one step; with
+        ``cosine`` the step size decays as lr (0.05 + 0.95 (1 + cos(pi t / steps)) / 2)."""
+        import math
         import torch
         gen = torch.Generator(device="cuda")
         gen.manual_seed(int(seed))
         losses = []
-        for it in range(int(steps)):
+        steps = int(steps)
+        for it in range(steps):
             ctx, freq = samples[it % len(samples)]
             n = ctx.nunk
             Z = torch.randn(nprobe, n, 2, device="cuda", generator=gen, dtype=torch.float32)
             Z = torch.view_as_complex(Z).contiguous()
             Y = ctx.matvec(freq, Z)
-            losses.append(self.train_step(ctx, freq, Z, Y, lr=lr, clip=clip))
+            lr_t = lr * (0.05 + 0.475 * (1.0 + math.cos(math.pi * it / steps))) if cosine else lr
+            losses.append(self.train_step(ctx, freq, Z, Y, lr=lr_t, clip=clip))
             if log is not None:
                 log(it, losses[-1])
         return losses
