@@ -215,6 +215,7 @@ def run_ours(args):
                   eps_out=wl["eps_out"], eps_in=wl["eps_in"] or 1.0, near_radius=wl["radius"])
     torch.cuda.synchronize()
     setup_s = time.time() - t0
+    ctx.set_path(args.path)
     info = ctx.info
     x_np = random_complex((B, ctx.nunk), seed=100 + rank).astype(np.complex64)
     x = torch.tensor(x_np, device="cuda")
@@ -389,6 +390,7 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solves", action="store_true", help="skip the batched solve measurement")
+    ap.add_argument("--path", type=int, default=0, choices=[0, 1], help="FP32 product path (aimx_set_path)")
     ap.add_argument("--solve-tol", type=float, default=1e-4)
     ap.add_argument("--gnn-steps", type=int, default=600, help="training steps of the learned preconditioner")
     args = ap.parse_args()

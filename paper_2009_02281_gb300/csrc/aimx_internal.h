@@ -195,6 +195,7 @@ struct aimx_ctx {
 
     aimx::PrecData<float> f32;
     aimx::PrecData<double> f64;
+    float* d_wsoa = nullptr;       // FP32 weights, field-major [4][U][N] (internal order)
 
     // kernel-generation scratch (FP64 full grids)
     double* d_kgen = nullptr;

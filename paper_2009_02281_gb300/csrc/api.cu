@@ -38,7 +38,7 @@ static void free_all(aimx_ctx* c) {
                     c->f32.nk,    c->f32.spec,  c->f32.grid,   c->f64.w,    c->f64.na,   c->f64.np,
                     c->f64.nk,    c->f64.spec,  c->f64.grid,   c->d_kgen,   c->d_stage,
                     c->d_xT,      c->d_G,       c->d_S,        c->d_part,   c->d_plane,  c->d_q5,
-                    c->pc.d_ptr,  c->pc.d_idx,  c->pc.d_work,  c->pc.d_inv};
+                    c->pc.d_ptr,  c->pc.d_idx,  c->pc.d_work,  c->pc.d_inv, c->d_wsoa};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& r : c->prof.recs) {

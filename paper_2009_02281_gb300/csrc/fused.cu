@@ -527,6 +527,7 @@ __global__ void __launch_bounds__(2 * N) k_xy_inv_reg(const float2* __restrict__
     constexpr int PITCH = N + 1;
     float2* acc = sm + 2 * N * PITCH;
     const int z = blockIdx.x, grp = blockIdx.y, b = blockIdx.z;
+    int2* meta = reinterpret_cast<int2*>(acc + (plane_hi[z] - plane_lo[z]));
     const int px = threadIdx.x / N, r = threadIdx.x - px * N;
     float2* pl = sm + px * N * PITCH;
     float2* O = sm;                       // parity-0 plane doubles as the output plane
@@ -534,7 +535,14 @@ __global__ void __launch_bounds__(2 * N) k_xy_inv_reg(const float2* __restrict__
     const int lo = plane_lo[z], hi = plane_hi[z];
     const int nb = hi - lo;
     const int U = P * P * P;
-    for (int k = threadIdx.x; k < nb; k += blockDim.x) acc[k] = make_float2(0.f, 0.f);
+    // per basis touching this plane: stencil corner (sx, sy) in the plane and the offset of its
+    // weights for this plane's stencil slot, computed once and reused for the four fields
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+        const int i = lo + k;
+        const int sx = anc[3 * i], sy = anc[3 * i + 1], slot = z - anc[3 * i + 2];
+        acc[k] = make_float2(0.f, 0.f);
+        meta[k] = make_int2(sy * PITCH + sx, slot * P * P * Ntot + i);
+    }
     float2 v[N];
 #pragma unroll 1
     for (int fl = 0; fl < 4; ++fl) {
@@ -573,15 +581,41 @@ __global__ void __launch_bounds__(2 * N) k_xy_inv_reg(const float2* __restrict__
             for (int x = 0; x < N; ++x) O[r * PITCH + x] = O[r * PITCH + x] + v[x];
         }
         __syncthreads();
-        for (int k = threadIdx.x; k < nb; k += blockDim.x) {
-            const int i = lo + k;
-            const int sx = anc[3 * i], sy = anc[3 * i + 1], sz = anc[3 * i + 2];
-            const int slot = z - sz;
-            const float* wi = w + ((int64_t)i * U + slot * P * P) * 4 + fl;
-            float2 s = make_float2(0.f, 0.f);
-            for (int uy = 0; uy < P; ++uy)
-                for (int ux = 0; ux < P; ++ux) rfma(s, __ldg(wi + (uy * P + ux) * 4), O[(sy + uy) * PITCH + sx + ux]);
-            acc[k] = acc[k] + s;
+        // two bases per iteration so that both weight gathers are in flight together
+        for (int k = threadIdx.x; k < nb; k += 2 * blockDim.x) {
+            const int k2 = k + blockDim.x;
+            const bool two = k2 < nb;
+            const int2 m0 = meta[k], m1 = two ? meta[k2] : m0;
+            // field-major weights ws[fl][u][i]: neighbouring bases of one slot are adjacent
+            const float* w0 = w + (int64_t)fl * U * Ntot + m0.y;
+            const float* w1 = w + (int64_t)fl * U * Ntot + m1.y;
+            float a0[9], a1[9];
+            if (P == 3) {
+#pragma unroll
+                for (int u = 0; u < 9; ++u) {
+                    a0[u] = __ldg(w0 + (int64_t)u * Ntot);
+                    a1[u] = __ldg(w1 + (int64_t)u * Ntot);
+                }
+                float2 s0 = make_float2(0.f, 0.f), s1 = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int uy = 0; uy < 3; ++uy)
+#pragma unroll
+                    for (int ux = 0; ux < 3; ++ux) {
+                        rfma(s0, a0[uy * 3 + ux], O[m0.x + uy * PITCH + ux]);
+                        rfma(s1, a1[uy * 3 + ux], O[m1.x + uy * PITCH + ux]);
+                    }
+                acc[k] = acc[k] + s0;
+                if (two) acc[k2] = acc[k2] + s1;
+            } else {
+                float2 s0 = make_float2(0.f, 0.f), s1 = make_float2(0.f, 0.f);
+                for (int uy = 0; uy < P; ++uy)
+                    for (int ux = 0; ux < P; ++ux) {
+                        rfma(s0, __ldg(w0 + (int64_t)(uy * P + ux) * Ntot), O[m0.x + uy * PITCH + ux]);
+                        rfma(s1, __ldg(w1 + (int64_t)(uy * P + ux) * Ntot), O[m1.x + uy * PITCH + ux]);
+                    }
+                acc[k] = acc[k] + s0;
+                if (two) acc[k2] = acc[k2] + s1;
+            }
         }
         __syncthreads();
     }
@@ -600,7 +634,7 @@ static bool reg_path(const aimx_ctx* ctx) {
     if (N != 8 && N != 16 && N != 32 && N != 64) return false;
     const int Nz = ctx->n[2];
     if (Nz != 8 && Nz != 16 && Nz != 32 && Nz != 64) return false;
-    return (size_t)(2 * N * (N + 1) + ctx->max_plane_bases) * sizeof(float2) <= 200 * 1024;
+    return (size_t)(2 * N * (N + 1) + 2 * ctx->max_plane_bases) * sizeof(float2) <= 200 * 1024;
 }
 
 static void ensure_const_twiddles() {
@@ -642,9 +676,9 @@ static void launch_xy_fwd_reg(const aimx_ctx* ctx, const float2* G, float2* S, i
 template <int N>
 static void launch_xy_inv_reg(const aimx_ctx* ctx, const float2* S, const int* plo, const int* phi, float2* part,
                               int B, cudaStream_t s) {
-    size_t sm = (2 * (size_t)N * (N + 1) + ctx->max_plane_bases) * sizeof(float2);
+    size_t sm = (2 * (size_t)N * (N + 1) + 2 * (size_t)ctx->max_plane_bases) * sizeof(float2);
     set_smem(k_xy_inv_reg<N>, sm);
-    k_xy_inv_reg<N><<<dim3(ctx->n[2], ctx->F / 4, B), 2 * N, sm, s>>>(S, ctx->f32.w, ctx->d_anc, plo, phi, part,
+    k_xy_inv_reg<N><<<dim3(ctx->n[2], ctx->F / 4, B), 2 * N, sm, s>>>(S, ctx->d_wsoa, ctx->d_anc, plo, phi, part,
                                                                       ctx->F, ctx->n[2], ctx->N, ctx->P);
 }
 

@@ -283,6 +283,16 @@ __global__ void k_precorrect(const double* w, const int* anc, const int* row_of,
     NK32[e] = (float)nk;
 }
 
+// field-major FP32 copy of the weights, ws[f][u][i] = w[i][u][f] (coalesced per-plane interpolation)
+__global__ void k_weights_soa(const double* __restrict__ w, float* __restrict__ ws, int N, int U) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)N * U * 4) return;
+    const int i = (int)(t % N);
+    const int64_t r = t / N;
+    const int u = (int)(r % U), f = (int)(r / U);
+    ws[t] = (float)w[((int64_t)i * U + u) * 4 + f];
+}
+
 __global__ void k_to_float(const double* a, float* b, size_t n) {
     size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (t < n) b[t] = (float)a[t];
@@ -588,6 +598,8 @@ void setup_context(aimx_ctx* ctx, const aimx_mesh* mesh, const aimx_material* ma
         AIMX_CUDA_TRY(cudaGetLastError());
         size_t n4 = (size_t)N * U * 4;
         k_to_float<<<(unsigned)((n4 + 255) / 256), 256>>>(ctx->f64.w, ctx->f32.w, n4);
+        ctx->d_wsoa = (float*)dev_alloc(ctx, sizeof(float) * n4);
+        k_weights_soa<<<(unsigned)((n4 + 255) / 256), 256>>>(ctx->f64.w, ctx->d_wsoa, N, U);
         AIMX_CUDA_TRY(cudaGetLastError());
     }
 
