@@ -8,7 +8,7 @@
 // only the N_a outputs on the grid are formed.  Pass structure:
 //
 //   k_transpose_x : x[b][n] -> xT[i][b] (internal basis order, RHS fastest)
-//   k_gather      : projection P, node-major gather (no atomics) -> G[b][f][z][y][x]
+//   k_gather_tile : projection P, node-major gather (no atomics) -> G[b][f][z][y][x]
 //   k_xy_fwd      : per z plane: 4 parity classes (px, py), 2-D N-point FFT
 //                   -> S[b][f][z][q][ky'][kx']
 //   k_zpass       : per (kx', ky', q) column tile: zero-padded M_z FFT along z,
@@ -72,38 +72,58 @@ __global__ void k_transpose_x(const float2* __restrict__ x, const int* __restric
 }
 
 // ------------------------------------------------------------------ K1
-__global__ void k_gather(const float4* __restrict__ w, const int* __restrict__ node_ptr,
-                         const int* __restrict__ node_w, const float2* __restrict__ xT, float2* G,
-                         int B, int F, int N, int U, int64_t NG) {
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= NG * B) return;
-    int64_t g = t % NG;
-    int b = (int)(t / NG);
-    float2 acc[8];
+// Projection gather, tiled: a block covers 16 consecutive grid nodes x 32
+// right-hand sides; lane = right-hand side, so the x reads ([nunk][B] layout)
+// are contiguous and each node's (basis, weight) list is read once per warp as
+// broadcasts; a shared-memory transpose writes the projected grid node-fastest.
+template <int F>
+__global__ void __launch_bounds__(256) k_gather_tile(const float4* __restrict__ w, const int* __restrict__ node_ptr,
+                                                     const int* __restrict__ node_w, const float2* __restrict__ xT,
+                                                     float2* G, int B, int N, int U, int64_t NG) {
+    constexpr int TG = 16;
+    __shared__ float2 tile[F][32][TG + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t g0 = (int64_t)blockIdx.x * TG;
+    const int b0 = blockIdx.y * 32;
+    const int b = b0 + lane;
+    const bool bok = b < B;
+    for (int gl = warp; gl < TG; gl += 8) {
+        const int64_t g = g0 + gl;
+        float2 acc[F];
 #pragma unroll
-    for (int f = 0; f < 8; ++f) acc[f] = make_float2(0.f, 0.f);
-    const int e1 = node_ptr[g + 1];
-    for (int e = node_ptr[g]; e < e1; ++e) {
-        int wi = node_w[e];
-        float4 wv = __ldg(w + wi);
-        int i = wi / U;
-        float2 xj = __ldg(xT + (int64_t)i * B + b);
-        rfma(acc[0], wv.x, xj);
-        rfma(acc[1], wv.y, xj);
-        rfma(acc[2], wv.z, xj);
-        rfma(acc[3], wv.w, xj);
-        if (F == 8) {
-            float2 xm = __ldg(xT + (int64_t)(N + i) * B + b);
-            rfma(acc[4], wv.x, xm);
-            rfma(acc[5], wv.y, xm);
-            rfma(acc[6], wv.z, xm);
-            rfma(acc[7], wv.w, xm);
+        for (int f = 0; f < F; ++f) acc[f] = make_float2(0.f, 0.f);
+        if (g < NG && bok) {
+            const int e1 = node_ptr[g + 1];
+            for (int e = node_ptr[g]; e < e1; ++e) {
+                const int wi = node_w[e];
+                const float4 wv = __ldg(w + wi);
+                const int i = wi / U;
+                const float2 xj = __ldg(xT + (int64_t)i * B + b);
+                rfma(acc[0], wv.x, xj);
+                rfma(acc[1], wv.y, xj);
+                rfma(acc[2], wv.z, xj);
+                rfma(acc[3], wv.w, xj);
+                if (F == 8) {
+                    const float2 xm = __ldg(xT + (int64_t)(N + i) * B + b);
+                    rfma(acc[4], wv.x, xm);
+                    rfma(acc[5], wv.y, xm);
+                    rfma(acc[6], wv.z, xm);
+                    rfma(acc[7], wv.w, xm);
+                }
+            }
         }
-    }
-    float2* out = G + (int64_t)b * F * NG + g;
 #pragma unroll
-    for (int f = 0; f < 8; ++f)
-        if (f < F) out[f * NG] = acc[f];
+        for (int f = 0; f < F; ++f) tile[f][lane][gl] = acc[f];
+    }
+    __syncthreads();
+    // rows (f, b): TG consecutive nodes each; 16 lanes per row, two rows per warp instruction
+    const int half = lane >> 4, gl = lane & 15;
+    for (int r = 2 * warp + half; r < F * 32; r += 16) {
+        const int f = r / 32, bl = r % 32;
+        const int bb = b0 + bl;
+        const int64_t g = g0 + gl;
+        if (bb < B && g < NG) G[((int64_t)bb * F + f) * NG + g] = tile[f][bl][gl];
+    }
 }
 
 // ------------------------------------------------------------------ K2
@@ -714,9 +734,14 @@ static void run_fused(aimx_ctx* ctx, const NearC& nc, int B, const float2* xb, f
     AIMX_CUDA_TRY(cudaGetLastError());
     delete sc;
     sc = scope(ST_GATHER);
-    tot = NG * B;
-    k_gather<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(reinterpret_cast<const float4*>(ctx->f32.w),
-                                                          ctx->d_node_ptr, ctx->d_node_w, fb.xT, fb.G, B, F, N, U, NG);
+    {
+        const dim3 grid((unsigned)((NG + 15) / 16), (unsigned)((B + 31) / 32));
+        const float4* w4 = reinterpret_cast<const float4*>(ctx->f32.w);
+        if (F == 8)
+            k_gather_tile<8><<<grid, 256, 0, s>>>(w4, ctx->d_node_ptr, ctx->d_node_w, fb.xT, fb.G, B, N, U, NG);
+        else
+            k_gather_tile<4><<<grid, 256, 0, s>>>(w4, ctx->d_node_ptr, ctx->d_node_w, fb.xT, fb.G, B, N, U, NG);
+    }
     AIMX_CUDA_TRY(cudaGetLastError());
     delete sc;
     sc = scope(ST_XY_FWD);
