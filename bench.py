@@ -195,6 +195,71 @@ def measure_solves(ctx, wl, args):
     return out
 
 
+def measure_batch(args, ws):
+    """The first args.batch_members members of the seeded uneven batch (spheres, boxes,
+    tori; PEC and dielectric; 4 RHS each): one captured graph per call versus the
+    same products issued one member after another on one stream."""
+    import torch
+    from synth import workloads, random_complex
+    from paper_2009_02281_gb300 import Batch, Context, PMCHWT, EFIE
+    members = workloads.uneven_batch(n=args.batch_members)
+    t0 = time.time()
+    ctxs = [Context(m["xyz"], m["tri"], m["grid_n"], order=m["order"],
+                    formulation=PMCHWT if m["formulation"] == "pmchwt" else EFIE,
+                    eps_out=m["eps_out"], eps_in=m["eps_in"] or 1.0, near_radius=m["radius"]) for m in members]
+    torch.cuda.synchronize()
+    setup_s = time.time() - t0
+    xs = [torch.tensor(random_complex((m["nrhs"], c.nunk), seed=700 + i).astype(np.complex64), device="cuda")
+          for i, (m, c) in enumerate(zip(members, ctxs))]
+    ys = [torch.empty_like(x) for x in xs]
+    freqs = [m["freq"] for m in members]
+    stream = torch.cuda.current_stream()
+    batch = Batch(ctxs)
+    batch.matvec(freqs, xs, ys)              # capture
+    for _ in range(2):
+        batch.matvec(freqs, xs, ys)
+        for c, f, x, y in zip(ctxs, freqs, xs, ys):
+            c.matvec(f, x, y)
+    torch.cuda.synchronize()
+    reps = 5
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    e[0].record(stream)
+    for _ in range(reps):
+        batch.matvec(freqs, xs, ys)
+    e[1].record(stream)
+    for _ in range(reps):
+        for c, f, x, y in zip(ctxs, freqs, xs, ys):
+            c.matvec(f, x, y)
+    e[2].record(stream)
+    torch.cuda.synchronize()
+    ms_graph = _barrier_max(e[0].elapsed_time(e[1]) / reps, ws, device="cuda")
+    ms_seq = _barrier_max(e[1].elapsed_time(e[2]) / reps, ws, device="cuda")
+    rhs = sum(m["nrhs"] for m in members)
+    step_bytes = 0.0
+    bins = {}
+    for m, c in zip(members, ctxs):
+        b, _ = _algorithmic_bytes(c.info, m, m["nrhs"])
+        step_bytes += b
+        key = "<5k" if c.nunk < 5000 else ("5k-20k" if c.nunk < 20000 else ">=20k")
+        d = bins.setdefault(key, {"members": 0, "unknowns": 0})
+        d["members"] += 1
+        d["unknowns"] += c.nunk
+    hbm, peak_kind = _peaks()
+    ach = step_bytes / (ms_graph * 1e-3) / 1e9
+    out = {"members": len(members), "rhs_per_call": rhs, "unknowns_total": int(sum(c.nunk for c in ctxs)),
+           "value": round(ws * rhs / (ms_graph * 1e-3), 2), "unit": UNIT, "ms_per_call": round(ms_graph, 3),
+           "sequential_ms_per_call": round(ms_seq, 3), "speedup_vs_sequential": round(ms_seq / ms_graph, 3),
+           "graph_nodes": batch.graph_nodes, "setup_s": round(setup_s, 2),
+           "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+                        "frac": round(ach / hbm, 4), "peak_kind": "of " + peak_kind,
+                        "algorithmic_bytes_per_call": step_bytes},
+           "size_bins": bins}
+    batch.close()
+    for c in ctxs:
+        c.close()
+    return out
+
+
 def run_ours(args):
     import torch
     ws, rank = _dist()
@@ -270,6 +335,26 @@ def run_ours(args):
     torch.cuda.synchronize()
     e2e_s = _barrier_max(time.perf_counter() - t0, ws, device="cuda")
 
+    # FP64 products (generic radix-2 path, the precision of the paper's solver) on a sub-batch
+    fp64 = None
+    if not args.no_fp64:
+        nb64 = min(B, 8)
+        x64 = torch.tensor(x_np[:nb64].astype(np.complex128), device="cuda")
+        y64 = torch.empty_like(x64)
+        ctx.matvec(freq, x64, y64)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 3
+        e0.record(stream)
+        for _ in range(reps):
+            ctx.matvec(freq, x64, y64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1) / reps
+        fp64 = {"value": round(ws * nb64 / (ms64 * 1e-3), 2), "unit": UNIT, "rhs_per_call": nb64,
+                "ms_per_call": round(ms64, 3), "path": "generic radix-2 FP64 (kernel spectra FP64)"}
+        del x64, y64
+
     hbm, peak_kind = _peaks()
     step_bytes, stage_bytes = _algorithmic_bytes(info, wl, B)
     dom = max(prof.items(), key=lambda kv: kv[1][0])[0] if prof else None
@@ -301,17 +386,22 @@ def run_ours(args):
         "e2e": {"value": round(ws * B * e2e_steps / e2e_s, 2), "unit": UNIT,
                 "h2d_bytes_per_step": int(x_np.nbytes), "d2h_bytes_per_step": int(x_np.nbytes)},
         "gpu_launches": launches,
+        "fp64": fp64,
         "clocks": clk,
         "setup_s": round(setup_s, 3),
         "first_call_ms_incl_kernel_generation": round(first_ms, 3),
     }
     if not args.no_solves:
         out["solves"] = measure_solves(ctx, wl, args)
+    if args.batch_members > 0:
+        ctx.close()
+        out["uneven_batch"] = measure_batch(args, ws)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl, args.cpu_rows)
     if rank == 0:
         print(json.dumps(out), flush=True)
-    ctx.close()
+    if args.batch_members <= 0:
+        ctx.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
 
@@ -390,6 +480,9 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solves", action="store_true", help="skip the batched solve measurement")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 product measurement")
+    ap.add_argument("--batch-members", type=int, default=16,
+                    help="members of the seeded uneven batch to time (0 = skip; 48 = the full batch)")
     ap.add_argument("--path", type=int, default=0, choices=[0, 1], help="FP32 product path (aimx_set_path)")
     ap.add_argument("--solve-tol", type=float, default=1e-4)
     ap.add_argument("--gnn-steps", type=int, default=600, help="training steps of the learned preconditioner")

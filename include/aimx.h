@@ -48,6 +48,7 @@ extern "C" {
 #define AIMX_E_CUDA     -5   /* a CUDA runtime call failed                             */
 #define AIMX_E_TIMEOUT  -6   /* a bounded device wait expired                          */
 #define AIMX_E_STATE    -7   /* call not valid for this context (e.g. wrong formulation) */
+#define AIMX_E_IO       -8   /* file not readable / writable, or not a matching static-data file */
 #define AIMX_E_NOCONV    1   /* warning: at least one RHS missed the solver tolerance  */
 
 /* ------------------------------------------------------------------ inputs */
@@ -278,6 +279,44 @@ int aimx_matvec_noalloc(aimx_ctx* ctx, double freq, int nrhs, const void* x, voi
  * Synchronous. */
 int aimx_export_setup(const aimx_ctx* ctx, int32_t* anchors, double* weights,
                       int64_t* row_ptr, int32_t* cols, double* na, double* nphi, double* nk);
+
+/* ------------------------------------------------------------------ static data (lifecycle) */
+
+/* The frequency-independent setup products of a context (mesh, material,
+ * resolved grid, order, FP64 projection weights, precorrected near matrices
+ * N^A, N^Phi, N^K and static self terms: the static part that AIMx computes
+ * once for all frequencies, Sec. III-A) written to / read from a binary file
+ * (native byte order, FNV-1a checksum).  aimx_load_static rebuilds the
+ * topology from the stored mesh and restores the stored arrays instead of
+ * recomputing the near integrals; the new context computes the same products
+ * bit for bit.  Errors: AIMX_E_ARG (null arguments), AIMX_E_IO (I/O failure,
+ * bad magic or version, checksum mismatch, arrays that do not match the
+ * mesh), plus the aimx_setup errors on load.  Synchronous. */
+int aimx_save_static(const aimx_ctx* ctx, const char* path);
+int aimx_load_static(const char* path, aimx_ctx** out);
+
+/* ------------------------------------------------------------------ batches of uneven meshes */
+
+/* A batch of n contexts (different meshes, grids, formulations) whose FP32
+ * products are applied together: members run concurrently on `nstreams`
+ * internal streams (0 = min(8, n)) and the whole batch is captured into one
+ * CUDA graph on the first call, replayed by later calls with the same
+ * per-member frequencies, RHS counts and buffer pointers (any change
+ * recaptures).  The paper treats one problem at a time; batching many small
+ * problems is how a GPU stays busy on them.  The member contexts are borrowed
+ * (the caller keeps them alive and does not use them concurrently with the
+ * batch); profiling is off inside the graph.
+ *   freqs [n] Hz, nrhs [n], x[i] / y[i]: device complex64 [nrhs[i]][n_unknowns_i]
+ *   of member i, caller-owned.  Asynchronous on `stream` after the first call
+ *   (the first call runs each member once and synchronises to build the graph).
+ * Errors: AIMX_E_ARG, AIMX_E_CUDA (capture failed), AIMX_E_NOMEM. */
+typedef struct aimx_batch aimx_batch;
+int aimx_batch_create(int n, aimx_ctx* const* ctxs, int nstreams, aimx_batch** out);
+int aimx_batch_destroy(aimx_batch* b);
+int aimx_batch_matvec(aimx_batch* b, const double* freqs, const int* nrhs, const void* const* x, void* const* y,
+                      void* stream);
+int64_t aimx_batch_graph_nodes(const aimx_batch* b);      /* nodes of the captured graph (0 before the first call) */
+const char* aimx_batch_last_error(const aimx_batch* b);
 
 /* ------------------------------------------------------------------------
  * Learned near-field preconditioner (no counterpart in the paper, whose

@@ -18,7 +18,8 @@ F64 = 1
 
 _STATUS = {0: "ok", -1: "invalid argument", -2: "invalid mesh", -3: "stencil outside the grid",
            -4: "out of memory", -5: "CUDA error", -6: "bounded device wait expired",
-           -7: "call not valid for this context", 1: "solver did not reach the tolerance"}
+           -7: "call not valid for this context", -8: "static-data file error",
+           1: "solver did not reach the tolerance"}
 
 
 class AimxError(RuntimeError):
@@ -82,6 +83,15 @@ _SIGS = [
                                   ctypes.c_void_p]),
     ("aimx_precond_apply", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("aimx_batch_create", ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_void_p)]),
+    ("aimx_batch_destroy", ctypes.c_int, [ctypes.c_void_p]),
+    ("aimx_batch_matvec", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_void_p]),
+    ("aimx_batch_graph_nodes", ctypes.c_int64, [ctypes.c_void_p]),
+    ("aimx_batch_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
+    ("aimx_save_static", ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
+    ("aimx_load_static", ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_void_p)]),
     ("aimx_gnn_create", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
     ("aimx_gnn_destroy", ctypes.c_int, [ctypes.c_void_p]),
     ("aimx_gnn_num_params", ctypes.c_int64, [ctypes.c_void_p]),
@@ -198,6 +208,26 @@ class Context:
         self.N = self.info["n_basis"]
         self.nunk = self.info["n_unknowns"]
         self.formulation = formulation
+
+    @classmethod
+    def load_static(cls, path):
+        """A context restored from a file written by save_static (aimx_load_static)."""
+        self = cls.__new__(cls)
+        self._lib = load()
+        out = ctypes.c_void_p()
+        rc = self._lib.aimx_load_static(os.fsencode(path), ctypes.byref(out))
+        if rc != 0:
+            raise AimxError(rc, str(path))
+        self._ctx = out
+        self.info = self._info()
+        self.N = self.info["n_basis"]
+        self.nunk = self.info["n_unknowns"]
+        self.formulation = self.info["formulation"]
+        return self
+
+    def save_static(self, path):
+        """Write the frequency-independent setup products to a file (aimx_save_static)."""
+        self._check(self._lib.aimx_save_static(self._ctx, os.fsencode(path)))
 
     def _check(self, rc):
         if rc < 0:
@@ -489,3 +519,46 @@ class Gnn:
             if log is not None:
                 log(it, losses[-1])
         return losses
+
+
+class Batch:
+    """FP32 products of several contexts as one captured CUDA graph (aimx_batch_*).
+
+    The contexts are borrowed: keep them open while the batch is used."""
+
+    def __init__(self, contexts, nstreams=0):
+        self._lib = load()
+        self.contexts = list(contexts)
+        arr = (ctypes.c_void_p * len(self.contexts))(*[c._ctx for c in self.contexts])
+        h = ctypes.c_void_p()
+        rc = self._lib.aimx_batch_create(len(self.contexts), arr, int(nstreams), ctypes.byref(h))
+        if rc != 0:
+            raise AimxError(rc, "aimx_batch_create")
+        self._b = h
+
+    def close(self):
+        if getattr(self, "_b", None):
+            self._lib.aimx_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def matvec(self, freqs, xs, ys, stream=None):
+        """ys[i] = A_i(freqs[i]) xs[i] for complex64 CUDA tensors [nrhs_i, n_unknowns_i]."""
+        n = len(self.contexts)
+        f = (ctypes.c_double * n)(*[float(v) for v in freqs])
+        nr = (ctypes.c_int * n)(*[int(x.shape[0]) for x in xs])
+        xp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+        yp = (ctypes.c_void_p * n)(*[y.data_ptr() for y in ys])
+        rc = self._lib.aimx_batch_matvec(self._b, f, nr, xp, yp, _stream_handle(stream))
+        if rc != 0:
+            raise AimxError(rc, (self._lib.aimx_batch_last_error(self._b) or b"").decode())
+        return ys
+
+    @property
+    def graph_nodes(self):
+        return int(self._lib.aimx_batch_graph_nodes(self._b))

@@ -230,8 +230,14 @@ void* dev_alloc(aimx_ctx* ctx, size_t bytes);
 void dev_free(aimx_ctx* ctx, void* p);
 
 // setup.cu
+// Precomputed setup products (internal basis order) restored by aimx_load_static.
+struct StaticData {
+    std::vector<double> w;     // [N][U][4] projection weights
+    std::vector<double> na, np, nk;  // [nnz] near matrices N^A, N^Phi, N^K
+    std::vector<double> diag;  // [N][3] static self terms
+};
 void setup_context(aimx_ctx* ctx, const aimx_mesh* mesh, const aimx_material* mat,
-                   const aimx_grid* grid, int order);
+                   const aimx_grid* grid, int order, const StaticData* pre = nullptr);
 
 // fft.cu
 const double2* twiddles64();

@@ -3,6 +3,7 @@
 // across the ABI.
 
 #include <algorithm>
+#include <cstdio>
 #include <cstring>
 #include <map>
 
@@ -95,6 +96,7 @@ const char* aimx_status_string(int status) {
         case AIMX_E_CUDA: return "CUDA error";
         case AIMX_E_TIMEOUT: return "bounded device wait expired";
         case AIMX_E_STATE: return "call not valid for this context";
+        case AIMX_E_IO: return "static-data file error";
         case AIMX_E_NOCONV: return "solver did not reach the tolerance";
         default: return "unknown status";
     }
@@ -284,6 +286,194 @@ int aimx_export_setup(const aimx_ctx* ctx, int32_t* anchors, double* weights, in
     } catch (const Error& e) {
         return fail(c, e);
     }
+    return AIMX_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ static data files
+
+namespace {
+
+constexpr char kMagic[8] = {'A', 'I', 'M', 'X', 'S', 'T', 'A', 'T'};
+constexpr int32_t kStaticVersion = 1;
+
+struct Fnv {
+    uint64_t h = 1469598103934665603ull;
+    void add(const void* p, size_t n) {
+        const unsigned char* c = static_cast<const unsigned char*>(p);
+        for (size_t i = 0; i < n; ++i) {
+            h ^= c[i];
+            h *= 1099511628211ull;
+        }
+    }
+};
+
+struct Writer {
+    FILE* f;
+    Fnv fnv;
+    bool ok = true;
+    void put(const void* p, size_t n) {
+        if (n && std::fwrite(p, 1, n, f) != n) ok = false;
+        fnv.add(p, n);
+    }
+    template <class T>
+    void val(const T& v) { put(&v, sizeof(T)); }
+    template <class T>
+    void vec(const std::vector<T>& v) { put(v.data(), sizeof(T) * v.size()); }
+};
+
+struct Reader {
+    FILE* f;
+    Fnv fnv;
+    bool ok = true;
+    void get(void* p, size_t n) {
+        if (n && std::fread(p, 1, n, f) != n) ok = false;
+        fnv.add(p, n);
+    }
+    template <class T>
+    T val() {
+        T v{};
+        get(&v, sizeof(T));
+        return v;
+    }
+    template <class T>
+    void vec(std::vector<T>& v, size_t n) {
+        if (!ok || n > (size_t(1) << 36) / sizeof(T)) {
+            ok = false;
+            return;
+        }
+        v.resize(n);
+        get(v.data(), sizeof(T) * n);
+    }
+};
+
+template <class T>
+std::vector<T> from_device(const T* d, size_t n) {
+    std::vector<T> h(n);
+    AIMX_CUDA_TRY(cudaMemcpy(h.data(), d, sizeof(T) * n, cudaMemcpyDeviceToHost));
+    return h;
+}
+
+}  // namespace
+
+extern "C" {
+
+int aimx_save_static(const aimx_ctx* ctx, const char* path) {
+    if (!ctx || !path) return AIMX_E_ARG;
+    aimx_ctx* c = const_cast<aimx_ctx*>(ctx);
+    try {
+        const int N = ctx->N;
+        const size_t nw = (size_t)N * ctx->U * 4;
+        std::vector<double> xyz = from_device(ctx->d_xyz, 3 * (size_t)ctx->nv);
+        std::vector<int> tri = from_device(ctx->d_tri, 3 * (size_t)ctx->nt);
+        std::vector<double> w = from_device(ctx->f64.w, nw);
+        std::vector<double> na = from_device(ctx->f64.na, (size_t)ctx->nnz);
+        std::vector<double> np = from_device(ctx->f64.np, (size_t)ctx->nnz);
+        std::vector<double> nk = from_device(ctx->f64.nk, (size_t)ctx->nnz);
+        std::vector<double> diag = from_device(ctx->d_diag, 3 * (size_t)N);
+        FILE* f = std::fopen(path, "wb");
+        if (!f) throw Error{AIMX_E_IO, std::string("cannot open ") + path + " for writing"};
+        Writer wr{f};
+        wr.put(kMagic, sizeof(kMagic));
+        wr.fnv = Fnv();
+        wr.val(kStaticVersion);
+        wr.val<int32_t>(ctx->nv);
+        wr.val<int32_t>(ctx->nt);
+        wr.val<int32_t>(ctx->form);
+        wr.val<int32_t>(ctx->order);
+        for (int a = 0; a < 3; ++a) wr.val<int32_t>(ctx->n[a]);
+        wr.val<int32_t>(ctx->radius);
+        wr.val<int32_t>(N);
+        wr.val<int64_t>(ctx->nnz);
+        wr.val(ctx->eps_out);
+        wr.val(ctx->mu_out);
+        wr.val(ctx->eps_in);
+        wr.val(ctx->mu_in);
+        for (int a = 0; a < 3; ++a) wr.val(ctx->h[a]);
+        for (int a = 0; a < 3; ++a) wr.val(ctx->origin[a]);
+        wr.vec(xyz);
+        wr.vec(tri);
+        wr.vec(w);
+        wr.vec(na);
+        wr.vec(np);
+        wr.vec(nk);
+        wr.vec(diag);
+        const uint64_t sum = wr.fnv.h;
+        if (std::fwrite(&sum, 1, sizeof(sum), f) != sizeof(sum)) wr.ok = false;
+        if (std::fclose(f) != 0) wr.ok = false;
+        if (!wr.ok) throw Error{AIMX_E_IO, std::string("write to ") + path + " failed"};
+    } catch (const Error& e) {
+        return fail(c, e);
+    }
+    return AIMX_OK;
+}
+
+int aimx_load_static(const char* path, aimx_ctx** out) {
+    if (!path || !out) return AIMX_E_ARG;
+    *out = nullptr;
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return AIMX_E_IO;
+    Reader rd{f};
+    char magic[8];
+    if (std::fread(magic, 1, 8, f) != 8 || std::memcmp(magic, kMagic, 8) != 0) {
+        std::fclose(f);
+        return AIMX_E_IO;
+    }
+    const int32_t version = rd.val<int32_t>();
+    const int32_t nv = rd.val<int32_t>(), nt = rd.val<int32_t>(), form = rd.val<int32_t>(),
+                  order = rd.val<int32_t>();
+    aimx_grid grid{};
+    for (int a = 0; a < 3; ++a) grid.n[a] = rd.val<int32_t>();
+    grid.near_radius = rd.val<int32_t>();
+    const int32_t N = rd.val<int32_t>();
+    const int64_t nnz = rd.val<int64_t>();
+    aimx_material mat{};
+    mat.formulation = form;
+    mat.eps_out = rd.val<double>();
+    mat.mu_out = rd.val<double>();
+    mat.eps_in = rd.val<double>();
+    mat.mu_in = rd.val<double>();
+    for (int a = 0; a < 3; ++a) grid.h[a] = rd.val<double>();
+    for (int a = 0; a < 3; ++a) grid.origin[a] = rd.val<double>();
+    std::vector<double> xyz;
+    std::vector<int> tri;
+    StaticData st;
+    const int U = (order + 1) * (order + 1) * (order + 1);
+    const bool sane = rd.ok && version == kStaticVersion && nv > 0 && nt > 0 && N > 0 && nnz > 0 && order >= 1 &&
+                      order <= 3;
+    if (sane) {
+        rd.vec(xyz, 3 * (size_t)nv);
+        rd.vec(tri, 3 * (size_t)nt);
+        rd.vec(st.w, (size_t)N * U * 4);
+        rd.vec(st.na, (size_t)nnz);
+        rd.vec(st.np, (size_t)nnz);
+        rd.vec(st.nk, (size_t)nnz);
+        rd.vec(st.diag, 3 * (size_t)N);
+    }
+    uint64_t sum = 0;
+    const bool got_sum = std::fread(&sum, 1, sizeof(sum), f) == sizeof(sum);
+    std::fclose(f);
+    if (!sane || !rd.ok || !got_sum || sum != rd.fnv.h) return AIMX_E_IO;
+    aimx_mesh mesh{nv, nt, xyz.data(), tri.data()};
+    aimx_ctx* ctx = new (std::nothrow) aimx_ctx();
+    if (!ctx) return AIMX_E_NOMEM;
+    try {
+        setup_context(ctx, &mesh, &mat, &grid, order, &st);
+        if (ctx->N != N || ctx->nnz != nnz) throw Error{AIMX_E_IO, "static data does not match the mesh"};
+    } catch (const Error& e) {
+        cudaDeviceSynchronize();
+        cudaGetLastError();
+        free_all(ctx);
+        int code = e.code;
+        delete ctx;
+        return code;
+    } catch (const std::bad_alloc&) {
+        free_all(ctx);
+        delete ctx;
+        return AIMX_E_NOMEM;
+    }
+    *out = ctx;
     return AIMX_OK;
 }
 

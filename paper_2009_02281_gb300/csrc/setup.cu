@@ -326,7 +326,7 @@ static int next_pow2(int v) {
 }
 
 void setup_context(aimx_ctx* ctx, const aimx_mesh* mesh, const aimx_material* mat,
-                   const aimx_grid* grid, int order) {
+                   const aimx_grid* grid, int order, const StaticData* pre) {
     if (!mesh || !mat || !grid || !mesh->xyz || !mesh->tri || mesh->nv < 3 || mesh->nt < 1)
         throw Error{AIMX_E_ARG, "null or empty mesh/material/grid"};
     if (order < 1 || order > 3) throw Error{AIMX_E_ARG, "order must be 1..3"};
@@ -589,12 +589,20 @@ void setup_context(aimx_ctx* ctx, const aimx_mesh* mesh, const aimx_material* ma
     // projection weights
     ctx->f64.w = (double*)dev_alloc(ctx, sizeof(double) * (size_t)N * U * 4);
     ctx->f32.w = (float*)dev_alloc(ctx, sizeof(float) * (size_t)N * U * 4);
+    if (pre && (pre->w.size() != (size_t)N * U * 4 || pre->na.size() != (size_t)ctx->nnz ||
+                pre->np.size() != (size_t)ctx->nnz || pre->nk.size() != (size_t)ctx->nnz ||
+                pre->diag.size() != 3 * (size_t)N))
+        throw Error{AIMX_E_IO, "static data does not match the mesh and grid"};
     {
         int threads = 128;
         int64_t tot = (int64_t)N * U;
-        k_weights<<<(unsigned)((tot + threads - 1) / threads), threads>>>(
-            gv, ctx->d_anc, N, P, nq_proj, ctx->origin[0], ctx->origin[1], ctx->origin[2], ctx->h[0],
-            ctx->h[1], ctx->h[2], ctx->f64.w);
+        if (pre)
+            AIMX_CUDA_TRY(cudaMemcpy(ctx->f64.w, pre->w.data(), sizeof(double) * pre->w.size(),
+                                     cudaMemcpyHostToDevice));
+        else
+            k_weights<<<(unsigned)((tot + threads - 1) / threads), threads>>>(
+                gv, ctx->d_anc, N, P, nq_proj, ctx->origin[0], ctx->origin[1], ctx->origin[2], ctx->h[0],
+                ctx->h[1], ctx->h[2], ctx->f64.w);
         AIMX_CUDA_TRY(cudaGetLastError());
         size_t n4 = (size_t)N * U * 4;
         k_to_float<<<(unsigned)((n4 + 255) / 256), 256>>>(ctx->f64.w, ctx->f32.w, n4);
@@ -605,6 +613,22 @@ void setup_context(aimx_ctx* ctx, const aimx_mesh* mesh, const aimx_material* ma
 
     // static near integrals + precorrection
     const int64_t nnz = ctx->nnz;
+    if (pre) {
+        auto put = [&](const std::vector<double>& h, double*& d64, float*& d32) {
+            d64 = (double*)dev_alloc(ctx, sizeof(double) * h.size());
+            d32 = (float*)dev_alloc(ctx, sizeof(float) * h.size());
+            AIMX_CUDA_TRY(cudaMemcpy(d64, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice));
+            k_to_float<<<(unsigned)((h.size() + 255) / 256), 256>>>(d64, d32, h.size());
+            AIMX_CUDA_TRY(cudaGetLastError());
+        };
+        put(pre->na, ctx->f64.na, ctx->f32.na);
+        put(pre->np, ctx->f64.np, ctx->f32.np);
+        put(pre->nk, ctx->f64.nk, ctx->f32.nk);
+        ctx->d_diag = upload(ctx, pre->diag);
+        AIMX_CUDA_TRY(cudaDeviceSynchronize());
+        dev_free(ctx, d_row_of);
+        return;
+    }
     double* d_LA = (double*)dev_alloc(ctx, sizeof(double) * nnz);
     double* d_LP = (double*)dev_alloc(ctx, sizeof(double) * nnz);
     double* d_KK = (double*)dev_alloc(ctx, sizeof(double) * nnz);

@@ -12,9 +12,17 @@ stand in for the paper's geometries, which are not available.
   (20480 triangles, 30720 RWG, two-region formulation with 61440 unknowns),
   diameter = 3 free-space wavelengths (f = 1.5 c Hz, about 449.7 MHz), 64^3 grid padded to
   128^3, order 2, near radius 3, 64 right-hand sides, FP32 matvec.
+* ``uneven_batch``: seeded mix of PEC (EFIE) and dielectric (eps_r ~ U[2, 6],
+  two-region) spheres, boxes and tori of size U[0.5, 4] free-space wavelengths
+  at f = c (wavelength 1 m), meshed for a log-uniform 2k-60k unknowns, each
+  with a power-of-two grid per axis (8..64 nodes) chosen for a spacing of
+  min(0.1 interior wavelength, mean mesh edge) and capped at 64 nodes, 4
+  right-hand sides, FP32.
 """
 
-from .meshes import icosphere
+import numpy as np
+
+from .meshes import box, icosphere, torus
 
 C0 = 299792458.0
 
@@ -30,6 +38,48 @@ def dielectric_sphere_61440(nrhs=64):
     return dict(name="dielectric_sphere_61440", xyz=xyz, tri=tri, formulation="pmchwt", eps_out=1.0,
                 eps_in=4.0, grid_n=(64, 64, 64), order=2, radius=3, freq=1.5 * C0, nrhs=nrhs,
                 precision="f32")
+
+
+def _pow2_nodes(extent, h, order=2):
+    m = (order + 1) // 2
+    need = int(np.ceil(extent / h)) + 1 + 2 * m
+    n = 8
+    while n < need and n < 64:
+        n *= 2
+    return n
+
+
+def uneven_batch(n=48, seed=0, nrhs=4):
+    """Members of an uneven batch of meshes (list of workload dicts)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        kind = ("sphere", "box", "torus")[int(rng.integers(3))]
+        dielectric = bool(rng.integers(2))
+        eps = float(rng.uniform(2.0, 6.0)) if dielectric else None
+        size = float(rng.uniform(0.5, 4.0))             # free-space wavelengths (1 m)
+        target = float(np.exp(rng.uniform(np.log(2000.0), np.log(60000.0))))
+        edges = target / (2 if dielectric else 1)
+        if kind == "sphere":
+            level = int(np.clip(np.round(np.log(edges / 30.0) / np.log(4.0)), 2, 5))
+            xyz, tri = icosphere(level, radius=0.5 * size)
+        elif kind == "box":
+            d = max(2, int(np.round(np.sqrt(edges / 18.0))))
+            a = 0.5 * size / np.sqrt(3.0)
+            xyz, tri = box([-a, -a, -a], [a, a, a], [d, d, d])
+        else:
+            nm = max(4, int(np.round(np.sqrt(edges / 6.0))))
+            xyz, tri = torus(0.35 * size, 0.15 * size, 2 * nm, nm)
+        lam_in = 1.0 / np.sqrt(eps) if dielectric else 1.0
+        ext = xyz.max(0) - xyz.min(0)
+        t = xyz[tri]
+        edge = np.mean(np.linalg.norm(t - np.roll(t, 1, axis=1), axis=2))
+        h = min(0.1 * lam_in, edge)       # resolve the wavelength and the mesh
+        grid = tuple(_pow2_nodes(e, h) for e in ext)
+        out.append(dict(name="%s_%s_%d" % (kind, "diel" if dielectric else "pec", i), xyz=xyz, tri=tri,
+                        formulation="pmchwt" if dielectric else "efie", eps_out=1.0, eps_in=eps,
+                        grid_n=grid, order=2, radius=3, freq=C0, nrhs=nrhs, precision="f32"))
+    return out
 
 
 WORKLOADS = {"pec_sphere_1920": pec_sphere_1920, "dielectric_sphere_61440": dielectric_sphere_61440}
