@@ -68,11 +68,17 @@ typedef struct {
 #define AIMX_PMCHWT  1   /* penetrable body, two regions, unknowns [J ; M/eta0]            */
 
 /* Materials.  Relative permittivity / permeability of the background (region
- * 1) and, for AIMX_PMCHWT, of the body (region 2).  Lossless values only. */
+ * 1) and, for AIMX_PMCHWT, of the body (region 2); lossless values.  sigma:
+ * conductivity (S/m) of an AIMX_EFIE body for the surface impedance boundary
+ * condition (skin effect, cited in Sec. VI): the system becomes Z + Z_s(w) G
+ * with Z_s = (1 + j)/(sigma delta), delta = sqrt(2/(w mu0 sigma)) and G the
+ * RWG Gram matrix, a static near-region matrix like N^A.  0 = perfect
+ * conductor.  Ignored for AIMX_PMCHWT. */
 typedef struct {
     int32_t formulation;
     double eps_out, mu_out;
     double eps_in, mu_in;
+    double sigma;
 } aimx_material;
 
 /* Auxiliary grid (Sec. II-B).  n: nodes per axis (required).  h: spacing per
@@ -279,6 +285,40 @@ int aimx_matvec_noalloc(aimx_ctx* ctx, double freq, int nrhs, const void* x, voi
  * Synchronous. */
 int aimx_export_setup(const aimx_ctx* ctx, int32_t* anchors, double* weights,
                       int64_t* row_ptr, int32_t* cols, double* na, double* nphi, double* nk);
+
+/* ------------------------------------------------------------------ delta-gap ports */
+
+/* A delta-gap port (cited in Sec. VI): the plane through `point` with unit
+ * `normal`, restricted to the axis-aligned box [box_lo, box_hi] (one conductor's
+ * cut).  Its gap edges are the RWG edges lying in the plane (to 1e-9 of the
+ * longest edge) with midpoints inside the box.  The port vector is
+ * c_m = l_m s_m on the gap edges, s_m = sign((centroid(T-) - centroid(T+)) . normal):
+ * a 1 V gap excites b = c, and the port current of coefficients x is c . x.
+ * AIMX_EFIE contexts only (AIMX_E_STATE otherwise); a port with no gap edge is
+ * AIMX_E_ARG. */
+typedef struct {
+    double point[3];
+    double normal[3];
+    double box_lo[3];
+    double box_hi[3];
+} aimx_port;
+
+/* Host port vectors c [nport][N] (caller basis order, float64) and gap-edge
+ * counts nedges [nport] (either may be NULL).  Synchronous. */
+int aimx_port_vectors(aimx_ctx* ctx, int nport, const aimx_port* ports, double* c, int32_t* nedges);
+/* b: device complex128 [nport][n_unknowns] = the unit-voltage excitations. */
+int aimx_rhs_ports(aimx_ctx* ctx, int nport, const aimx_port* ports, void* b, void* stream);
+/* I: host complex128 [nrhs][nport] port currents of device complex128 x [nrhs][n_unknowns].  Synchronous. */
+int aimx_port_currents(aimx_ctx* ctx, int nport, const aimx_port* ports, int nrhs, const void* x, void* I,
+                       void* stream);
+/* Y-parameter sweep: for each frequency solve the nport unit-voltage systems
+ * (lockstep GMRES, opts as aimx_solve, warm start from the previous frequency)
+ * and write Y [nf][nport][nport] (host complex128, Y[f][i][j] = current at port
+ * i for 1 V at port j).  stats: host [nf][nport] or NULL.  Static data and the
+ * kernel-generation buffers are reused across the sweep (Sec. III-A).  Returns
+ * AIMX_E_NOCONV (> 0) if any system missed the tolerance (Y still written). */
+int aimx_sweep_ports(aimx_ctx* ctx, int nf, const double* freqs, int nport, const aimx_port* ports, void* Y,
+                     const aimx_solve_opts* opts, aimx_solve_stats* stats, void* stream);
 
 /* ------------------------------------------------------------------ static data (lifecycle) */
 

@@ -35,7 +35,21 @@ class _Mesh(ctypes.Structure):
 
 class _Material(ctypes.Structure):
     _fields_ = [("formulation", ctypes.c_int32), ("eps_out", ctypes.c_double), ("mu_out", ctypes.c_double),
-                ("eps_in", ctypes.c_double), ("mu_in", ctypes.c_double)]
+                ("eps_in", ctypes.c_double), ("mu_in", ctypes.c_double), ("sigma", ctypes.c_double)]
+
+
+class Port(ctypes.Structure):
+    """Delta-gap port: plane (point, normal) restricted to the box [box_lo, box_hi] (aimx_port)."""
+    _fields_ = [("point", ctypes.c_double * 3), ("normal", ctypes.c_double * 3), ("box_lo", ctypes.c_double * 3),
+                ("box_hi", ctypes.c_double * 3)]
+
+    @classmethod
+    def make(cls, point, normal, box_lo, box_hi):
+        p = cls()
+        for a in range(3):
+            p.point[a], p.normal[a] = float(point[a]), float(normal[a])
+            p.box_lo[a], p.box_hi[a] = float(box_lo[a]), float(box_hi[a])
+        return p
 
 
 class _Grid(ctypes.Structure):
@@ -90,6 +104,15 @@ _SIGS = [
                                          ctypes.c_void_p, ctypes.c_void_p]),
     ("aimx_batch_graph_nodes", ctypes.c_int64, [ctypes.c_void_p]),
     ("aimx_batch_last_error", ctypes.c_char_p, [ctypes.c_void_p]),
+    ("aimx_port_vectors", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_void_p]),
+    ("aimx_rhs_ports", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p]),
+    ("aimx_port_currents", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("aimx_sweep_ports", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p]),
     ("aimx_save_static", ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
     ("aimx_load_static", ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_void_p)]),
     ("aimx_gnn_create", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]),
@@ -183,14 +206,14 @@ class Context:
     """An AIMx problem on the current CUDA device (wraps aimx_setup / aimx_destroy)."""
 
     def __init__(self, xyz, tri, grid_n, order=2, formulation=EFIE, eps_out=1.0, mu_out=1.0,
-                 eps_in=1.0, mu_in=1.0, h=None, origin=None, near_radius=3, pad=None):
+                 eps_in=1.0, mu_in=1.0, h=None, origin=None, near_radius=3, pad=None, sigma=0.0):
         self._lib = load()
         self._xyz = np.ascontiguousarray(xyz, dtype=np.float64)
         self._tri = np.ascontiguousarray(tri, dtype=np.int32)
         mesh = _Mesh(len(self._xyz), len(self._tri),
                      self._xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                      self._tri.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
-        mat = _Material(formulation, eps_out, mu_out, eps_in, mu_in)
+        mat = _Material(formulation, eps_out, mu_out, eps_in, mu_in, sigma)
         g = _Grid()
         for a in range(3):
             g.n[a] = int(grid_n[a])
@@ -384,6 +407,48 @@ class Context:
         self._check(self._lib.aimx_export_setup(self._ctx, _ptr(anc), _ptr(w), _ptr(rp), _ptr(cols), _ptr(na),
                                                 _ptr(nphi), _ptr(nk)))
         return dict(anchors=anc, weights=w, row_ptr=rp, cols=cols, NA=na, NP=nphi, NK=nk)
+
+    # ---------------------------------------------------------------- delta-gap ports
+    @staticmethod
+    def _ports(ports):
+        return (Port * len(ports))(*ports)
+
+    def port_vectors(self, ports):
+        """(c [nport, N] float64 port vectors, gap-edge counts [nport])."""
+        c = np.zeros((len(ports), self.N))
+        ne = np.zeros(len(ports), dtype=np.int32)
+        self._check(self._lib.aimx_port_vectors(self._ctx, len(ports), self._ports(ports), _ptr(c), _ptr(ne)))
+        return c, ne
+
+    def rhs_ports(self, ports, stream=None):
+        """Unit-voltage excitations as a CUDA complex128 tensor [nport, nunk]."""
+        import torch
+        b = torch.empty((len(ports), self.nunk), dtype=torch.complex128, device="cuda")
+        self._check(self._lib.aimx_rhs_ports(self._ctx, len(ports), self._ports(ports),
+                                             ctypes.c_void_p(b.data_ptr()), _stream_handle(stream)))
+        return b
+
+    def port_currents(self, ports, x, stream=None):
+        """Port currents [nrhs, nport] (complex128) of CUDA complex128 coefficients x [nrhs, nunk]."""
+        if x.dim() == 1:
+            x = x.unsqueeze(0)
+        x = x.contiguous()
+        out = np.zeros((x.shape[0], len(ports)), dtype=np.complex128)
+        self._check(self._lib.aimx_port_currents(self._ctx, len(ports), self._ports(ports), x.shape[0],
+                                                 ctypes.c_void_p(x.data_ptr()), _ptr(out), _stream_handle(stream)))
+        return out
+
+    def sweep_ports(self, freqs, ports, tol=1e-6, restart=50, max_iter=1000, inner_precision=F32,
+                    precond=PRECOND_DIAG, stream=None):
+        """Y-parameters [nf, nport, nport] over a frequency sweep; returns (Y, stats, status)."""
+        f = np.ascontiguousarray(freqs, dtype=np.float64)
+        P = len(ports)
+        Y = np.zeros((len(f), P, P), dtype=np.complex128)
+        st = (_SolveStats * (len(f) * P))()
+        o = _opts(tol, restart, max_iter, inner_precision, precond)
+        rc = self._check(self._lib.aimx_sweep_ports(self._ctx, len(f), _ptr(f), P, self._ports(ports), _ptr(Y),
+                                                    ctypes.byref(o), st, _stream_handle(stream)))
+        return Y, _stats_list(st), rc
 
     # ---------------------------------------------------------------- learned preconditioner
     def gnn_attach(self, net):

@@ -9,7 +9,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libaimx.so")
-SOURCES = ["setup.cu", "fft.cu", "matvec.cu", "fused.cu", "solve.cu", "precond.cu", "gnn.cu", "batch.cu",
+SOURCES = ["setup.cu", "fft.cu", "matvec.cu", "fused.cu", "solve.cu", "precond.cu", "gnn.cu", "batch.cu", "ports.cu",
            "noalloc.cu", "api.cu"]
 HEADERS = ["aimx_internal.h", "cplx.cuh", "fftreg.cuh", "regfft.cuh"]
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -60,6 +60,7 @@ struct PrecData {
     T* na = nullptr;       // near N^A  [nnz]
     T* np = nullptr;       // near N^Phi[nnz]
     T* nk = nullptr;       // near N^K  [nnz]
+    T* ng = nullptr;       // near Gram matrix [nnz] (surface impedance, EFIE with sigma > 0)
     T* spec = nullptr;     // octant spectra [nspec][Oz][Oy][Ox] complex (2 T each)
     double spec_freq = -1.0;
     // work buffers of the generic FFT path
@@ -163,6 +164,7 @@ struct aimx_ctx {
     double origin[3] = {0, 0, 0};
     int radius = 3;
     double eps_out = 1, mu_out = 1, eps_in = 1, mu_in = 1;
+    double sigma = 0;      // conductivity for the surface impedance (EFIE), 0 = PEC
     int F = 4;             // grid fields per RHS (4 EFIE, 8 PMCHWT)
     int nspec = 2;         // spectra per frequency (2 EFIE, 7 PMCHWT)
     int64_t nnz = 0;
@@ -191,6 +193,11 @@ struct aimx_ctx {
     int* d_node_w = nullptr;       // [N*U] weight row index i*U+u
     int* d_node_x = nullptr;       // [N*U] caller basis index of that entry
     double* d_diag = nullptr;      // [N][3] static self terms L^A_s, L^Phi_s, K_s
+    double* d_gdiag = nullptr;     // [N] Gram self terms (surface impedance only)
+    // host copies for port definitions (caller order)
+    std::vector<double> h_xyz;     // [nv][3]
+    std::vector<int> h_ea, h_eb, h_tp, h_tm;   // [N] edge vertices, T+ / T-
+    std::vector<double> h_cen;     // [nt][3] triangle centroids
     double* d_q5 = nullptr;        // [25][4] 5 x 5 collapsed Gauss-Legendre rule (l1, l2, l3, w)
 
     aimx::PrecData<float> f32;
@@ -252,8 +259,9 @@ void fft3d_full(T* grid, int batch, const int M[3], bool inverse, cudaStream_t s
 template <class T>
 void ensure_spectra(aimx_ctx* ctx, double freq, cudaStream_t s);
 struct Coefs {
-    // spectral combinations (EFIE uses s[0], s[1]; PMCHWT all) and near coefficients
-    double2 near[6];  // EFIE: aA, aPhi ; PMCHWT: aA, aPhi, aK, bK, bA, bPhi
+    // near-matrix coefficients; EFIE: aA, aPhi, Z_s (Gram, 0 without a surface
+    // impedance); PMCHWT: aA, aPhi, aK, bK, bA, bPhi
+    double2 near[6];
 };
 Coefs near_coefs(const aimx_ctx* ctx, double freq);
 

@@ -39,7 +39,8 @@ static void free_all(aimx_ctx* c) {
                     c->f32.nk,    c->f32.spec,  c->f32.grid,   c->f64.w,    c->f64.na,   c->f64.np,
                     c->f64.nk,    c->f64.spec,  c->f64.grid,   c->d_kgen,   c->d_stage,
                     c->d_xT,      c->d_G,       c->d_S,        c->d_part,   c->d_plane,  c->d_q5,
-                    c->pc.d_ptr,  c->pc.d_idx,  c->pc.d_work,  c->pc.d_inv, c->d_wsoa};
+                    c->pc.d_ptr,  c->pc.d_idx,  c->pc.d_work,  c->pc.d_inv, c->d_wsoa,   c->f32.ng,
+                    c->f64.ng,    c->d_gdiag};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& r : c->prof.recs) {
@@ -390,6 +391,7 @@ int aimx_save_static(const aimx_ctx* ctx, const char* path) {
         wr.val(ctx->mu_out);
         wr.val(ctx->eps_in);
         wr.val(ctx->mu_in);
+        wr.val(ctx->sigma);
         for (int a = 0; a < 3; ++a) wr.val(ctx->h[a]);
         for (int a = 0; a < 3; ++a) wr.val(ctx->origin[a]);
         wr.vec(xyz);
@@ -434,6 +436,7 @@ int aimx_load_static(const char* path, aimx_ctx** out) {
     mat.mu_out = rd.val<double>();
     mat.eps_in = rd.val<double>();
     mat.mu_in = rd.val<double>();
+    mat.sigma = rd.val<double>();
     for (int a = 0; a < 3; ++a) grid.h[a] = rd.val<double>();
     for (int a = 0; a < 3; ++a) grid.origin[a] = rd.val<double>();
     std::vector<double> xyz;

@@ -336,6 +336,11 @@ Coefs near_coefs(const aimx_ctx* ctx, double freq) {
     if (ctx->form == AIMX_EFIE) {
         c.near[0] = jmul(m.w * m.mu[0]);
         c.near[1] = jmul(-m.w * m.mu[0] / (m.k[0] * m.k[0]));
+        if (ctx->sigma > 0) {
+            // surface impedance Z_s = (1 + j) / (sigma delta), delta = sqrt(2 / (w mu0 sigma))
+            const double delta = std::sqrt(2.0 / (m.w * kMu0 * ctx->sigma));
+            c.near[2] = make_double2(1.0 / (ctx->sigma * delta), 1.0 / (ctx->sigma * delta));
+        }
     } else {
         for (int g = 0; g < 2; ++g) {
             c.near[0] = c.near[0] + jmul(m.w * m.mu[g]);

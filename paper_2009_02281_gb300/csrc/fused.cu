@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(kThreads) k_final(const float2* __restrict__ p
             for (int e = row_ptr[i]; e < e1; ++e) {
                 int j = cols[e];
                 float va = __ldg(na + e), vp = __ldg(np + e);
-                float vk = F == 8 ? __ldg(nk + e) : 0.f;
+                float vk = nk ? __ldg(nk + e) : 0.f;   // N^K (two-region) or the Gram matrix (EFIE + SIBC)
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     int bl = lane + 32 * h;
@@ -379,6 +379,8 @@ __global__ void __launch_bounds__(kThreads) k_final(const float2* __restrict__ p
                             rfma(aM[h], va, xm);
                             rfma(pM[h], vp, xm);
                             rfma(kM[h], vk, xm);
+                        } else if (nk) {
+                            rfma(kJ[h], vk, xj);
                         }
                     }
                 }
@@ -388,6 +390,7 @@ __global__ void __launch_bounds__(kThreads) k_final(const float2* __restrict__ p
                 int bl = lane + 32 * h;
                 if (bl < nbc) {
                     float2 e = accE[r][bl] + nc.c[0] * aJ[h] + nc.c[1] * pJ[h];
+                    if (F == 4 && nk) e = e + nc.c[2] * kJ[h];
                     if (F == 8) {
                         e = e + nc.c[2] * kM[h];
                         float2 hh = accH[r][bl] + nc.c[3] * kJ[h] + nc.c[4] * aM[h] + nc.c[5] * pM[h];
@@ -802,7 +805,8 @@ static void run_fused(aimx_ctx* ctx, const NearC& nc, int B, const float2* xb, f
     delete sc;
     sc = scope(ST_FINAL);
     k_final<<<(N + kFinalRows - 1) / kFinalRows, kThreads, 0, s>>>(fb.part, fb.xT, ctx->d_row_ptr, ctx->d_cols,
-                                                                   ctx->f32.na, ctx->f32.np, ctx->f32.nk, ctx->d_perm,
+                                                                   ctx->f32.na, ctx->f32.np,
+                                                                   F == 8 ? ctx->f32.nk : ctx->f32.ng, ctx->d_perm,
                                                                    yb, nc, F, N, nunk, P, B);
     AIMX_CUDA_TRY(cudaGetLastError());
     delete sc;

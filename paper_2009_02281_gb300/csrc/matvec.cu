@@ -134,13 +134,15 @@ __global__ void k_interp_near(const T* __restrict__ w, const int* __restrict__ a
     const C* xb = x + (int64_t)b * nunk;
     C cA = mk((T)nc.c[0].x, (T)nc.c[0].y), cP = mk((T)nc.c[1].x, (T)nc.c[1].y);
     if (F == 4) {
-        C sA = czero<T>(), sP = czero<T>();
+        C sA = czero<T>(), sP = czero<T>(), sG = czero<T>();
         for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
             C xj = xb[perm[cols[e]]];
             rfma(sA, na[e], xj);
             rfma(sP, np[e], xj);
+            if (nk) rfma(sG, nk[e], xj);   // Gram matrix (surface impedance)
         }
         aE = aE + cA * sA + cP * sP;
+        if (nk) aE = aE + mk((T)nc.c[2].x, (T)nc.c[2].y) * sG;
         y[(int64_t)b * nunk + perm[i]] = aE;
     } else {
         C cK = mk((T)nc.c[2].x, (T)nc.c[2].y), dK = mk((T)nc.c[3].x, (T)nc.c[3].y);
@@ -203,7 +205,7 @@ void matvec_generic(aimx_ctx* ctx, double freq, int nrhs, const T* x, T* y, cuda
         fft3d_padded<T>(reinterpret_cast<T*>(grid), nb * F, ctx->M, act, true, s);
         int64_t tn = (int64_t)ctx->N * nb;
         k_interp_near<T><<<(unsigned)((tn + 127) / 128), 128, 0, s>>>(
-            pd.w, ctx->d_anc, ctx->d_perm, ctx->d_row_ptr, ctx->d_cols, pd.na, pd.np, pd.nk, grid,
+            pd.w, ctx->d_anc, ctx->d_perm, ctx->d_row_ptr, ctx->d_cols, pd.na, pd.np, F == 8 ? pd.nk : pd.ng, grid,
             xc + (int64_t)b0 * ctx->nunk, yc + (int64_t)b0 * ctx->nunk, nc, nb, F, ctx->N, ctx->nunk,
             ctx->P, ctx->M[0], ctx->M[1], ctx->M[2]);
         AIMX_CUDA_TRY(cudaGetLastError());

@@ -74,6 +74,7 @@ struct RegionTables {
     double2 cA[2], cP[2];  // per region: multiplier of (N^A + G^A) and of (N^Phi + G^Phi) in the E (or EFIE) rows
     double2 dA[2], dP[2];  // the same in the H rows (two-region form)
     double cK;             // eta0 (K blocks: E-M gets +cK * sum_regions, H-J gets -cK * sum_regions)
+    double2 zs;            // surface impedance multiplying the Gram matrix (EFIE), 0 without
 };
 
 __device__ inline double near_value(const int* row_ptr, const int* cols, const double* vals, int m, int n) {
@@ -141,7 +142,9 @@ __global__ void k_block_assemble(const int* __restrict__ bptr, const int* __rest
             }
         }
         if (form == AIMX_EFIE) {
-            Z[lm * D + ln] = rt.cA[0] * (make_double2(vA, 0) + GA[0]) + rt.cP[0] * (make_double2(vP, 0) + GP[0]);
+            double2 z = rt.cA[0] * (make_double2(vA, 0) + GA[0]) + rt.cP[0] * (make_double2(vP, 0) + GP[0]);
+            if (nk) z = z + near_value(row_ptr, cols, nk, m, n) * rt.zs;   // nk carries the Gram matrix here
+            Z[lm * D + ln] = z;
         } else {
             double2 eJ = make_double2(0, 0), hM = make_double2(0, 0), k = make_double2(0, 0);
             for (int g = 0; g < rt.nreg; ++g) {
@@ -255,6 +258,8 @@ static void region_tables(const aimx_ctx* ctx, double freq, int span, std::vecto
     rt.nreg = nreg;
     rt.span = span;
     rt.cK = kEta0;
+    rt.zs = near_coefs(ctx, freq).near[2];
+    if (ctx->form != AIMX_EFIE) rt.zs = make_double2(0.0, 0.0);
     for (int g = 0; g < nreg; ++g) {
         const double k = w * std::sqrt(mu[g] * eps[g]);
         for (int iz = 0; iz < S; ++iz)
@@ -304,7 +309,8 @@ void precond_block_prepare(aimx_ctx* ctx, double freq, cudaStream_t s) {
     AIMX_CUDA_TRY(cudaMemcpyAsync(dH, H.data(), sizeof(double2) * H.size(), cudaMemcpyHostToDevice, s));
     AIMX_CUDA_TRY(cudaMemcpyAsync(dHg, Hg.data(), sizeof(double2) * Hg.size(), cudaMemcpyHostToDevice, s));
     k_block_assemble<<<nblk, 128, 0, s>>>(ctx->pc.d_ptr, ctx->pc.d_idx, nblk, D, ctx->d_anc, ctx->f64.w, ctx->P,
-                                          ctx->d_row_ptr, ctx->d_cols, ctx->f64.na, ctx->f64.np, ctx->f64.nk, dH, dHg,
+                                          ctx->d_row_ptr, ctx->d_cols, ctx->f64.na, ctx->f64.np,
+                                          ctx->form == AIMX_EFIE ? ctx->f64.ng : ctx->f64.nk, dH, dHg,
                                           rt, ctx->form, ctx->pc.d_work);
     AIMX_CUDA_TRY(cudaGetLastError());
     k_block_invert<<<nb_(nblk, 64), 64, 0, s>>>(ctx->pc.d_work, ctx->pc.d_inv, nblk, D);

@@ -283,6 +283,43 @@ __global__ void k_precorrect(const double* w, const int* anc, const int* row_of,
     NK32[e] = (float)nk;
 }
 
+// Surface-impedance Gram matrix on the near pattern: G_mn = int f_m . f_n dS over
+// the triangles m and n share (a degree-2 integrand; the 5 x 5 collapsed rule
+// q5 is exact).  Internal order; also the self terms into gdiag.
+__global__ void k_gram(GeomView g, const int* __restrict__ row_of, const int* __restrict__ cols, int64_t nnz,
+                       const double* __restrict__ q5, double* __restrict__ ng, double* __restrict__ gdiag) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= nnz) return;
+    const int m = row_of[e], n = cols[e];
+    double acc = 0.0;
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+            const int t = g.btri[2 * m + a];
+            if (t != g.btri[2 * n + b]) continue;
+            const double sm = a ? -1.0 : 1.0, sn = b ? -1.0 : 1.0;
+            const double cm = g.blen[m] / (2.0 * g.area[t]), cn = g.blen[n] / (2.0 * g.area[t]);
+            const double* pm = g.xyz + 3 * g.bfree[2 * m + a];
+            const double* pn = g.xyz + 3 * g.bfree[2 * n + b];
+            const int* tv = g.tri + 3 * t;
+            const double* v0 = g.xyz + 3 * tv[0];
+            const double* v1 = g.xyz + 3 * tv[1];
+            const double* v2 = g.xyz + 3 * tv[2];
+            double s = 0.0;
+            for (int k = 0; k < 25; ++k) {
+                const double l1 = q5[4 * k], l2 = q5[4 * k + 1], l3 = q5[4 * k + 2], wq = q5[4 * k + 3];
+                double d = 0.0;
+                for (int c = 0; c < 3; ++c) {
+                    const double r = l1 * v0[c] + l2 * v1[c] + l3 * v2[c];
+                    d += (r - pm[c]) * (r - pn[c]);
+                }
+                s += wq * d;
+            }
+            acc += sm * sn * cm * cn * g.area[t] * s;
+        }
+    ng[e] = acc;
+    if (m == n) gdiag[m] = acc;
+}
+
 // field-major FP32 copy of the weights, ws[f][u][i] = w[i][u][f] (coalesced per-plane interpolation)
 __global__ void k_weights_soa(const double* __restrict__ w, float* __restrict__ ws, int N, int U) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -325,6 +362,19 @@ static int next_pow2(int v) {
     return p;
 }
 
+// Gram values on the near pattern (FP64 and FP32) and their self terms, when a surface impedance is set
+static void build_gram(aimx_ctx* ctx, const GeomView& gv, const int* d_row_of) {
+    if (!(ctx->sigma > 0)) return;
+    const int64_t nnz = ctx->nnz;
+    ctx->f64.ng = (double*)dev_alloc(ctx, sizeof(double) * nnz);
+    ctx->f32.ng = (float*)dev_alloc(ctx, sizeof(float) * nnz);
+    ctx->d_gdiag = (double*)dev_alloc(ctx, sizeof(double) * ctx->N);
+    k_gram<<<(unsigned)((nnz + 127) / 128), 128>>>(gv, d_row_of, ctx->d_cols, nnz, ctx->d_q5, ctx->f64.ng,
+                                                   ctx->d_gdiag);
+    k_to_float<<<(unsigned)((nnz + 255) / 256), 256>>>(ctx->f64.ng, ctx->f32.ng, (size_t)nnz);
+    AIMX_CUDA_TRY(cudaGetLastError());
+}
+
 void setup_context(aimx_ctx* ctx, const aimx_mesh* mesh, const aimx_material* mat,
                    const aimx_grid* grid, int order, const StaticData* pre) {
     if (!mesh || !mat || !grid || !mesh->xyz || !mesh->tri || mesh->nv < 3 || mesh->nt < 1)
@@ -339,6 +389,7 @@ void setup_context(aimx_ctx* ctx, const aimx_mesh* mesh, const aimx_material* ma
     ctx->mu_out = mat->mu_out > 0 ? mat->mu_out : 1.0;
     ctx->eps_in = mat->eps_in > 0 ? mat->eps_in : 1.0;
     ctx->mu_in = mat->mu_in > 0 ? mat->mu_in : 1.0;
+    ctx->sigma = (mat->formulation == AIMX_EFIE && mat->sigma > 0) ? mat->sigma : 0.0;
     ctx->order = order;
     ctx->P = order + 1;
     ctx->U = ctx->P * ctx->P * ctx->P;
@@ -385,7 +436,7 @@ void setup_context(aimx_ctx* ctx, const aimx_mesh* mesh, const aimx_material* ma
     std::stable_sort(he.begin(), he.end(), [](const HalfEdge& x, const HalfEdge& y) {
         return x.a != y.a ? x.a < y.a : x.b < y.b;
     });
-    std::vector<int> tp, tm, pp, pm;
+    std::vector<int> tp, tm, pp, pm, ea, eb;
     std::vector<double> blen;
     for (size_t s = 0; s < he.size();) {
         size_t e = s;
@@ -405,6 +456,8 @@ void setup_context(aimx_ctx* ctx, const aimx_mesh* mesh, const aimx_material* ma
             };
             tp.push_back(tplus);
             tm.push_back(tminus);
+            ea.push_back(he[s].a);
+            eb.push_back(he[s].b);
             pp.push_back(freev(tplus));
             pm.push_back(freev(tminus));
             const double* A = &xyz[3 * he[s].a];
@@ -417,6 +470,12 @@ void setup_context(aimx_ctx* ctx, const aimx_mesh* mesh, const aimx_material* ma
     const int N = (int)tp.size();
     if (N == 0) throw Error{AIMX_E_MESH, "mesh has no interior edge"};
     ctx->N = N;
+    ctx->h_xyz = xyz;
+    ctx->h_ea = ea;
+    ctx->h_eb = eb;
+    ctx->h_tp = tp;
+    ctx->h_tm = tm;
+    ctx->h_cen = cen;
     ctx->nunk = ctx->form == AIMX_EFIE ? N : 2 * N;
 
     // grid
@@ -625,6 +684,7 @@ void setup_context(aimx_ctx* ctx, const aimx_mesh* mesh, const aimx_material* ma
         put(pre->np, ctx->f64.np, ctx->f32.np);
         put(pre->nk, ctx->f64.nk, ctx->f32.nk);
         ctx->d_diag = upload(ctx, pre->diag);
+        build_gram(ctx, gv, d_row_of);
         AIMX_CUDA_TRY(cudaDeviceSynchronize());
         dev_free(ctx, d_row_of);
         return;
@@ -678,6 +738,7 @@ void setup_context(aimx_ctx* ctx, const aimx_mesh* mesh, const aimx_material* ma
     ctx->d_diag = (double*)dev_alloc(ctx, sizeof(double) * 3 * (size_t)N);
     k_diag<<<(N + 127) / 128, 128>>>(ctx->d_row_ptr, ctx->d_cols, d_LA, d_LP, d_KK, N, ctx->d_diag);
     AIMX_CUDA_TRY(cudaGetLastError());
+    build_gram(ctx, gv, d_row_of);
     AIMX_CUDA_TRY(cudaDeviceSynchronize());
     dev_free(ctx, d_LA);
     dev_free(ctx, d_LP);

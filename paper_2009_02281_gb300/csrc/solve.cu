@@ -171,14 +171,16 @@ __global__ void k_f32_to_f64(const float2* __restrict__ a, double2* b, int64_t n
 }
 
 // inverse of the static self block of every basis (internal -> caller order)
-__global__ void k_build_precond(const double* __restrict__ diag, const int* __restrict__ perm, double2* minv, int N,
-                                int form, double2 aA, double2 aP, double2 aK, double2 bK, double2 bA, double2 bP) {
+__global__ void k_build_precond(const double* __restrict__ diag, const double* __restrict__ gdiag,
+                                const int* __restrict__ perm, double2* minv, int N, int form, double2 aA, double2 aP,
+                                double2 aK, double2 bK, double2 bA, double2 bP) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const double la = diag[3 * i], lp = diag[3 * i + 1], kk = diag[3 * i + 2];
     const int o = perm[i];
     if (form == AIMX_EFIE) {
         double2 d = la * aA + lp * aP;
+        if (gdiag) d = d + gdiag[i] * aK;   // surface impedance: aK holds Z_s
         double den = d.x * d.x + d.y * d.y;
         minv[o] = den > 0 ? make_double2(d.x / den, -d.y / den) : make_double2(1.0, 0.0);
     } else {
@@ -198,7 +200,7 @@ static inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t -
 
 void build_diag_inverse(aimx_ctx* ctx, double freq, double2* minv, cudaStream_t s) {
     Coefs cf = near_coefs(ctx, freq);
-    k_build_precond<<<nblk(ctx->N), 256, 0, s>>>(ctx->d_diag, ctx->d_perm, minv, ctx->N, ctx->form, cf.near[0],
+    k_build_precond<<<nblk(ctx->N), 256, 0, s>>>(ctx->d_diag, ctx->d_gdiag, ctx->d_perm, minv, ctx->N, ctx->form, cf.near[0],
                                                  cf.near[1], cf.near[2], cf.near[3], cf.near[4], cf.near[5]);
     AIMX_CUDA_TRY(cudaGetLastError());
 }
@@ -343,7 +345,7 @@ extern "C" int aimx_solve(aimx_ctx* ctx, double freq, int nrhs, const void* bdev
             AIMX_CUDA_TRY(cudaMemcpyAsync(W.minv, one.data(), sizeof(double2) * one.size(), cudaMemcpyHostToDevice, s));
             AIMX_CUDA_TRY(cudaStreamSynchronize(s));
         } else {
-            k_build_precond<<<nblk(N), 256, 0, s>>>(ctx->d_diag, ctx->d_perm, W.minv, N, ctx->form, cf.near[0],
+            k_build_precond<<<nblk(N), 256, 0, s>>>(ctx->d_diag, ctx->d_gdiag, ctx->d_perm, W.minv, N, ctx->form, cf.near[0],
                                                      cf.near[1], cf.near[2], cf.near[3], cf.near[4], cf.near[5]);
             AIMX_CUDA_TRY(cudaGetLastError());
         }
@@ -773,7 +775,7 @@ extern "C" int aimx_precond_apply(aimx_ctx* ctx, double freq, int precond, int n
                 AIMX_CUDA_TRY(cudaMemcpy(minv, one.data(), sizeof(double2) * one.size(), cudaMemcpyHostToDevice));
             } else {
                 Coefs cf = near_coefs(ctx, freq);
-                k_build_precond<<<nblk(N), 256, 0, s>>>(ctx->d_diag, ctx->d_perm, minv, N, ctx->form, cf.near[0],
+                k_build_precond<<<nblk(N), 256, 0, s>>>(ctx->d_diag, ctx->d_gdiag, ctx->d_perm, minv, N, ctx->form, cf.near[0],
                                                          cf.near[1], cf.near[2], cf.near[3], cf.near[4], cf.near[5]);
             }
             k_precond<double><<<nblk((int64_t)N * nrhs), 256, 0, s>>>((const double2*)v, (double2*)z, minv, N, nunk,

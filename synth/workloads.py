@@ -12,6 +12,11 @@ stand in for the paper's geometries, which are not available.
   (20480 triangles, 30720 RWG, two-region formulation with 61440 unknowns),
   diameter = 3 free-space wavelengths (f = 1.5 c Hz, about 449.7 MHz), 64^3 grid padded to
   128^3, order 2, near radius 3, 64 right-hand sides, FP32 matvec.
+* ``conductor_bars``: 8 parallel copper bars (sigma = 5.8e7 S/m, surface
+  impedance) of 1000 x 10 x 5 um with 10 um gaps in eps_r = 3.5, structured
+  mesh with 3.2 um cells along the bars (75k unknowns), one delta-gap port at
+  the middle of each bar, a 256 x 16 x 8 grid (padded 512 x 32 x 16), 100
+  log-spaced frequencies from 1 MHz to 100 GHz.
 * ``uneven_batch``: seeded mix of PEC (EFIE) and dielectric (eps_r ~ U[2, 6],
   two-region) spheres, boxes and tori of size U[0.5, 4] free-space wavelengths
   at f = c (wavelength 1 m), meshed for a log-uniform 2k-60k unknowns, each
@@ -38,6 +43,27 @@ def dielectric_sphere_61440(nrhs=64):
     return dict(name="dielectric_sphere_61440", xyz=xyz, tri=tri, formulation="pmchwt", eps_out=1.0,
                 eps_in=4.0, grid_n=(64, 64, 64), order=2, radius=3, freq=1.5 * C0, nrhs=nrhs,
                 precision="f32")
+
+
+def conductor_bars(nbars=8, length=1000e-6, width=10e-6, thickness=5e-6, gap=10e-6, divisions=(312, 3, 2)):
+    """Parallel copper bars in a dielectric: the sweep workload (inputs only).
+
+    Bars along x, side by side in y with ``gap`` between them, meshed as
+    structured boxes (an even x division puts a vertex line at the middle,
+    where each bar's delta-gap port sits).  Returns the merged mesh, the port
+    definitions (point, normal, box_lo, box_hi) and the sweep settings."""
+    from .meshes import merge_meshes
+    parts, ports = [], []
+    for i in range(nbars):
+        y0 = i * (width + gap)
+        parts.append(box([0.0, y0, 0.0], [length, y0 + width, thickness], list(divisions)))
+        eps = 0.25 * gap
+        ports.append(([0.5 * length, 0.0, 0.0], [1.0, 0.0, 0.0], [-eps, y0 - eps, -eps],
+                      [length + eps, y0 + width + eps, thickness + eps]))
+    xyz, tri, _ = merge_meshes(parts)
+    return dict(name="conductor_bars_%d" % nbars, xyz=xyz, tri=tri, formulation="efie", eps_out=3.5, eps_in=None,
+                sigma=5.8e7, grid_n=(256, 16, 8), order=2, radius=3, ports=ports,
+                freqs=np.logspace(6, 11, 100), precision="f32")
 
 
 def _pow2_nodes(extent, h, order=2):

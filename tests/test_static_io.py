@@ -40,7 +40,7 @@ def _tiny_file(good_sum=True):
     """A well-formed header for a one-triangle 'mesh' with consistent array sizes."""
     nv, nt, form, order, n, radius, N, nnz = 3, 1, 0, 1, (4, 4, 4), 3, 1, 1
     body = struct.pack("<8i", 1, nv, nt, form, order, *n) + struct.pack("<ii", radius, N) + struct.pack("<q", nnz)
-    body += struct.pack("<4d", 1.0, 1.0, 1.0, 1.0) + struct.pack("<6d", 1, 1, 1, 0, 0, 0)
+    body += struct.pack("<5d", 1.0, 1.0, 1.0, 1.0, 0.0) + struct.pack("<6d", 1, 1, 1, 0, 0, 0)
     U = (order + 1) ** 3
     body += np.zeros(3 * nv).tobytes() + np.array([0, 1, 2], dtype=np.int32).tobytes()
     body += np.zeros(N * U * 4).tobytes() + np.zeros(3 * nnz).tobytes() + np.zeros(3 * N).tobytes()
