@@ -195,6 +195,47 @@ def measure_solves(ctx, wl, args):
     return out
 
 
+def measure_config1(args, ws):
+    """The 1920-unknown PEC sphere in FP64 (latency-bound): one-RHS product latency and the
+    plane-wave solve to 1e-6 (FP64 products inside GMRES), wall time per solve."""
+    import torch
+    from synth import workloads, planewave_batch
+    from paper_2009_02281_gb300 import Context, EFIE, F64
+    wl = workloads.pec_sphere_1920()
+    t0 = time.time()
+    ctx = Context(wl["xyz"], wl["tri"], wl["grid_n"], order=wl["order"], formulation=EFIE, near_radius=wl["radius"])
+    torch.cuda.synchronize()
+    setup_s = time.time() - t0
+    f = wl["freq"]
+    stream = torch.cuda.current_stream()
+    x = torch.ones((1, ctx.nunk), dtype=torch.complex128, device="cuda")
+    y = torch.empty_like(x)
+    for _ in range(5):
+        ctx.matvec(f, x, y)
+    torch.cuda.synchronize()
+    reps = 50
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        ctx.matvec(f, x, y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    us = 1e3 * e0.elapsed_time(e1) / reps
+    b = ctx.rhs_planewave(f, [[0.0, 0.0, 1.0]], [[1.0, 0.0, 0.0]])
+    ctx.solve(f, b, tol=1e-6, inner_precision=F64)     # warm-up
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    nsol = 5
+    for _ in range(nsol):
+        _, st, rc = ctx.solve(f, b, tol=1e-6, inner_precision=F64)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t) / nsol
+    ctx.close()
+    return {"workload": "pec_sphere_1920", "setup_s": round(setup_s, 3), "fp64_matvec_us": round(us, 1),
+            "solve_ms": round(1e3 * dt, 2), "solves_per_s": round(ws / dt, 2), "iterations": st[0]["iterations"],
+            "rel_residual": st[0]["rel_residual"], "status": rc}
+
+
 def measure_batch(args, ws):
     """The first args.batch_members members of the seeded uneven batch (spheres, boxes,
     tori; PEC and dielectric; 4 RHS each): one captured graph per call versus the
@@ -396,6 +437,8 @@ def run_ours(args):
     if args.batch_members > 0:
         ctx.close()
         out["uneven_batch"] = measure_batch(args, ws)
+    if not args.no_config1:
+        out["pec_sphere_1920"] = measure_config1(args, ws)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl, args.cpu_rows)
     if rank == 0:
@@ -481,6 +524,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solves", action="store_true", help="skip the batched solve measurement")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 product measurement")
+    ap.add_argument("--no-config1", action="store_true", help="skip the 1920-unknown FP64 latency measurement")
     ap.add_argument("--batch-members", type=int, default=16,
                     help="members of the seeded uneven batch to time (0 = skip; 48 = the full batch)")
     ap.add_argument("--path", type=int, default=0, choices=[0, 1], help="FP32 product path (aimx_set_path)")

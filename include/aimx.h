@@ -190,10 +190,14 @@ typedef struct {
 /* Solve A(k) x = b for nrhs right-hand sides in lockstep (the iterative GMRES
  * solve of Sec. V): cycles of right-preconditioned GMRES(restart) with FP64
  * Krylov vectors (classical Gram-Schmidt applied twice) and FP32 (or FP64)
- * AIMx products, each cycle started from the FP64 true residual b - A x
- * (iterative refinement).  b, x: device [nrhs][nunk] complex128 (double2),
- * caller-owned; stats: host array [nrhs] or NULL.  Returns AIMX_E_NOCONV (> 0)
- * when any right-hand side misses tol.  Synchronises stream. */
+ * AIMx products, each cycle started from the true residual b - A x
+ * (iterative refinement).  With FP32 inner products and tol >= 1e-5 the
+ * intermediate true residuals use the FP32 product (its ~1e-6 relative error
+ * is far below the target); convergence is always confirmed, and
+ * stats.rel_residual always computed, with the FP64 product.  b, x: device
+ * [nrhs][nunk] complex128 (double2), caller-owned; stats: host array [nrhs] or
+ * NULL.  Returns AIMX_E_NOCONV (> 0) when any right-hand side misses tol.
+ * Synchronises stream. */
 int aimx_solve(aimx_ctx* ctx, double freq, int nrhs, const void* b, void* x, const aimx_solve_opts* opts,
                aimx_solve_stats* stats, void* stream);
 

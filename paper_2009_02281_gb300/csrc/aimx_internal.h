@@ -82,6 +82,9 @@ enum Stage {
     ST_G_MIX,
     ST_G_INTERP,
     ST_SOLVE_BLAS,
+    ST_SOLVE_RESIDUAL,
+    ST_SOLVE_PRECOND,
+    ST_SOLVE_REORTH,
     ST_COUNT
 };
 

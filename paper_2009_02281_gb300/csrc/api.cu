@@ -79,7 +79,8 @@ StageScope::~StageScope() {
 static const char* kStageNames[ST_COUNT] = {
     "kernel_spectra", "transpose_x", "gather_projection", "xy_fft_forward", "z_fft_mix_inverse",
     "xy_fft_inverse_interp", "near_final", "generic_projection", "generic_fft", "generic_mix",
-    "generic_interp_near", "solver_vector_ops"};
+    "generic_interp_near", "solver_vector_ops", "solver_true_residual", "solver_precond",
+    "solver_reorthogonalization"};
 
 }  // namespace aimx
 

@@ -65,16 +65,82 @@ __global__ void k_dots(const double2* __restrict__ V, const double2* __restrict_
     (void)nvec;
 }
 
+// Segmented form of k_dots for the Arnoldi step: block (segment s, rhs b) holds
+// its kDotSeg entries of w in registers (kDotSeg / 256 per thread) and streams
+// the Krylov vectors four at a time, so w is read once per pass instead of once
+// per vector; each warp writes its partial sums to
+// part[((b * nseg + s) * 8 + warp) * ldp + i] (no block barriers; the final
+// reduction runs in a fixed order, so the result is deterministic).
+constexpr int kDotSeg = 2048;
+constexpr int kDotPer = kDotSeg / 256;
+
+__global__ void __launch_bounds__(256) k_dots_seg(const double2* __restrict__ V, const double2* __restrict__ w,
+                                                  double2* part, int nunk, int64_t vstride, int nvec, int nseg,
+                                                  int ldp) {
+    const int sg = blockIdx.x, b = blockIdx.y;
+    const int n0 = sg * kDotSeg;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double2 xr[kDotPer];
+#pragma unroll
+    for (int k = 0; k < kDotPer; ++k) {
+        const int n = n0 + threadIdx.x + 256 * k;
+        xr[k] = n < nunk ? w[(int64_t)b * nunk + n] : make_double2(0.0, 0.0);
+    }
+    double2* pw = part + (((int64_t)b * nseg + sg) * 8 + wid) * ldp;
+    for (int i0 = 0; i0 < nvec; i0 += 4) {
+        double re[4] = {0, 0, 0, 0}, im[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            if (i0 + t >= nvec) break;
+            const double2* v = V + b * vstride + (int64_t)(i0 + t) * nunk;
+#pragma unroll
+            for (int k = 0; k < kDotPer; ++k) {
+                const int n = n0 + threadIdx.x + 256 * k;
+                if (n < nunk) {
+                    const double2 a = v[n];
+                    re[t] += a.x * xr[k].x + a.y * xr[k].y;
+                    im[t] += a.x * xr[k].y - a.y * xr[k].x;
+                }
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+            for (int o = 16; o > 0; o >>= 1) {
+                re[t] += __shfl_down_sync(0xffffffffu, re[t], o);
+                im[t] += __shfl_down_sync(0xffffffffu, im[t], o);
+            }
+        if (lane == 0)
+            for (int t = 0; t < 4 && i0 + t < nvec; ++t) pw[i0 + t] = make_double2(re[t], im[t]);
+    }
+}
+
+// h[b * ldh + i] = sum over segments and warps of part[((b * nseg + s) * 8 + warp) * ldp + i]
+__global__ void k_dots_fin(const double2* __restrict__ part, double2* h, int nvec, int nseg, int ldp, int ldh) {
+    const int b = blockIdx.x;
+    for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
+        double2 t = make_double2(0.0, 0.0);
+        for (int q = 0; q < nseg * 8; ++q) t = t + part[((int64_t)b * nseg * 8 + q) * ldp + i];
+        h[b * ldh + i] = t;
+    }
+}
+
 // w[b] -= sum_{i < nvec} h[b][i] V[b][i]
 __global__ void k_subtract(const double2* __restrict__ V, double2* w, const double2* __restrict__ h, int nunk,
                            int64_t vstride, int ldh, int nvec, int nrhs) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= (int64_t)nunk * nrhs) return;
     const int b = (int)(t / nunk), n = (int)(t % nunk);
-    double2 acc = w[t];
+    // two independent accumulators (even / odd vectors) halve the dependent FP64 FMA chain
+    double2 acc0 = w[t], acc1 = make_double2(0.0, 0.0);
     const double2* v = V + b * vstride + n;
-    for (int i = 0; i < nvec; ++i) acc = acc - h[b * ldh + i] * v[(int64_t)i * nunk];
-    w[t] = acc;
+    const double2* hb = h + b * ldh;
+    int i = 0;
+    for (; i + 1 < nvec; i += 2) {
+        acc0 = acc0 - hb[i] * v[(int64_t)i * nunk];
+        acc1 = acc1 - hb[i + 1] * v[(int64_t)(i + 1) * nunk];
+    }
+    if (i < nvec) acc0 = acc0 - hb[i] * v[(int64_t)i * nunk];
+    w[t] = acc0 + acc1;
 }
 
 // y[b] = sum_{i < nvec} c[b][i] V[b][i]
@@ -163,6 +229,11 @@ __global__ void k_precond_inplace(double2* v, const double2* __restrict__ minv, 
         vb[i] = m[0] * a + m[1] * c;
         vb[N + i] = m[2] * a + m[3] * c;
     }
+}
+
+__global__ void k_f64_to_f32(const double2* __restrict__ a, float2* b, int64_t n) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t < n) b[t] = make_float2((float)a[t].x, (float)a[t].y);
 }
 
 __global__ void k_f32_to_f64(const float2* __restrict__ a, double2* b, int64_t n) {
@@ -322,6 +393,9 @@ extern "C" int aimx_solve(aimx_ctx* ctx, double freq, int nrhs, const void* bdev
         W.h = (double2*)alloc(sizeof(double2) * (size_t)nrhs * (m + 1));
         h2 = (double2*)alloc(sizeof(double2) * (size_t)nrhs * (m + 1));
         W.nrm = (double*)alloc(sizeof(double) * nrhs);
+        const int nseg = (nunk + kDotSeg - 1) / kDotSeg;
+        double2* dpart = (double2*)alloc(sizeof(double2) * (size_t)nrhs * nseg * 8 * (m + 1));
+        double* dnrm0 = (double*)alloc(sizeof(double) * nrhs);
         W.active = (int*)alloc(sizeof(int) * nrhs);
         W.minv = (double2*)alloc(sizeof(double2) * 4 * (size_t)N);
         double* dscale = (double*)alloc(sizeof(double) * nrhs);
@@ -349,31 +423,51 @@ extern "C" int aimx_solve(aimx_ctx* ctx, double freq, int nrhs, const void* bdev
                                                      cf.near[1], cf.near[2], cf.near[3], cf.near[4], cf.near[5]);
             AIMX_CUDA_TRY(cudaGetLastError());
         }
-        std::vector<double> bnorm(nrhs), rnorm(nrhs), hn(nrhs);
+        std::vector<double> bnorm(nrhs), rnorm(nrhs), hn(nrhs), hn0(nrhs);
         k_norms<<<nrhs, 256, 0, s>>>(b, W.nrm, nunk, nunk);
         AIMX_CUDA_TRY(cudaMemcpyAsync(bnorm.data(), W.nrm, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
         if (!o.use_x0) AIMX_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double2) * nv, s));
         AIMX_CUDA_TRY(cudaStreamSynchronize(s));
         std::vector<int> iters(nrhs, 0), refs(nrhs, 0), act(nrhs, 1);
         std::vector<double> relres(nrhs, 1.0);
-        auto true_residual = [&]() {
-            matvec_generic<double>(ctx, freq, nrhs, (const double*)x, (double*)W.w, s);
+        // Intermediate true residuals may use the FP32 product when the inner products are FP32
+        // and the target is >= 1e-5 (the FP32 product's relative error, ~1e-6, is then far below
+        // it); convergence is always confirmed, and the reported residual computed, in FP64.
+        bool low = o.inner_precision == AIMX_F32 && o.tol >= 1e-5;
+        auto true_residual = [&](bool use32) {
+            StageScope sc(ctx, ST_SOLVE_RESIDUAL, s);
+            if (use32) {
+                k_f64_to_f32<<<nblk(nv), 256, 0, s>>>(x, (float2*)W.z, nv);
+                matvec_any(ctx, freq, nrhs, W.z, W.az, AIMX_F32, s);
+                k_f32_to_f64<<<nblk(nv), 256, 0, s>>>((const float2*)W.az, W.w, nv);
+            } else {
+                matvec_generic<double>(ctx, freq, nrhs, (const double*)x, (double*)W.w, s);
+            }
             k_residual<<<nblk(nv), 256, 0, s>>>(b, W.w, W.r, nv);
             k_norms<<<nrhs, 256, 0, s>>>(W.r, W.nrm, nunk, nunk);
             AIMX_CUDA_TRY(cudaMemcpyAsync(rnorm.data(), W.nrm, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
             AIMX_CUDA_TRY(cudaStreamSynchronize(s));
             for (int k = 0; k < nrhs; ++k) relres[k] = bnorm[k] > 0 ? rnorm[k] / bnorm[k] : 0.0;
         };
-        true_residual();
+        true_residual(low);
         std::vector<HostGmres> hg(nrhs);
         std::vector<double2> hb1((size_t)nrhs * (m + 1)), hb2((size_t)nrhs * (m + 1));
         std::vector<double> scale(nrhs);
         std::vector<double2> coef((size_t)nrhs * (m + 1));
         for (int ref = 0; ref < o.max_refine; ++ref) {
-            int nact = 0;
-            for (int k = 0; k < nrhs; ++k) {
-                act[k] = (relres[k] > o.tol && iters[k] < o.max_iter && std::isfinite(relres[k])) ? 1 : 0;
-                nact += act[k];
+            auto count_active = [&]() {
+                int c = 0;
+                for (int k = 0; k < nrhs; ++k) {
+                    act[k] = (relres[k] > o.tol && iters[k] < o.max_iter && std::isfinite(relres[k])) ? 1 : 0;
+                    c += act[k];
+                }
+                return c;
+            };
+            int nact = count_active();
+            if (!nact && low) {   // confirm in FP64 before stopping
+                low = false;
+                true_residual(false);
+                nact = count_active();
             }
             if (!nact) break;
             AIMX_CUDA_TRY(cudaMemcpyAsync(W.active, act.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, s));
@@ -396,6 +490,7 @@ extern "C" int aimx_solve(aimx_ctx* ctx, double freq, int nrhs, const void* bdev
                 // w = A M v_j
                 const double2* vj = W.V + (int64_t)j * nunk;
                 if (o.inner_precision == AIMX_F32) {
+                    StageScope* pcs = new StageScope(ctx, ST_SOLVE_PRECOND, s);
                     if (block)
                         precond_block_apply<float>(ctx, vj, vstride, (float2*)W.z, nrhs, s);
                     else if (learned)
@@ -403,6 +498,7 @@ extern "C" int aimx_solve(aimx_ctx* ctx, double freq, int nrhs, const void* bdev
                     else
                         k_precond<float><<<nblk((int64_t)N * nrhs), 256, 0, s>>>(vj, (float2*)W.z, W.minv, N, nunk,
                                                                                    nrhs, ctx->form, vstride);
+                    delete pcs;
                     matvec_any(ctx, freq, nrhs, W.z, W.az, AIMX_F32, s);
                     k_f32_to_f64<<<nblk(nv), 256, 0, s>>>((const float2*)W.az, W.w, nv);
                 } else {
@@ -415,18 +511,38 @@ extern "C" int aimx_solve(aimx_ctx* ctx, double freq, int nrhs, const void* bdev
                                                                                     nunk, nrhs, ctx->form, vstride);
                     matvec_any(ctx, freq, nrhs, W.z, W.w, AIMX_F64, s);
                 }
-                // CGS2 against v_0 .. v_j
-                dim3 gd(j + 1, nrhs);
-                k_dots<<<gd, 256, 0, s>>>(W.V, W.w, W.h, nunk, vstride, m + 1, j + 1);
+                // Classical Gram-Schmidt against v_0 .. v_j, FP64, with a second pass whenever
+                // the first cancels more than 1 - 1/sqrt(2) of the norm of w for any active
+                // right-hand side (the Daniel-Gragg-Kaufman-Stewart criterion: "twice is enough")
+                StageScope* bls = new StageScope(ctx, ST_SOLVE_BLAS, s);
+                const dim3 gd(nseg, nrhs);
+                k_norms<<<nrhs, 256, 0, s>>>(W.w, dnrm0, nunk, nunk);
+                k_dots_seg<<<gd, 256, 0, s>>>(W.V, W.w, dpart, nunk, vstride, j + 1, nseg, m + 1);
+                k_dots_fin<<<nrhs, 128, 0, s>>>(dpart, W.h, j + 1, nseg, m + 1, m + 1);
                 k_subtract<<<nblk(nv), 256, 0, s>>>(W.V, W.w, W.h, nunk, vstride, m + 1, j + 1, nrhs);
-                k_dots<<<gd, 256, 0, s>>>(W.V, W.w, h2, nunk, vstride, m + 1, j + 1);
-                k_subtract<<<nblk(nv), 256, 0, s>>>(W.V, W.w, h2, nunk, vstride, m + 1, j + 1, nrhs);
                 k_norms<<<nrhs, 256, 0, s>>>(W.w, W.nrm, nunk, nunk);
                 AIMX_CUDA_TRY(cudaGetLastError());
                 AIMX_CUDA_TRY(cudaMemcpyAsync(hb1.data(), W.h, sizeof(double2) * hb1.size(), cudaMemcpyDeviceToHost, s));
-                AIMX_CUDA_TRY(cudaMemcpyAsync(hb2.data(), h2, sizeof(double2) * hb2.size(), cudaMemcpyDeviceToHost, s));
+                AIMX_CUDA_TRY(cudaMemcpyAsync(hn0.data(), dnrm0, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
                 AIMX_CUDA_TRY(cudaMemcpyAsync(hn.data(), W.nrm, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
                 AIMX_CUDA_TRY(cudaStreamSynchronize(s));
+                bool again = false;
+                for (int k = 0; k < nrhs; ++k)
+                    if (!done[k] && hn[k] < 0.7071067811865476 * hn0[k]) again = true;
+                if (again) {
+                    StageScope rs(ctx, ST_SOLVE_REORTH, s);
+                    k_dots_seg<<<gd, 256, 0, s>>>(W.V, W.w, dpart, nunk, vstride, j + 1, nseg, m + 1);
+                    k_dots_fin<<<nrhs, 128, 0, s>>>(dpart, h2, j + 1, nseg, m + 1, m + 1);
+                    k_subtract<<<nblk(nv), 256, 0, s>>>(W.V, W.w, h2, nunk, vstride, m + 1, j + 1, nrhs);
+                    k_norms<<<nrhs, 256, 0, s>>>(W.w, W.nrm, nunk, nunk);
+                    AIMX_CUDA_TRY(cudaGetLastError());
+                    AIMX_CUDA_TRY(cudaMemcpyAsync(hb2.data(), h2, sizeof(double2) * hb2.size(), cudaMemcpyDeviceToHost, s));
+                    AIMX_CUDA_TRY(cudaMemcpyAsync(hn.data(), W.nrm, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+                    AIMX_CUDA_TRY(cudaStreamSynchronize(s));
+                } else {
+                    std::fill(hb2.begin(), hb2.end(), make_double2(0, 0));
+                }
+                delete bls;
                 jlast = j + 1;
                 int ndone = 0;
                 for (int k = 0; k < nrhs; ++k) {
@@ -470,8 +586,9 @@ extern "C" int aimx_solve(aimx_ctx* ctx, double freq, int nrhs, const void* bdev
                 k_add_masked<<<nblk(nv), 256, 0, s>>>(x, W.d, W.active, nunk, nrhs);
             }
             AIMX_CUDA_TRY(cudaGetLastError());
-            true_residual();
+            true_residual(low);
         }
+        if (low) true_residual(false);   // reported residuals always from the FP64 product
         bool allok = true;
         for (int k = 0; k < nrhs; ++k) {
             bool ok = relres[k] <= o.tol;
