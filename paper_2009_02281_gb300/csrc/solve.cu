@@ -269,6 +269,17 @@ __global__ void k_build_precond(const double* __restrict__ diag, const double* _
 
 static inline unsigned nblk(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
+static int num_sms_solve() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+            n = 1;
+    }
+    return n;
+}
+
 void build_diag_inverse(aimx_ctx* ctx, double freq, double2* minv, cudaStream_t s) {
     Coefs cf = near_coefs(ctx, freq);
     k_build_precond<<<nblk(ctx->N), 256, 0, s>>>(ctx->d_diag, ctx->d_gdiag, ctx->d_perm, minv, ctx->N, ctx->form, cf.near[0],
@@ -396,6 +407,7 @@ extern "C" int aimx_solve(aimx_ctx* ctx, double freq, int nrhs, const void* bdev
         const int nseg = (nunk + kDotSeg - 1) / kDotSeg;
         double2* dpart = (double2*)alloc(sizeof(double2) * (size_t)nrhs * nseg * 8 * (m + 1));
         double* dnrm0 = (double*)alloc(sizeof(double) * nrhs);
+        const bool selective = nv >= ((int64_t)1 << 20);
         W.active = (int*)alloc(sizeof(int) * nrhs);
         W.minv = (double2*)alloc(sizeof(double2) * 4 * (size_t)N);
         double* dscale = (double*)alloc(sizeof(double) * nrhs);
@@ -513,34 +525,56 @@ extern "C" int aimx_solve(aimx_ctx* ctx, double freq, int nrhs, const void* bdev
                 }
                 // Classical Gram-Schmidt against v_0 .. v_j, FP64, with a second pass whenever
                 // the first cancels more than 1 - 1/sqrt(2) of the norm of w for any active
-                // right-hand side (the Daniel-Gragg-Kaufman-Stewart criterion: "twice is enough")
+                // right-hand side (the Daniel-Gragg-Kaufman-Stewart criterion: "twice is enough").
+                // Small batches always take both passes: a second pass costs less there than the
+                // extra host round trip the test needs.
                 StageScope* bls = new StageScope(ctx, ST_SOLVE_BLAS, s);
                 const dim3 gd(nseg, nrhs);
-                k_norms<<<nrhs, 256, 0, s>>>(W.w, dnrm0, nunk, nunk);
-                k_dots_seg<<<gd, 256, 0, s>>>(W.V, W.w, dpart, nunk, vstride, j + 1, nseg, m + 1);
-                k_dots_fin<<<nrhs, 128, 0, s>>>(dpart, W.h, j + 1, nseg, m + 1, m + 1);
-                k_subtract<<<nblk(nv), 256, 0, s>>>(W.V, W.w, W.h, nunk, vstride, m + 1, j + 1, nrhs);
-                k_norms<<<nrhs, 256, 0, s>>>(W.w, W.nrm, nunk, nunk);
-                AIMX_CUDA_TRY(cudaGetLastError());
-                AIMX_CUDA_TRY(cudaMemcpyAsync(hb1.data(), W.h, sizeof(double2) * hb1.size(), cudaMemcpyDeviceToHost, s));
-                AIMX_CUDA_TRY(cudaMemcpyAsync(hn0.data(), dnrm0, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
-                AIMX_CUDA_TRY(cudaMemcpyAsync(hn.data(), W.nrm, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
-                AIMX_CUDA_TRY(cudaStreamSynchronize(s));
-                bool again = false;
-                for (int k = 0; k < nrhs; ++k)
-                    if (!done[k] && hn[k] < 0.7071067811865476 * hn0[k]) again = true;
-                if (again) {
-                    StageScope rs(ctx, ST_SOLVE_REORTH, s);
-                    k_dots_seg<<<gd, 256, 0, s>>>(W.V, W.w, dpart, nunk, vstride, j + 1, nseg, m + 1);
-                    k_dots_fin<<<nrhs, 128, 0, s>>>(dpart, h2, j + 1, nseg, m + 1, m + 1);
+                // h = V^H w: the segmented kernel when it fills the GPU, else one block per (vector, rhs)
+                auto dots = [&](double2* hout) {
+                    if ((int64_t)nseg * nrhs >= 2 * num_sms_solve()) {
+                        k_dots_seg<<<gd, 256, 0, s>>>(W.V, W.w, dpart, nunk, vstride, j + 1, nseg, m + 1);
+                        k_dots_fin<<<nrhs, 128, 0, s>>>(dpart, hout, j + 1, nseg, m + 1, m + 1);
+                    } else {
+                        k_dots<<<dim3(j + 1, nrhs), 256, 0, s>>>(W.V, W.w, hout, nunk, vstride, m + 1, j + 1);
+                    }
+                };
+                if (!selective) {
+                    dots(W.h);
+                    k_subtract<<<nblk(nv), 256, 0, s>>>(W.V, W.w, W.h, nunk, vstride, m + 1, j + 1, nrhs);
+                    dots(h2);
                     k_subtract<<<nblk(nv), 256, 0, s>>>(W.V, W.w, h2, nunk, vstride, m + 1, j + 1, nrhs);
                     k_norms<<<nrhs, 256, 0, s>>>(W.w, W.nrm, nunk, nunk);
                     AIMX_CUDA_TRY(cudaGetLastError());
+                    AIMX_CUDA_TRY(cudaMemcpyAsync(hb1.data(), W.h, sizeof(double2) * hb1.size(), cudaMemcpyDeviceToHost, s));
                     AIMX_CUDA_TRY(cudaMemcpyAsync(hb2.data(), h2, sizeof(double2) * hb2.size(), cudaMemcpyDeviceToHost, s));
                     AIMX_CUDA_TRY(cudaMemcpyAsync(hn.data(), W.nrm, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
                     AIMX_CUDA_TRY(cudaStreamSynchronize(s));
                 } else {
-                    std::fill(hb2.begin(), hb2.end(), make_double2(0, 0));
+                    k_norms<<<nrhs, 256, 0, s>>>(W.w, dnrm0, nunk, nunk);
+                    dots(W.h);
+                    k_subtract<<<nblk(nv), 256, 0, s>>>(W.V, W.w, W.h, nunk, vstride, m + 1, j + 1, nrhs);
+                    k_norms<<<nrhs, 256, 0, s>>>(W.w, W.nrm, nunk, nunk);
+                    AIMX_CUDA_TRY(cudaGetLastError());
+                    AIMX_CUDA_TRY(cudaMemcpyAsync(hb1.data(), W.h, sizeof(double2) * hb1.size(), cudaMemcpyDeviceToHost, s));
+                    AIMX_CUDA_TRY(cudaMemcpyAsync(hn0.data(), dnrm0, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+                    AIMX_CUDA_TRY(cudaMemcpyAsync(hn.data(), W.nrm, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+                    AIMX_CUDA_TRY(cudaStreamSynchronize(s));
+                    bool again = false;
+                    for (int k = 0; k < nrhs; ++k)
+                        if (!done[k] && hn[k] < 0.7071067811865476 * hn0[k]) again = true;
+                    if (again) {
+                        StageScope rs(ctx, ST_SOLVE_REORTH, s);
+                        dots(h2);
+                        k_subtract<<<nblk(nv), 256, 0, s>>>(W.V, W.w, h2, nunk, vstride, m + 1, j + 1, nrhs);
+                        k_norms<<<nrhs, 256, 0, s>>>(W.w, W.nrm, nunk, nunk);
+                        AIMX_CUDA_TRY(cudaGetLastError());
+                        AIMX_CUDA_TRY(cudaMemcpyAsync(hb2.data(), h2, sizeof(double2) * hb2.size(), cudaMemcpyDeviceToHost, s));
+                        AIMX_CUDA_TRY(cudaMemcpyAsync(hn.data(), W.nrm, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+                        AIMX_CUDA_TRY(cudaStreamSynchronize(s));
+                    } else {
+                        std::fill(hb2.begin(), hb2.end(), make_double2(0, 0));
+                    }
                 }
                 delete bls;
                 jlast = j + 1;
