@@ -232,10 +232,13 @@ int aimx_farfield(aimx_ctx* ctx, double freq, int nrhs, const void* x, int ndir,
 int aimx_sweep(aimx_ctx* ctx, int nf, const double* freqs, int nwave, const double* dirs, const double* pols, void* X,
                const aimx_solve_opts* opts, int warm_start, aimx_solve_stats* stats, void* stream);
 
-/* Select the FP32 matvec implementation: 0 = automatic (the plane-fused
+/* Select the matvec implementation: 0 = automatic (FP32: the plane-fused
  * path whenever the grid is padded to exactly twice a power-of-two size per
- * axis, else the generic path), 1 = always the generic path.  Both compute the
- * same product; FP64 always uses the generic path. */
+ * axis, else the generic path), 1 = always the generic path, 2 = the generic
+ * path with its 3-D FFTs done by cuFFT (full, unpruned transforms; the plain
+ * comparison path, FP32 and FP64).  All compute the same product; FP64 uses
+ * the generic path (with cuFFT under 2).  aimx_matvec_path returns 0
+ * (plane-fused), 1 (generic) or 2 (generic with cuFFT). */
 int aimx_set_path(aimx_ctx* ctx, int path);
 
 /* 0 if aimx_matvec at this precision runs the plane-fused path, 1 if generic. */

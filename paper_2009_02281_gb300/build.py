@@ -57,7 +57,7 @@ def build(force=False, verbose=False):
     with concurrent.futures.ThreadPoolExecutor(max_workers=len(srcs)) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = LIB + ".tmp"
-    cmd = [nvcc] + GENCODE + ["-shared", "-o", tmp] + objs + ["-lcudart"]
+    cmd = [nvcc] + GENCODE + ["-shared", "-o", tmp] + objs + ["-lcudart", "-lcufft"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))

@@ -223,7 +223,9 @@ struct aimx_ctx {
     int fused_cap = 0;             // RHS capacity of the buffers above
     int max_plane_bases = 0;
     int* d_plane = nullptr;        // [2][Nz] plane_lo then plane_hi
-    int path = 0;                  // 0 = automatic, 1 = force the generic FFT path
+    int path = 0;                  // 0 = automatic, 1 = generic FFT path, 2 = generic with cuFFT (comparison)
+    int cufft_plan[2] = {0, 0};    // cached cuFFT plans (FP32, FP64) of the comparison path
+    int cufft_batch[2] = {0, 0};   // batch each plan was made for
 
     aimx::Profiler prof;
     aimx::PrecondBlocks pc;
@@ -312,6 +314,7 @@ void gnn_free(aimx_ctx* ctx);
 void build_diag_inverse(aimx_ctx* ctx, double freq, double2* minv, cudaStream_t s);
 
 // matvec.cu
+void cufft_release(aimx_ctx* ctx);
 template <class T>
 void matvec_generic(aimx_ctx* ctx, double freq, int nrhs, const T* x, T* y, cudaStream_t s);
 

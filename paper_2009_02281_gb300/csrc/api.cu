@@ -49,6 +49,7 @@ static void free_all(aimx_ctx* c) {
     }
     for (auto e : c->prof.pool) cudaEventDestroy(e);
     gnn_free(c);
+    cufft_release(c);
     c->prof.recs.clear();
     c->prof.pool.clear();
 }
@@ -200,14 +201,15 @@ int aimx_matvec_host(aimx_ctx* ctx, double freq, int nrhs, const void* x, void* 
 }
 
 int aimx_set_path(aimx_ctx* ctx, int path) {
-    if (!ctx || path < 0 || path > 1) return AIMX_E_ARG;
+    if (!ctx || path < 0 || path > 2) return AIMX_E_ARG;
     ctx->path = path;
     return AIMX_OK;
 }
 
 int aimx_matvec_path(const aimx_ctx* ctx, int precision) {
     if (!ctx) return AIMX_E_ARG;
-    return (precision == AIMX_F32 && ctx->path == 0 && fused_supported(ctx)) ? 0 : 1;
+    if (precision == AIMX_F32 && ctx->path == 0 && fused_supported(ctx)) return 0;
+    return ctx->path == 2 ? 2 : 1;
 }
 
 int aimx_profile(aimx_ctx* ctx, int enable) {

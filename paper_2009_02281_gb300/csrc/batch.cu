@@ -33,7 +33,7 @@ struct aimx_batch {
 namespace {
 
 void member_matvec(aimx_ctx* c, double freq, int nrhs, const void* x, void* y, cudaStream_t s) {
-    if (c->path != 1 && fused_supported(c))
+    if (c->path == 0 && fused_supported(c))
         matvec_fused(c, freq, nrhs, static_cast<const float*>(x), static_cast<float*>(y), s);
     else
         matvec_generic<float>(c, freq, nrhs, static_cast<const float*>(x), static_cast<float*>(y), s);

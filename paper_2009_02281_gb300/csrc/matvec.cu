@@ -9,6 +9,8 @@
 //    inverse FFT;
 // 3. interpolation W = P^T and the sparse near correction, written once.
 
+#include <cufft.h>
+
 #include "aimx_internal.h"
 #include "cplx.cuh"
 
@@ -166,6 +168,45 @@ __global__ void k_interp_near(const T* __restrict__ w, const int* __restrict__ a
     }
 }
 
+// Comparison path: the full (unpruned) 3-D transforms of the padded grids by cuFFT
+// (Z2Z / C2C, unnormalised, the same sign convention as fft3d_padded; the 1/M of
+// the round trip is folded into the kernel spectra).  Plans are cached per
+// precision and batch size.
+template <class T>
+static void cufft_padded(aimx_ctx* ctx, cplx_t<T>* grid, int batch, int dir, cudaStream_t s) {
+    constexpr int pi = sizeof(T) == 8 ? 1 : 0;
+    cufftHandle& plan = reinterpret_cast<cufftHandle&>(ctx->cufft_plan[pi]);
+    if (plan && ctx->cufft_batch[pi] != batch) {
+        cufftDestroy(plan);
+        plan = 0;
+    }
+    if (!plan) {
+        int n[3] = {ctx->M[2], ctx->M[1], ctx->M[0]};
+        if (cufftPlanMany(&plan, 3, n, nullptr, 1, 0, nullptr, 1, 0, pi ? CUFFT_Z2Z : CUFFT_C2C, batch) !=
+            CUFFT_SUCCESS) {
+            plan = 0;
+            throw Error{AIMX_E_CUDA, "cufftPlanMany failed"};
+        }
+        ctx->cufft_batch[pi] = batch;
+    }
+    if (cufftSetStream(plan, s) != CUFFT_SUCCESS) throw Error{AIMX_E_CUDA, "cufftSetStream failed"};
+    cufftResult r;
+    if (pi)
+        r = cufftExecZ2Z(plan, reinterpret_cast<cufftDoubleComplex*>(grid), reinterpret_cast<cufftDoubleComplex*>(grid),
+                         dir);
+    else
+        r = cufftExecC2C(plan, reinterpret_cast<cufftComplex*>(grid), reinterpret_cast<cufftComplex*>(grid), dir);
+    if (r != CUFFT_SUCCESS) throw Error{AIMX_E_CUDA, "cufftExec failed"};
+}
+
+void cufft_release(aimx_ctx* ctx) {
+    for (int k = 0; k < 2; ++k)
+        if (ctx->cufft_plan[k]) {
+            cufftDestroy((cufftHandle)ctx->cufft_plan[k]);
+            ctx->cufft_plan[k] = 0;
+        }
+}
+
 template <class T>
 void matvec_generic(aimx_ctx* ctx, double freq, int nrhs, const T* x, T* y, cudaStream_t s) {
     using C = cplx_t<T>;
@@ -198,11 +239,17 @@ void matvec_generic(aimx_ctx* ctx, double freq, int nrhs, const T* x, T* y, cuda
             pd.w, ctx->d_node_ptr, ctx->d_node_w, ctx->d_node_x, xc + (int64_t)b0 * ctx->nunk, grid, nb,
             F, ctx->N, ctx->nunk, ctx->n[0], ctx->n[1], ctx->n[2], ctx->M[0], ctx->M[1], ctx->M[2]);
         AIMX_CUDA_TRY(cudaGetLastError());
-        fft3d_padded<T>(reinterpret_cast<T*>(grid), nb * F, ctx->M, act, false, s);
+        if (ctx->path == 2)
+            cufft_padded<T>(ctx, grid, nb * F, CUFFT_FORWARD, s);
+        else
+            fft3d_padded<T>(reinterpret_cast<T*>(grid), nb * F, ctx->M, act, false, s);
         k_mix<T><<<(unsigned)((MT + 255) / 256), 256, 0, s>>>(
             grid, reinterpret_cast<const C*>(pd.spec), nb, F, ctx->M[0], ctx->M[1], ctx->M[2]);
         AIMX_CUDA_TRY(cudaGetLastError());
-        fft3d_padded<T>(reinterpret_cast<T*>(grid), nb * F, ctx->M, act, true, s);
+        if (ctx->path == 2)
+            cufft_padded<T>(ctx, grid, nb * F, CUFFT_INVERSE, s);
+        else
+            fft3d_padded<T>(reinterpret_cast<T*>(grid), nb * F, ctx->M, act, true, s);
         int64_t tn = (int64_t)ctx->N * nb;
         k_interp_near<T><<<(unsigned)((tn + 127) / 128), 128, 0, s>>>(
             pd.w, ctx->d_anc, ctx->d_perm, ctx->d_row_ptr, ctx->d_cols, pd.na, pd.np, F == 8 ? pd.nk : pd.ng, grid,

@@ -172,3 +172,27 @@ def test_config1_sized_efie(torch_cuda):
     ctx.close()
     assert _relerr(y64, ref) <= TOL64
     assert _relerr(y32, ref) <= TOL32
+
+
+@pytest.mark.parametrize("form", ["efie", "pmchwt"])
+def test_cufft_comparison_path_parity(efie_l2, pmchwt_l1, torch_cuda, form):
+    """The plain comparison path (cuFFT transforms of the full padded grids) computes the same product."""
+    torch = torch_cuda
+    from synth import random_complex
+    from oracle import operator as op
+    ctx, prob = efie_l2 if form == "efie" else pmchwt_l1
+    f = 1.1 * C0 / (2 * np.pi)
+    x = random_complex((2, ctx.nunk), seed=61)
+    if form == "efie":
+        ref = np.stack([op.matvec_efie(prob, f, v) for v in x])
+    else:
+        ref = np.stack([op.matvec_pmchwt(prob, f, v, 1.0, 4.0) for v in x])
+    ctx.set_path(2)
+    try:
+        assert ctx.matvec_path() == 2
+        y64 = ctx.matvec(f, torch.tensor(x, dtype=torch.complex128, device="cuda")).cpu().numpy()
+        y32 = ctx.matvec(f, torch.tensor(x, dtype=torch.complex64, device="cuda")).cpu().numpy()
+    finally:
+        ctx.set_path(0)
+    assert _relerr(y64, ref) <= TOL64
+    assert _relerr(y32, ref) <= TOL32
