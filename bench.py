@@ -236,6 +236,54 @@ def measure_config1(args, ws):
             "rel_residual": st[0]["rel_residual"], "status": rc}
 
 
+def learned_eval(args):
+    """Learned preconditioner trained on seeded small copper-block layouts (10 mm
+    region, 1-4 mm blocks, several frequencies) and evaluated on held-out larger
+    layouts (20 mm region, up to 12 blocks of 1-6 mm) at held-out frequencies:
+    GMRES iterations and wall time against the diagonal preconditioner."""
+    import torch
+    from synth import workloads, planewave_batch
+    from paper_2009_02281_gb300 import Context, EFIE, Gnn, PRECOND_DIAG, PRECOND_LEARNED
+
+    def make(w):
+        return Context(w["xyz"], w["tri"], w["grid_n"], order=2, formulation=EFIE, eps_out=1.0, sigma=w["sigma"])
+
+    train_w = [workloads.copper_blocks(s, region=10e-3, footprint=(1e-3, 4e-3)) for s in range(8)]
+    train = [make(w) for w in train_w]
+    samples = [(c, f) for c in train for f in (10e9, 25e9, 40e9)]
+    net = Gnn(EFIE)
+    net.init_params(0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = net.fit(samples, steps=args.gnn_eval_steps, nprobe=8, lr=2e-3, clip=1.0, seed=1)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    out = {"train_layouts": len(train), "train_unknowns": [c.nunk for c in train], "train_freqs_ghz": [10, 25, 40],
+           "steps": args.gnn_eval_steps, "train_s": round(train_s, 2), "loss_first": round(losses[0], 4),
+           "loss_last": round(float(np.mean(losses[-50:])), 4), "eval": []}
+    dirs, pols = planewave_batch(8, seed=5)
+    for seed in (100, 101):
+        w = workloads.copper_blocks(seed, nblocks=12, region=20e-3)
+        ctx = make(w)
+        ctx.gnn_attach(net)
+        for f in (15e9, 30e9, 45e9):
+            b = ctx.rhs_planewave(f, dirs, pols)
+            row = {"layout": seed, "unknowns": ctx.nunk, "freq_ghz": f / 1e9}
+            for name, pc in (("diag", PRECOND_DIAG), ("learned", PRECOND_LEARNED)):
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                _, st, rc = ctx.solve(f, b, tol=1e-5, restart=100, max_iter=4000, precond=pc)
+                torch.cuda.synchronize()
+                row[name] = {"iterations_mean": float(np.mean([s["iterations"] for s in st])),
+                             "wall_s": round(time.perf_counter() - t, 3), "status": rc}
+            out["eval"].append(row)
+        ctx.close()
+    for c in train:
+        c.close()
+    net.close()
+    return out
+
+
 def measure_batch(args, ws):
     """The first args.batch_members members of the seeded uneven batch (spheres, boxes,
     tori; PEC and dielectric; 4 RHS each): one captured graph per call versus the
@@ -466,6 +514,8 @@ def run_ours(args):
         out["uneven_batch"] = measure_batch(args, ws)
     if not args.no_config1:
         out["pec_sphere_1920"] = measure_config1(args, ws)
+    if not args.no_learned_eval:
+        out["learned_generalisation"] = learned_eval(args)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl, args.cpu_rows)
     if rank == 0:
@@ -552,6 +602,9 @@ def main():
     ap.add_argument("--no-solves", action="store_true", help="skip the batched solve measurement")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 product measurement")
     ap.add_argument("--no-config1", action="store_true", help="skip the 1920-unknown FP64 latency measurement")
+    ap.add_argument("--no-learned-eval", action="store_true",
+                    help="skip training on small copper layouts and evaluating on held-out larger ones")
+    ap.add_argument("--gnn-eval-steps", type=int, default=1500, help="training steps of the generalisation study")
     ap.add_argument("--batch-members", type=int, default=16,
                     help="members of the seeded uneven batch to time (0 = skip; 48 = the full batch)")
     ap.add_argument("--path", type=int, default=0, choices=[0, 1], help="product path for the timed steps (aimx_set_path)")

@@ -17,6 +17,10 @@ stand in for the paper's geometries, which are not available.
   mesh with 3.2 um cells along the bars (75k unknowns), one delta-gap port at
   the middle of each bar, a 256 x 16 x 8 grid (padded 512 x 32 x 16), 100
   log-spaced frequencies from 1 MHz to 100 GHz.
+* ``copper_blocks``: seeded layouts of 2-12 rectangular copper blocks (1-6 mm
+  footprint, 0.2-1 mm thick, surface impedance) on a 20 mm square, structured
+  meshes of ~0.4 mm cells: the learned preconditioner's training and held-out
+  evaluation layouts.
 * ``uneven_batch``: seeded mix of PEC (EFIE) and dielectric (eps_r ~ U[2, 6],
   two-region) spheres, boxes and tori of size U[0.5, 4] free-space wavelengths
   at f = c (wavelength 1 m), meshed for a log-uniform 2k-60k unknowns, each
@@ -64,6 +68,37 @@ def conductor_bars(nbars=8, length=1000e-6, width=10e-6, thickness=5e-6, gap=10e
     return dict(name="conductor_bars_%d" % nbars, xyz=xyz, tri=tri, formulation="efie", eps_out=3.5, eps_in=None,
                 sigma=5.8e7, grid_n=(256, 16, 8), order=2, radius=3, ports=ports,
                 freqs=np.logspace(6, 11, 100), precision="f32")
+
+
+def copper_blocks(seed, nblocks=None, edge=0.4e-3, region=20e-3, footprint=(1e-3, 6e-3)):
+    """A seeded layout of rectangular copper blocks on a plane (inputs only).
+
+    ``nblocks`` (default U{2..12}) boxes of 1-6 mm footprint and 0.2-1 mm
+    height placed without overlap in a ``region`` x ``region`` square, meshed as
+    structured boxes with cells of about ``edge``; sigma = 5.8e7 S/m, free
+    space around them.  Returns a workload dict (EFIE with surface impedance)."""
+    from .meshes import merge_meshes
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(2, 13)) if nblocks is None else int(nblocks)
+    placed, parts = [], []
+    tries = 0
+    while len(placed) < n and tries < 2000:
+        tries += 1
+        w, d = rng.uniform(footprint[0], footprint[1], size=2)
+        t = rng.uniform(0.2e-3, 1e-3)
+        x0, y0 = rng.uniform(0, region - w), rng.uniform(0, region - d)
+        gap = 0.5e-3
+        if any(x0 < bx + bw + gap and bx < x0 + w + gap and y0 < by + bd + gap and by < y0 + d + gap
+               for bx, by, bw, bd in placed):
+            continue
+        placed.append((x0, y0, w, d))
+        div = [max(1, int(round(w / edge))), max(1, int(round(d / edge))), max(1, int(round(t / edge)))]
+        parts.append(box([x0, y0, 0.0], [x0 + w, y0 + d, t], div))
+    xyz, tri, _ = merge_meshes(parts)
+    ext = xyz.max(0) - xyz.min(0)
+    grid = tuple(_pow2_nodes(e, edge) for e in ext)
+    return dict(name="copper_blocks_%d" % seed, xyz=xyz, tri=tri, formulation="efie", eps_out=1.0, eps_in=None,
+                sigma=5.8e7, grid_n=grid, order=2, radius=3, precision="f32")
 
 
 def _pow2_nodes(extent, h, order=2):
