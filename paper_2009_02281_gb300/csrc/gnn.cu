@@ -288,9 +288,9 @@ __global__ void k_edge_message(const float* __restrict__ P, const float* __restr
     const float cb0 = bf(w, oc + lane), cb1 = bf(w, oc + lane + 32);
     for (int m = warp; m < N; m += nwarp) {
         float s0 = 0.f, s1 = 0.f;
-        for (int t = row_ptr[m]; t < row_ptr[m + 1]; ++t) {
+        auto edge = [&](int t) {
             const int n = cols[t];
-            if (n == m) continue;
+            if (n == m) return;
             float ef[kNed];
             load_row<kNed>(e, t, ef);
             float w0 = P[(int64_t)n * kW + lane] + cb0, w1 = P[(int64_t)n * kW + lane + 32] + cb1;
@@ -301,7 +301,15 @@ __global__ void k_edge_message(const float* __restrict__ P, const float* __restr
             }
             s0 += fmaxf(w0, 0.f);
             s1 += fmaxf(w1, 0.f);
+        };
+        // two edges per iteration keep two independent gathers in flight
+        int t = row_ptr[m];
+        const int te = row_ptr[m + 1];
+        for (; t + 1 < te; t += 2) {
+            edge(t);
+            edge(t + 1);
         }
+        if (t < te) edge(t);
         const float di = deginv[m];
         S[(int64_t)m * kW + lane] = s0 * di;
         S[(int64_t)m * kW + lane + 32] = s1 * di;
@@ -662,20 +670,21 @@ __global__ void k_edge_backward(const float* __restrict__ P, const float* __rest
     for (int n = warp; n < N; n += nwarp) {
         const float p0 = P[(int64_t)n * kW + lane] + cb0, p1 = P[(int64_t)n * kW + lane + 32] + cb1;
         float d0 = 0.f, d1 = 0.f;
-        for (int t = row_ptr[n]; t < row_ptr[n + 1]; ++t) {
+        auto edge = [&](int t) {
             const int m = cols[t];
-            if (m == n) continue;
+            if (m == n) return;
             const int tr = trans[t];  // edge (m, n) in row m
             float ef[kNed];
             load_row<kNed>(e, tr, ef);
+            const float ds0 = dS[(int64_t)m * kW + lane], ds1 = dS[(int64_t)m * kW + lane + 32];
             float w0 = p0, w1 = p1;
 #pragma unroll
             for (int f = 0; f < kNed; ++f) {
                 w0 = fmaf(C0[f], ef[f], w0);
                 w1 = fmaf(C1[f], ef[f], w1);
             }
-            const float g0 = w0 > 0.f ? dS[(int64_t)m * kW + lane] : 0.f;
-            const float g1 = w1 > 0.f ? dS[(int64_t)m * kW + lane + 32] : 0.f;
+            const float g0 = w0 > 0.f ? ds0 : 0.f;
+            const float g1 = w1 > 0.f ? ds1 : 0.f;
             d0 += g0;
             d1 += g1;
 #pragma unroll
@@ -683,7 +692,14 @@ __global__ void k_edge_backward(const float* __restrict__ P, const float* __rest
                 aC0[f] = fmaf(g0, ef[f], aC0[f]);
                 aC1[f] = fmaf(g1, ef[f], aC1[f]);
             }
+        };
+        int t = row_ptr[n];
+        const int te = row_ptr[n + 1];
+        for (; t + 1 < te; t += 2) {
+            edge(t);
+            edge(t + 1);
         }
+        if (t < te) edge(t);
         ac0 += d0;
         ac1 += d1;
         dP[(int64_t)n * kW + lane] = d0;
@@ -701,68 +717,84 @@ __global__ void k_edge_backward(const float* __restrict__ P, const float* __rest
 // Per-block partials of a row reduction over R rows in fixed chunks:
 //   out[o][i] = sum_r A(r, o) B[r][i] (o < na <= 64, i < nb <= 64), then (bias) sum_r A(r, o).
 // MODE 0: A(r, o) = A[r * na + o];  MODE 1: A(r, o) = Ge[r * K + o / 8] * basis[r * 8 + o % 8].
+// Thread t owns the 4 x 4 output tile o in [4 (t / 16), +4), i in [4 (t % 16), +4): two 128-bit
+// shared loads feed 16 FMAs per row.
 template <int MODE>
 __global__ void __launch_bounds__(256) k_rows_wgrad(const float* __restrict__ A, const float* __restrict__ Ge,
                                                     const float* __restrict__ basis, int K, int na,
                                                     const float* __restrict__ B, int nb, int bias, int64_t R,
                                                     int64_t chunk, float* __restrict__ part) {
-    __shared__ float As[32][kW + 1];
-    __shared__ float Bs[32][kW + 1];
+    __shared__ __align__(16) float As[32][kW];
+    __shared__ __align__(16) float Bs[32][kW];
     const int t = threadIdx.x;
+    const int ot = t >> 4, it = t & 15;
+    const bool active = 4 * ot < na && 4 * it < nb;
     const int64_t lo = blockIdx.x * chunk, hi = min(R, lo + chunk);
-    const int nout = na * nb;
-    float acc[16], accb = 0.f;
+    float acc[4][4], accb[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-    for (int j = 0; j < 16; ++j) acc[j] = 0.f;
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[a][c] = 0.f;
     for (int64_t r0 = lo; r0 < hi; r0 += 32) {
-        for (int k = t; k < 32 * na; k += 256) {
-            const int r = k / na, c = k % na;
-            float v = 0.f;
+        for (int k = t; k < 32 * kW; k += 256) {
+            const int r = k / kW, c = k % kW;
+            float va = 0.f, vb = 0.f;
             if (r0 + r < hi) {
-                if (MODE == 0)
-                    v = A[(r0 + r) * na + c];
-                else
-                    v = Ge[(r0 + r) * K + c / kNB] * basis[(r0 + r) * kNB + c % kNB];
+                if (c < na) {
+                    if (MODE == 0)
+                        va = A[(r0 + r) * na + c];
+                    else
+                        va = Ge[(r0 + r) * K + c / kNB] * basis[(r0 + r) * kNB + c % kNB];
+                }
+                if (c < nb) vb = B[(r0 + r) * nb + c];
             }
-            As[r][c] = v;
-        }
-        for (int k = t; k < 32 * nb; k += 256) {
-            const int r = k / nb, c = k % nb;
-            Bs[r][c] = (r0 + r < hi) ? B[(r0 + r) * nb + c] : 0.f;
+            As[r][c] = va;
+            Bs[r][c] = vb;
         }
         __syncthreads();
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const int idx = t + 256 * j;
-            if (idx < nout) {
-                const int o = idx / nb, i = idx % nb;
-                float a = acc[j];
+        if (active) {
 #pragma unroll 8
-                for (int r = 0; r < 32; ++r) a = fmaf(As[r][o], Bs[r][i], a);
-                acc[j] = a;
+            for (int r = 0; r < 32; ++r) {
+                const float4 a4 = *reinterpret_cast<const float4*>(&As[r][4 * ot]);
+                const float4 b4 = *reinterpret_cast<const float4*>(&Bs[r][4 * it]);
+                const float av[4] = {a4.x, a4.y, a4.z, a4.w}, bv[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[a][c] = fmaf(av[a], bv[c], acc[a][c]);
+                    if (it == 0) accb[a] += av[a];
+                }
             }
         }
-        if (bias && t < na)
-            for (int r = 0; r < 32; ++r) accb += As[r][t];
         __syncthreads();
     }
-    const int len = nout + (bias ? na : 0);
+    const int len = na * nb + (bias ? na : 0);
     float* pb = part + (int64_t)blockIdx.x * len;
+    if (active) {
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-        const int idx = t + 256 * j;
-        if (idx < nout) pb[idx] = acc[j];
+        for (int a = 0; a < 4; ++a) {
+            const int o = 4 * ot + a;
+            if (o >= na) continue;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int i = 4 * it + c;
+                if (i < nb) pb[o * nb + i] = acc[a][c];
+            }
+            if (bias && it == 0) pb[na * nb + o] = accb[a];
+        }
     }
-    if (bias && t < na) pb[nout + t] = accb;
 }
 
-// grad[j] = sum_b part[b][j] in block order (FP64 accumulation)
+// grad[j] = sum_b part[b][j]: one warp per output, lane-strided partial sums in FP64
+// followed by a fixed shuffle tree (deterministic)
 __global__ void k_reduce_parts(const float* __restrict__ part, int nparts, int len, float* __restrict__ grad) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (j >= len) return;
     double s = 0;
-    for (int b = 0; b < nparts; ++b) s += part[(int64_t)b * len + j];
-    grad[j] = (float)s;
+    for (int b = lane; b < nparts; b += 32) s += part[(int64_t)b * len + j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) grad[j] = (float)s;
 }
 
 __global__ void k_reduce_loss(const double* __restrict__ lossn, int N, double* __restrict__ out) {
@@ -985,7 +1017,7 @@ static void gnn_diag_inverse(aimx_ctx* ctx, double freq, cudaStream_t s) {
 }
 
 static void reduce_into(const float* part, int nparts, int64_t len, float* grad, cudaStream_t s) {
-    k_reduce_parts<<<gb(len), 256, 0, s>>>(part, nparts, (int)len, grad);
+    k_reduce_parts<<<gb(len * 32), 256, 0, s>>>(part, nparts, (int)len, grad);
 }
 
 // fixed-partition row reduction (see k_rows_wgrad) reduced into grad
