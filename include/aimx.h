@@ -84,7 +84,8 @@ typedef struct {
 /* Auxiliary grid (Sec. II-B).  n: nodes per axis (required).  h: spacing per
  * axis; all zero = derived from the vertex bounding box as
  * h_a = (hi_a - lo_a) / (n_a - 1 - 2m), origin_a = lo_a - m h_a with margin
- * m = floor((order + 1) / 2).  When h is given, origin must be given too.
+ * m = floor((order + 1) / 2); an axis along which the mesh is flat takes the
+ * largest spacing of the other axes.  When h is given, origin must be given too.
  * near_radius: near-region radius in cells (Chebyshev distance of stencil
  * anchors), 0 = 3.  pad: zero-padded FFT length per axis, 0 = smallest power
  * of two >= 2 n_a - 1 (any value >= 2 n_a - 1 gives the same product). */

@@ -43,6 +43,10 @@ def make_grid(xyz, order, n_nodes, h=None, origin=None):
         if np.any(denom <= 0):
             raise GridError("grid too small for the stencil margin")
         h = (hi - lo) / denom
+        # an axis along which the mesh is flat takes the largest spacing of the others
+        flat = (hi - lo) <= 0
+        if np.any(flat) and not np.all(flat):
+            h = np.where(flat, h.max(), h)
     h = np.asarray(h, dtype=np.float64)
     if np.any(h <= 0):
         raise GridError("non-positive grid spacing")

@@ -500,13 +500,24 @@ void setup_context(aimx_ctx* ctx, const aimx_mesh* mesh, const aimx_material* ma
             ctx->h[a] = grid->h[a];
             ctx->origin[a] = grid->origin[a];
         }
-        if (!(ctx->h[a] > 0)) throw Error{AIMX_E_GRID, "non-positive grid spacing"};
         int pmin = 2 * grid->n[a] - 1;
         int pad = grid->pad[a] > 0 ? grid->pad[a] : next_pow2(pmin);
         if (pad < pmin || (pad & (pad - 1)) || pad > kTwiddleLen)
             throw Error{AIMX_E_ARG, "pad must be a power of two >= 2n-1 and <= 4096"};
         ctx->M[a] = pad;
     }
+
+    if (auto_h) {
+        // an axis along which the mesh is flat takes the largest spacing of the others
+        const double hmax = std::max(ctx->h[0], std::max(ctx->h[1], ctx->h[2]));
+        for (int a = 0; a < 3; ++a)
+            if (!(hi[a] - lo[a] > 0) && hmax > 0) {
+                ctx->h[a] = hmax;
+                ctx->origin[a] = lo[a] - m * hmax;
+            }
+    }
+    for (int a = 0; a < 3; ++a)
+        if (!(ctx->h[a] > 0)) throw Error{AIMX_E_GRID, "non-positive grid spacing"};
 
     // anchors s_a = floor((c_a - o_a) / h_a - (n - 1) / 2), caller order
     std::vector<int> anc0(3 * (size_t)N);

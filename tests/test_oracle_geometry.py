@@ -182,3 +182,13 @@ def test_box_mesh_closed():
     r = rw.build_rwg(xyz, tri)
     assert r["n"] == 3 * len(tri) // 2
     assert len(xyz) - r["n"] + len(tri) == 2
+
+
+def test_flat_axis_takes_largest_spacing():
+    """A planar mesh gets a usable spacing along its flat axis (the largest of the others)."""
+    import numpy as np
+    from oracle import grid as gridmod
+    xyz = np.array([[0, 0, 0], [0.3, 0, 0], [0, 0.2, 0], [0.3, 0.2, 0.0]])
+    g = gridmod.make_grid(xyz, 2, np.array([8, 8, 8]))
+    assert g["h"][2] == max(g["h"][0], g["h"][1]) > 0
+    assert g["origin"][2] == -g["margin"] * g["h"][2]
