@@ -33,6 +33,7 @@ if ROOT not in sys.path:
 
 METRIC = "AIMx matvecs/s"
 UNIT = "RHS-matvecs/s"
+C0 = 299792458.0
 FALLBACK_HBM = 6800.0
 L2_FLUSH_BYTES = 512 << 20
 
@@ -223,6 +224,18 @@ def measure_config1(args, ws):
     us = 1e3 * e0.elapsed_time(e1) / reps
     b = ctx.rhs_planewave(f, [[0.0, 0.0, 1.0]], [[1.0, 0.0, 0.0]])
     ctx.solve(f, b, tol=1e-6, inner_precision=F64)     # warm-up
+    # the sweep: 100 frequencies from ka = 1 to ka = pi (50-150 MHz), static data reused,
+    # kernel spectra regenerated per frequency, warm start from the previous frequency
+    freqs = np.linspace(C0 / (2 * np.pi), C0 / 2, 100)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    _, sst, src = ctx.sweep(freqs, [[0.0, 0.0, 1.0]], [[1.0, 0.0, 0.0]], tol=1e-6, inner_precision=F64)
+    torch.cuda.synchronize()
+    sweep_s = time.perf_counter() - t
+    sweep = {"frequencies": len(freqs), "f_range_hz": [float(freqs[0]), float(freqs[-1])], "rhs": 1,
+             "wall_s": round(sweep_s, 3), "solves_per_s": round(ws * len(freqs) / sweep_s, 2),
+             "converged": sum(1 for q in sst if q["status"] == 0),
+             "iterations_mean": round(float(np.mean([q["iterations"] for q in sst])), 1), "status": src}
     torch.cuda.synchronize()
     t = time.perf_counter()
     nsol = 5
@@ -233,7 +246,7 @@ def measure_config1(args, ws):
     ctx.close()
     return {"workload": "pec_sphere_1920", "setup_s": round(setup_s, 3), "fp64_matvec_us": round(us, 1),
             "solve_ms": round(1e3 * dt, 2), "solves_per_s": round(ws / dt, 2), "iterations": st[0]["iterations"],
-            "rel_residual": st[0]["rel_residual"], "status": rc}
+            "rel_residual": st[0]["rel_residual"], "status": rc, "sweep": sweep}
 
 
 def learned_eval(args):

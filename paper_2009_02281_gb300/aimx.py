@@ -374,7 +374,7 @@ class Context:
         return X, _stats_list(st), rc
 
     def set_path(self, path):
-        """0 = automatic (plane-fused FP32 path when supported), 1 = generic path."""
+        """0 = automatic (plane-fused FP32 path when supported), 1 = generic path, 2 = generic with cuFFT."""
         self._check(self._lib.aimx_set_path(self._ctx, int(path)))
 
     def matvec_path(self, precision=F32):
