@@ -245,6 +245,34 @@ int aimx_set_path(aimx_ctx* ctx, int path);
 /* 0 if aimx_matvec at this precision runs the plane-fused path, 1 if generic. */
 int aimx_matvec_path(const aimx_ctx* ctx, int precision);
 
+/* ------------------------------------------------------------------ linear-term modification
+ * Sec. III-A-3, Eqs. linterm and Lmatdecomplin.  The term k^2 G_lin,
+ * G_lin = -r / (8 pi), of the Green's function's Taylor series is not smooth
+ * at r = 0, so the grid represents it poorly where a basis and a testing
+ * function overlap (share a triangle).  With enable = 1 every product of this
+ * context (aimx_matvec in both precisions and paths, aimx_solve, aimx_sweep,
+ * batches) adds, on those pairs, k^2 (L_lin,direct - L_lin,P): the direct
+ * integrals of G_lin minus their precorrection with the sampled kernel
+ * -|d h| / (8 pi) (0 at d = 0).  In the L operator this is
+ * k^2 N^A_lin - N^Phi_lin, scaled as L is in each region's rows (EFIE; both
+ * regions of PMCHWT).  The K operator is unchanged.
+ *   - The first enable builds the overlap pattern and its values (FP64 direct
+ *     integrals: closed-form inner integrals of |r - r'|, the 5 x 5 collapsed
+ *     Gauss rule outside) and keeps them until aimx_destroy; synchronous.
+ *   - Preconditioners (diagonal, block, learned) keep the unmodified near
+ *     matrices.  Static data files do not hold these values.
+ *   - enable = 0 turns the term off again; other values are AIMX_E_ARG.
+ * Off by default, as in the paper's numerical results. */
+int aimx_set_linear_term(aimx_ctx* ctx, int enable);
+
+/* Copy the linear-term values to host arrays in caller numbering (any output
+ * pointer may be NULL): nlin = number of overlapping pairs; row_ptr int64
+ * [N+1]; cols int32 [nlin] (ascending per row); na, nphi double [nlin] =
+ * N^A_lin, N^Phi_lin.  AIMX_E_STATE before the first aimx_set_linear_term(ctx, 1).
+ * Synchronous. */
+int aimx_export_linear_term(const aimx_ctx* ctx, int64_t* nlin, int64_t* row_ptr, int32_t* cols,
+                            double* na, double* nphi);
+
 /* ------------------------------------------------------------------ profiling
  * Per-stage timing with CUDA events recorded on the stream each stage is
  * launched on (the paper's per-phase accounting, Table II, at kernel level).

@@ -170,3 +170,26 @@ def matvec_efie_lin(prob, freq, x, eps_bg=1.0, lin=None):
     mu, eps, k = regs[0]
     a, p = lin_apply(prob, k, x, lin)
     return op.matvec_efie(prob, freq, x, eps_bg) + 1j * w * mu * (a - p)
+
+
+def matvec_pmchwt_lin(prob, freq, x, eps_out, eps_in, mu_in=1.0, lin=None):
+    """Two-region PMCHWT AIMx product with the modification in the L operator of both regions.
+
+    Each region's L = L^A - k^-2 L^Phi gains k^2 N^A_lin - N^Phi_lin, scaled as L
+    is in the rows it enters (j w mu on J in the E rows, eta0^2 j w eps on M/eta0
+    in the H rows); the K operator is unchanged.
+    """
+    from . import operator as op
+    from .constants import ETA0
+    N = prob["N"]
+    lin = lin if lin is not None else lin_matrices(prob)
+    w, regs = op.materials(freq, eps_out, eps_in, mu_in)
+    y = op.matvec_pmchwt(prob, freq, x, eps_out, eps_in, mu_in)
+    addE = np.zeros(N, dtype=np.complex128)
+    addH = np.zeros(N, dtype=np.complex128)
+    for mu, eps, k in regs:
+        aJ, pJ = lin_apply(prob, k, x[:N], lin)
+        aM, pM = lin_apply(prob, k, x[N:], lin)
+        addE += 1j * w * mu * (aJ - pJ)
+        addH += ETA0 ** 2 * 1j * w * eps * (aM - pM)
+    return y + np.concatenate([addE, addH])

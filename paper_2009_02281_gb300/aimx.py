@@ -80,6 +80,8 @@ _SIGS = [
                                         ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
     ("aimx_export_setup", ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 7),
     ("aimx_set_path", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("aimx_set_linear_term", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("aimx_export_linear_term", ctypes.c_int, [ctypes.c_void_p] * 6),
     ("aimx_matvec_path", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("aimx_profile", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("aimx_profile_read", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
@@ -379,6 +381,21 @@ class Context:
 
     def matvec_path(self, precision=F32):
         return self._check(self._lib.aimx_matvec_path(self._ctx, int(precision)))
+
+    def set_linear_term(self, enable=True):
+        """Linear-term modification of Sec. III-A-3 on overlapping pairs (built on the first enable)."""
+        self._check(self._lib.aimx_set_linear_term(self._ctx, 1 if enable else 0))
+
+    def export_linear_term(self):
+        """{row_ptr, cols, NA, NP}: N^A_lin, N^Phi_lin on the overlapping pairs, caller numbering."""
+        nl = np.zeros(1, dtype=np.int64)
+        self._check(self._lib.aimx_export_linear_term(self._ctx, _ptr(nl), None, None, None, None))
+        n = int(nl[0])
+        rp = np.zeros(self.N + 1, dtype=np.int64)
+        cols = np.zeros(n, dtype=np.int32)
+        na, nphi = np.zeros(n), np.zeros(n)
+        self._check(self._lib.aimx_export_linear_term(self._ctx, None, _ptr(rp), _ptr(cols), _ptr(na), _ptr(nphi)))
+        return dict(row_ptr=rp, cols=cols, NA=na, NP=nphi)
 
     # ---------------------------------------------------------------- profiling
     def profile(self, enable=True):

@@ -61,6 +61,8 @@ struct PrecData {
     T* np = nullptr;       // near N^Phi[nnz]
     T* nk = nullptr;       // near N^K  [nnz]
     T* ng = nullptr;       // near Gram matrix [nnz] (surface impedance, EFIE with sigma > 0)
+    T* la = nullptr;       // linear-term N^A_lin on the overlap pattern [nlin] (when enabled)
+    T* lp = nullptr;       // linear-term N^Phi_lin on the overlap pattern [nlin]
     T* spec = nullptr;     // octant spectra [nspec][Oz][Oy][Ox] complex (2 T each)
     double spec_freq = -1.0;
     // work buffers of the generic FFT path
@@ -197,6 +199,14 @@ struct aimx_ctx {
     int* d_node_x = nullptr;       // [N*U] caller basis index of that entry
     double* d_diag = nullptr;      // [N][3] static self terms L^A_s, L^Phi_s, K_s
     double* d_gdiag = nullptr;     // [N] Gram self terms (surface impedance only)
+    // linear-term modification (Sec. III-A-3): pairs of bases that share a triangle
+    int linterm = 0;               // 1 = products add k^2 (L_lin,direct - L_lin,P) on those pairs
+    int64_t nlin = 0;              // overlapping pairs (0 until first enabled)
+    std::vector<int> lin_ptr;      // overlap CSR, internal order [N+1]
+    std::vector<int> lin_cols;     // [nlin] internal column ids, ascending
+    int* d_lin_ptr = nullptr;
+    int* d_lin_cols = nullptr;
+    int config_gen = 0;            // bumped when a setting that changes the product's kernels changes
     // host copies for port definitions (caller order)
     std::vector<double> h_xyz;     // [nv][3]
     std::vector<int> h_ea, h_eb, h_tp, h_tm;   // [N] edge vertices, T+ / T-
@@ -248,6 +258,8 @@ struct StaticData {
     std::vector<double> na, np, nk;  // [nnz] near matrices N^A, N^Phi, N^K
     std::vector<double> diag;  // [N][3] static self terms
 };
+// overlap pattern and N^A_lin, N^Phi_lin (direct - precorrection), built once on demand
+void build_linterm(aimx_ctx* ctx);
 void setup_context(aimx_ctx* ctx, const aimx_mesh* mesh, const aimx_material* mat,
                    const aimx_grid* grid, int order, const StaticData* pre = nullptr);
 
@@ -267,6 +279,9 @@ struct Coefs {
     // near-matrix coefficients; EFIE: aA, aPhi, Z_s (Gram, 0 without a surface
     // impedance); PMCHWT: aA, aPhi, aK, bK, bA, bPhi
     double2 near[6];
+    // linear-term coefficients of N^A_lin and N^Phi_lin x, J rows then M rows
+    // (zero while the modification is off)
+    double2 lin[4];
 };
 Coefs near_coefs(const aimx_ctx* ctx, double freq);
 

@@ -40,7 +40,8 @@ static void free_all(aimx_ctx* c) {
                     c->f64.nk,    c->f64.spec,  c->f64.grid,   c->d_kgen,   c->d_stage,
                     c->d_xT,      c->d_G,       c->d_S,        c->d_part,   c->d_plane,  c->d_q5,
                     c->pc.d_ptr,  c->pc.d_idx,  c->pc.d_work,  c->pc.d_inv, c->d_wsoa,   c->f32.ng,
-                    c->f64.ng,    c->d_gdiag};
+                    c->f64.ng,    c->d_gdiag,   c->d_lin_ptr,  c->d_lin_cols, c->f64.la, c->f64.lp,
+                    c->f32.la,    c->f32.lp};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& r : c->prof.recs) {
@@ -202,7 +203,60 @@ int aimx_matvec_host(aimx_ctx* ctx, double freq, int nrhs, const void* x, void* 
 
 int aimx_set_path(aimx_ctx* ctx, int path) {
     if (!ctx || path < 0 || path > 2) return AIMX_E_ARG;
+    if (ctx->path != path) ctx->config_gen++;
     ctx->path = path;
+    return AIMX_OK;
+}
+
+int aimx_set_linear_term(aimx_ctx* ctx, int enable) {
+    if (!ctx || enable < 0 || enable > 1) return AIMX_E_ARG;
+    try {
+        if (enable) build_linterm(ctx);
+        if (ctx->linterm != enable) ctx->config_gen++;
+        ctx->linterm = enable;
+    } catch (const Error& e) {
+        return fail(ctx, e);
+    }
+    return AIMX_OK;
+}
+
+int aimx_export_linear_term(const aimx_ctx* ctx, int64_t* nlin, int64_t* row_ptr, int32_t* cols, double* na,
+                            double* nphi) {
+    if (!ctx) return AIMX_E_ARG;
+    aimx_ctx* c = const_cast<aimx_ctx*>(ctx);
+    if (!ctx->nlin) {
+        c->last_error = "the linear term has not been enabled on this context";
+        return AIMX_E_STATE;
+    }
+    try {
+        const int N = ctx->N;
+        const int64_t nl = ctx->nlin;
+        if (nlin) *nlin = nl;
+        if (row_ptr || cols || na || nphi) {
+            std::vector<double> va(nl), vp(nl);
+            AIMX_CUDA_TRY(cudaMemcpy(va.data(), ctx->f64.la, nl * sizeof(double), cudaMemcpyDeviceToHost));
+            AIMX_CUDA_TRY(cudaMemcpy(vp.data(), ctx->f64.lp, nl * sizeof(double), cudaMemcpyDeviceToHost));
+            std::vector<int64_t> rp(N + 1, 0);
+            for (int i = 0; i < N; ++i) rp[ctx->perm[i] + 1] = ctx->lin_ptr[i + 1] - ctx->lin_ptr[i];
+            for (int i = 0; i < N; ++i) rp[i + 1] += rp[i];
+            if (row_ptr) std::memcpy(row_ptr, rp.data(), sizeof(int64_t) * (N + 1));
+            std::vector<std::pair<int, int>> tmp;
+            for (int i = 0; i < N; ++i) {
+                tmp.clear();
+                for (int e = ctx->lin_ptr[i]; e < ctx->lin_ptr[i + 1]; ++e)
+                    tmp.push_back({ctx->perm[ctx->lin_cols[e]], e});
+                std::sort(tmp.begin(), tmp.end());
+                const int64_t base = rp[ctx->perm[i]];
+                for (size_t k = 0; k < tmp.size(); ++k) {
+                    if (cols) cols[base + k] = tmp[k].first;
+                    if (na) na[base + k] = va[tmp[k].second];
+                    if (nphi) nphi[base + k] = vp[tmp[k].second];
+                }
+            }
+        }
+    } catch (const Error& e) {
+        return fail(c, e);
+    }
     return AIMX_OK;
 }
 

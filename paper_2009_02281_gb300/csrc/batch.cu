@@ -26,6 +26,7 @@ struct aimx_batch {
     std::vector<int> nrhs;
     std::vector<const void*> x;
     std::vector<void*> y;
+    std::vector<int> gen;            // members' config_gen at capture
     size_t nodes = 0;
     std::string last_error;
 };
@@ -51,7 +52,9 @@ bool same_signature(const aimx_batch* b, const double* freqs, const int* nrhs, c
                     void* const* y) {
     if (!b->exec) return false;
     for (size_t i = 0; i < b->ctx.size(); ++i)
-        if (b->freq[i] != freqs[i] || b->nrhs[i] != nrhs[i] || b->x[i] != x[i] || b->y[i] != y[i]) return false;
+        if (b->freq[i] != freqs[i] || b->nrhs[i] != nrhs[i] || b->x[i] != x[i] || b->y[i] != y[i] ||
+            b->gen[i] != b->ctx[i]->config_gen)
+            return false;
     return true;
 }
 
@@ -102,6 +105,8 @@ void capture(aimx_batch* b, const double* freqs, const int* nrhs, const void* co
     b->nrhs.assign(nrhs, nrhs + n);
     b->x.assign(x, x + n);
     b->y.assign(y, y + n);
+    b->gen.resize(n);
+    for (size_t i = 0; i < n; ++i) b->gen[i] = b->ctx[i]->config_gen;
 }
 
 }  // namespace

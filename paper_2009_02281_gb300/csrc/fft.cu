@@ -333,6 +333,20 @@ Coefs near_coefs(const aimx_ctx* ctx, double freq) {
     Mats m = materials(ctx, freq);
     Coefs c;
     for (auto& v : c.near) v = make_double2(0, 0);
+    for (auto& v : c.lin) v = make_double2(0, 0);
+    if (ctx->linterm) {
+        // L = L^A - k^-2 L^Phi gains k^2 (N^A_lin - k^-2 N^Phi_lin) = k^2 N^A_lin - N^Phi_lin,
+        // scaled like L in each region's rows
+        for (int g = 0; g < m.nreg; ++g) {
+            const double k2 = m.k[g] * m.k[g];
+            c.lin[0] = c.lin[0] + jmul(m.w * m.mu[g] * k2);
+            c.lin[1] = c.lin[1] + jmul(-m.w * m.mu[g]);
+            if (ctx->form == AIMX_PMCHWT) {
+                c.lin[2] = c.lin[2] + jmul(kEta0 * kEta0 * m.w * m.eps[g] * k2);
+                c.lin[3] = c.lin[3] + jmul(-kEta0 * kEta0 * m.w * m.eps[g]);
+            }
+        }
+    }
     if (ctx->form == AIMX_EFIE) {
         c.near[0] = jmul(m.w * m.mu[0]);
         c.near[1] = jmul(-m.w * m.mu[0] / (m.k[0] * m.k[0]));

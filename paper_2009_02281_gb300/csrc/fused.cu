@@ -326,12 +326,15 @@ __global__ void __launch_bounds__(kThreads) k_xy_inv(const float2* __restrict__ 
 // ------------------------------------------------------------------ K5
 struct NearC {
     float2 c[6];
+    float2 lin[4];   // linear-term coefficients (J rows: A, Phi; M rows: A, Phi)
 };
 
 __global__ void __launch_bounds__(kThreads) k_final(const float2* __restrict__ part, const float2* __restrict__ xT,
                                                     const int* __restrict__ row_ptr, const int* __restrict__ cols,
                                                     const float* __restrict__ na, const float* __restrict__ np,
                                                     const float* __restrict__ nk, const int* __restrict__ perm,
+                                                    const int* __restrict__ lin_ptr, const int* __restrict__ lin_cols,
+                                                    const float* __restrict__ la, const float* __restrict__ lp,
                                                     float2* y, NearC nc, int F, int N, int nunk, int P, int B) {
     __shared__ float2 accE[kFinalRows][kFinalB];
     __shared__ float2 accH[kFinalRows][kFinalB];
@@ -359,6 +362,25 @@ __global__ void __launch_bounds__(kThreads) k_final(const float2* __restrict__ p
         for (int r = warp; r < kFinalRows; r += nwarps) {
             int i = i0 + r;
             if (i >= N) continue;
+            if (lin_ptr) {
+                // linear-term modification: a few overlapping pairs per row, added to this
+                // lane's own partial sums before the near correction
+                const int l1 = lin_ptr[i + 1];
+                for (int e = lin_ptr[i]; e < l1; ++e) {
+                    const int j = lin_cols[e];
+                    const float va = __ldg(la + e), vp = __ldg(lp + e);
+                    const float2 cJ = va * nc.lin[0] + vp * nc.lin[1];
+                    const float2 cM = va * nc.lin[2] + vp * nc.lin[3];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        int bl = lane + 32 * h;
+                        if (bl < nbc) {
+                            accE[r][bl] = accE[r][bl] + cJ * __ldg(xT + (int64_t)j * B + bc + bl);
+                            if (F == 8) accH[r][bl] = accH[r][bl] + cM * __ldg(xT + (int64_t)(N + j) * B + bc + bl);
+                        }
+                    }
+                }
+            }
             float2 aJ[2], pJ[2], kJ[2], aM[2], pM[2], kM[2];
             for (int h = 0; h < 2; ++h) aJ[h] = pJ[h] = kJ[h] = aM[h] = pM[h] = kM[h] = make_float2(0.f, 0.f);
             const int e1 = row_ptr[i + 1];
@@ -807,6 +829,8 @@ static void run_fused(aimx_ctx* ctx, const NearC& nc, int B, const float2* xb, f
     k_final<<<(N + kFinalRows - 1) / kFinalRows, kThreads, 0, s>>>(fb.part, fb.xT, ctx->d_row_ptr, ctx->d_cols,
                                                                    ctx->f32.na, ctx->f32.np,
                                                                    F == 8 ? ctx->f32.nk : ctx->f32.ng, ctx->d_perm,
+                                                                   ctx->linterm ? ctx->d_lin_ptr : nullptr,
+                                                                   ctx->d_lin_cols, ctx->f32.la, ctx->f32.lp,
                                                                    yb, nc, F, N, nunk, P, B);
     AIMX_CUDA_TRY(cudaGetLastError());
     delete sc;
@@ -816,6 +840,7 @@ static NearC near_c(const aimx_ctx* ctx, double freq) {
     Coefs cf = near_coefs(ctx, freq);
     NearC nc;
     for (int k = 0; k < 6; ++k) nc.c[k] = make_float2((float)cf.near[k].x, (float)cf.near[k].y);
+    for (int k = 0; k < 4; ++k) nc.lin[k] = make_float2((float)cf.lin[k].x, (float)cf.lin[k].y);
     return nc;
 }
 

@@ -18,6 +18,7 @@ namespace aimx {
 
 struct NearCoefs {
     double2 c[6];
+    double2 lin[4];   // linear-term coefficients (J rows: A, Phi; M rows: A, Phi)
 };
 
 // Fields per RHS: EFIE (Jx, Jy, Jz, rho); PMCHWT adds (Mx, My, Mz, rho_M).
@@ -113,6 +114,8 @@ __global__ void k_interp_near(const T* __restrict__ w, const int* __restrict__ a
                               const int* __restrict__ perm, const int* __restrict__ row_ptr,
                               const int* __restrict__ cols, const T* __restrict__ na,
                               const T* __restrict__ np, const T* __restrict__ nk,
+                              const int* __restrict__ lin_ptr, const int* __restrict__ lin_cols,
+                              const T* __restrict__ la, const T* __restrict__ lp,
                               const cplx_t<T>* __restrict__ grid, const cplx_t<T>* __restrict__ x,
                               cplx_t<T>* y, NearCoefs nc, int nrhs, int F, int N, int nunk, int P,
                               int Mx, int My, int Mz) {
@@ -134,6 +137,23 @@ __global__ void k_interp_near(const T* __restrict__ w, const int* __restrict__ a
             for (int f = 0; f < 4; ++f) rfma(aH, wi[4 * u + f], gb[(4 + f) * MT + node]);
     }
     const C* xb = x + (int64_t)b * nunk;
+    if (lin_ptr) {
+        // linear-term modification on the overlapping pairs
+        const C lA = mk((T)nc.lin[0].x, (T)nc.lin[0].y), lP = mk((T)nc.lin[1].x, (T)nc.lin[1].y);
+        const C mA = mk((T)nc.lin[2].x, (T)nc.lin[2].y), mP = mk((T)nc.lin[3].x, (T)nc.lin[3].y);
+        C sA = czero<T>(), sP = czero<T>(), tA = czero<T>(), tP = czero<T>();
+        for (int e = lin_ptr[i]; e < lin_ptr[i + 1]; ++e) {
+            const int j = perm[lin_cols[e]];
+            rfma(sA, la[e], xb[j]);
+            rfma(sP, lp[e], xb[j]);
+            if (F == 8) {
+                rfma(tA, la[e], xb[N + j]);
+                rfma(tP, lp[e], xb[N + j]);
+            }
+        }
+        aE = aE + lA * sA + lP * sP;
+        if (F == 8) aH = aH + mA * tA + mP * tP;
+    }
     C cA = mk((T)nc.c[0].x, (T)nc.c[0].y), cP = mk((T)nc.c[1].x, (T)nc.c[1].y);
     if (F == 4) {
         C sA = czero<T>(), sP = czero<T>(), sG = czero<T>();
@@ -215,6 +235,7 @@ void matvec_generic(aimx_ctx* ctx, double freq, int nrhs, const T* x, T* y, cuda
     Coefs cf = near_coefs(ctx, freq);
     NearCoefs nc;
     for (int k = 0; k < 6; ++k) nc.c[k] = cf.near[k];
+    for (int k = 0; k < 4; ++k) nc.lin[k] = cf.lin[k];
     const int F = ctx->F;
     const int64_t MT = (int64_t)ctx->M[0] * ctx->M[1] * ctx->M[2];
     const size_t per_rhs = (size_t)F * MT;
@@ -252,7 +273,8 @@ void matvec_generic(aimx_ctx* ctx, double freq, int nrhs, const T* x, T* y, cuda
             fft3d_padded<T>(reinterpret_cast<T*>(grid), nb * F, ctx->M, act, true, s);
         int64_t tn = (int64_t)ctx->N * nb;
         k_interp_near<T><<<(unsigned)((tn + 127) / 128), 128, 0, s>>>(
-            pd.w, ctx->d_anc, ctx->d_perm, ctx->d_row_ptr, ctx->d_cols, pd.na, pd.np, F == 8 ? pd.nk : pd.ng, grid,
+            pd.w, ctx->d_anc, ctx->d_perm, ctx->d_row_ptr, ctx->d_cols, pd.na, pd.np, F == 8 ? pd.nk : pd.ng,
+            ctx->linterm ? ctx->d_lin_ptr : nullptr, ctx->d_lin_cols, pd.la, pd.lp, grid,
             xc + (int64_t)b0 * ctx->nunk, yc + (int64_t)b0 * ctx->nunk, nc, nb, F, ctx->N, ctx->nunk,
             ctx->P, ctx->M[0], ctx->M[1], ctx->M[2]);
         AIMX_CUDA_TRY(cudaGetLastError());

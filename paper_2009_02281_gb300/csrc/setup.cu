@@ -150,6 +150,43 @@ __device__ inline void tri_potentials(const TriFrame& T, V3 r, double& I1, V3& J
     G = g - (sgn * bsum) * T.n;
 }
 
+// Potentials of the linear kernel R = |r - r'| (Sec. III-A-3):
+//   IR = int_T R dS',   JR = int_T (rho' - rho) R dS'.
+// With d the signed height of r over T and the per-edge quantities above,
+//   div'((rho' - rho) R) = 3 R - d^2 / R  gives  IR = (d^2 I1 + sum_i t0 E1_i) / 3,
+//   grad'(R^3) = 3 R (rho' - rho)           gives  JR = sum_i m_i E3_i / 3,
+// where E1 = int_edge R dl and E3 = int_edge R^3 dl in closed form.  f2 is set
+// to 0 where R0 = 0 (every term it enters carries a factor R0^2 or t0 there).
+__device__ inline void tri_r_potentials(const TriFrame& T, V3 r, double& IR, V3& JR, V3& rho) {
+    double d = dot(r - T.v[0], T.n);
+    rho = r - d * T.n;
+    double ad = fabs(d);
+    double i1 = 0.0, bsum = 0.0, e1 = 0.0;
+    V3 j = v3(0, 0, 0);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        V3 a = T.v[i], b = T.v[(i + 1) % 3];
+        double sm = dot(a - rho, T.lh[i]);
+        double sp = dot(b - rho, T.lh[i]);
+        double t0 = dot(a - rho, T.mh[i]);
+        double Rm = norm3(r - a);
+        double Rp = norm3(r - b);
+        double R02 = t0 * t0 + d * d;
+        double f2 = 0.0;
+        if (R02 > 0.0) f2 = (sp + sm >= 0.0) ? log((Rp + sp) / (Rm + sm)) : log((Rm - sm) / (Rp - sp));
+        double beta = atan2(t0 * sp, R02 + ad * Rp) - atan2(t0 * sm, R02 + ad * Rm);
+        i1 += t0 * f2;
+        bsum += beta;
+        double lin = sp * Rp - sm * Rm;
+        e1 += t0 * 0.5 * (lin + R02 * f2);
+        double E3 = 0.25 * (sp * Rp * Rp * Rp - sm * Rm * Rm * Rm) + 0.375 * R02 * lin + 0.375 * R02 * R02 * f2;
+        j = j + E3 * T.mh[i];
+    }
+    double I1 = i1 - ad * bsum;
+    IR = (d * d * I1 + e1) / 3.0;
+    JR = (1.0 / 3.0) * j;
+}
+
 // ------------------------------------------------------------------ device setup kernels
 
 struct GeomView {
@@ -283,6 +320,72 @@ __global__ void k_precorrect(const double* w, const int* anc, const int* row_of,
     NK32[e] = (float)nk;
 }
 
+// Linear-term modification (Sec. III-A-3, Eq. Lmatdecomplin), one thread per
+// overlapping pair (row i, column j): the direct integrals of the kernel
+// G_lin = -R / (8 pi) (closed-form inner potentials, 5 x 5 outer rule) minus
+// their precorrection with the sampled kernel H_lin[d] = -|d h| / (8 pi)
+// between the two stencils.  FP64 and FP32 copies.
+__global__ void k_linterm(GeomView g, const int* __restrict__ row_of, const int* __restrict__ cols, int64_t nlin,
+                          int nq, const double* __restrict__ w, const int* __restrict__ anc, int P, double hx,
+                          double hy, double hz, double* NA, double* NP, float* NA32, float* NP32) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= nlin) return;
+    const int i = row_of[e], j = cols[e];
+    double la = 0.0, lp = 0.0;
+    for (int ss = 0; ss < 2; ++ss) {
+        int ts = g.btri[2 * j + ss];
+        double sgs = ss == 0 ? 1.0 : -1.0;
+        double cs = g.blen[j] / (2.0 * g.area[ts]);
+        V3 ps = load3(g.xyz + 3 * g.bfree[2 * j + ss]);
+        TriFrame T;
+        make_frame(T, vtx(g, ts, 0), vtx(g, ts, 1), vtx(g, ts, 2));
+        for (int so = 0; so < 2; ++so) {
+            int to = g.btri[2 * i + so];
+            double sgo = so == 0 ? 1.0 : -1.0;
+            double Ao = g.area[to];
+            double co = g.blen[i] / (2.0 * Ao);
+            V3 po = load3(g.xyz + 3 * g.bfree[2 * i + so]);
+            V3 a = vtx(g, to, 0), b = vtx(g, to, 1), c = vtx(g, to, 2);
+            for (int q = 0; q < nq; ++q) {
+                V3 r = c_qnear[4 * q] * a + c_qnear[4 * q + 1] * b + c_qnear[4 * q + 2] * c;
+                double W = c_qnear[4 * q + 3] * Ao;
+                double IR;
+                V3 JR, rho;
+                tri_r_potentials(T, r, IR, JR, rho);
+                V3 fo = (sgo * co) * (r - po);
+                V3 vp = (sgs * cs) * (JR + IR * (rho - ps));
+                la += W * dot(fo, vp);
+                lp += W * (sgo * 2.0 * co) * (sgs * 2.0 * cs) * IR;
+            }
+        }
+    }
+    const double inv8pi = 1.0 / (8.0 * kPi);
+    la *= -inv8pi;
+    lp *= -inv8pi;
+    const int U = P * P * P;
+    const int dx0 = anc[3 * i] - anc[3 * j], dy0 = anc[3 * i + 1] - anc[3 * j + 1],
+              dz0 = anc[3 * i + 2] - anc[3 * j + 2];
+    const double* wi = w + (size_t)i * U * 4;
+    const double* wj = w + (size_t)j * U * 4;
+    double pa = 0.0, pp = 0.0;
+    for (int u = 0; u < U; ++u) {
+        int ux = u % P, uy = (u / P) % P, uz = u / (P * P);
+        double a0 = wi[4 * u], a1 = wi[4 * u + 1], a2 = wi[4 * u + 2], a3 = wi[4 * u + 3];
+        for (int v = 0; v < U; ++v) {
+            int vx = v % P, vy = (v / P) % P, vz = v / (P * P);
+            double rx = (dx0 + ux - vx) * hx, ry = (dy0 + uy - vy) * hy, rz = (dz0 + uz - vz) * hz;
+            double hl = -sqrt(rx * rx + ry * ry + rz * rz) * inv8pi;
+            const double* b = wj + 4 * v;
+            pa += hl * (a0 * b[0] + a1 * b[1] + a2 * b[2]);
+            pp += hl * a3 * b[3];
+        }
+    }
+    NA[e] = la - pa;
+    NP[e] = lp - pp;
+    NA32[e] = (float)(la - pa);
+    NP32[e] = (float)(lp - pp);
+}
+
 // Surface-impedance Gram matrix on the near pattern: G_mn = int f_m . f_n dS over
 // the triangles m and n share (a degree-2 integrand; the 5 x 5 collapsed rule
 // q5 is exact).  Internal order; also the self terms into gdiag.
@@ -373,6 +476,50 @@ static void build_gram(aimx_ctx* ctx, const GeomView& gv, const int* d_row_of) {
                                                    ctx->d_gdiag);
     k_to_float<<<(unsigned)((nnz + 255) / 256), 256>>>(ctx->f64.ng, ctx->f32.ng, (size_t)nnz);
     AIMX_CUDA_TRY(cudaGetLastError());
+}
+
+void build_linterm(aimx_ctx* ctx) {
+    if (ctx->nlin) return;
+    const int N = ctx->N;
+    // bases on each triangle (internal ids); pairs that share one overlap
+    std::vector<std::vector<int>> on_tri(ctx->nt);
+    for (int i = 0; i < N; ++i) {
+        const int o = ctx->perm[i];
+        on_tri[ctx->h_tp[o]].push_back(i);
+        on_tri[ctx->h_tm[o]].push_back(i);
+    }
+    std::vector<int> ptr(N + 1, 0), cols, row_of;
+    std::vector<int> nb;
+    for (int i = 0; i < N; ++i) {
+        const int o = ctx->perm[i];
+        nb.clear();
+        for (int t : {ctx->h_tp[o], ctx->h_tm[o]}) nb.insert(nb.end(), on_tri[t].begin(), on_tri[t].end());
+        std::sort(nb.begin(), nb.end());
+        nb.erase(std::unique(nb.begin(), nb.end()), nb.end());
+        cols.insert(cols.end(), nb.begin(), nb.end());
+        row_of.insert(row_of.end(), nb.size(), i);
+        ptr[i + 1] = (int)cols.size();
+    }
+    const int64_t nl = (int64_t)cols.size();
+    int* d_row_of = upload(ctx, row_of);
+    ctx->d_lin_ptr = upload(ctx, ptr);
+    ctx->d_lin_cols = upload(ctx, cols);
+    ctx->f64.la = (double*)dev_alloc(ctx, sizeof(double) * nl);
+    ctx->f64.lp = (double*)dev_alloc(ctx, sizeof(double) * nl);
+    ctx->f32.la = (float*)dev_alloc(ctx, sizeof(float) * nl);
+    ctx->f32.lp = (float*)dev_alloc(ctx, sizeof(float) * nl);
+    GeomView gv{ctx->d_xyz, ctx->d_tri, ctx->d_area, ctx->d_btri, ctx->d_bfree, ctx->d_blen};
+    k_linterm<<<(unsigned)((nl + 127) / 128), 128>>>(gv, d_row_of, ctx->d_lin_cols, nl, 25, ctx->f64.w, ctx->d_anc,
+                                                     ctx->P, ctx->h[0], ctx->h[1], ctx->h[2], ctx->f64.la,
+                                                     ctx->f64.lp, ctx->f32.la, ctx->f32.lp);
+    cudaError_t e1 = cudaGetLastError();
+    cudaError_t e2 = cudaDeviceSynchronize();
+    dev_free(ctx, d_row_of);
+    AIMX_CUDA_TRY(e1);
+    AIMX_CUDA_TRY(e2);
+    ctx->lin_ptr = ptr;
+    ctx->lin_cols = cols;
+    ctx->nlin = nl;
 }
 
 void setup_context(aimx_ctx* ctx, const aimx_mesh* mesh, const aimx_material* mat,

@@ -182,3 +182,21 @@ def test_matvec_matches_dense(sphere):
     y = linterm.matvec_efie_lin(prob, f, x, lin=lin)
     Z = linterm.dense_efie_lin(prob, f, lin=lin)
     assert np.linalg.norm(y - Z @ x) <= 1e-12 * np.linalg.norm(y)
+
+
+def test_pmchwt_with_equal_media_doubles_the_efie_term(sphere):
+    """With identical media the two regions' L terms coincide: the E rows gain twice the EFIE term."""
+    from synth import random_complex
+    prob, lin = sphere
+    N = prob["N"]
+    f = 0.3 * C0
+    xJ = random_complex((N,), seed=6)
+    x = np.concatenate([xJ, np.zeros(N, dtype=np.complex128)])
+    dP = linterm.matvec_pmchwt_lin(prob, f, x, 1.0, 1.0, lin=lin) - op.matvec_pmchwt(prob, f, x, 1.0, 1.0)
+    dE = linterm.matvec_efie_lin(prob, f, xJ, lin=lin) - op.matvec_efie(prob, f, xJ)
+    assert np.linalg.norm(dP[:N] - 2 * dE) <= 1e-12 * np.linalg.norm(dE)
+    assert np.linalg.norm(dP[N:]) == 0.0
+    xM = np.concatenate([np.zeros(N, dtype=np.complex128), xJ])
+    dM = linterm.matvec_pmchwt_lin(prob, f, xM, 1.0, 1.0, lin=lin) - op.matvec_pmchwt(prob, f, xM, 1.0, 1.0)
+    # eta0^2 j w eps0 = j w mu0: the H rows gain the same as the E rows
+    assert np.linalg.norm(dM[N:] - 2 * dE) <= 1e-12 * np.linalg.norm(dE)
