@@ -265,6 +265,31 @@ int aimx_matvec_path(const aimx_ctx* ctx, int precision);
  * Off by default, as in the paper's numerical results. */
 int aimx_set_linear_term(aimx_ctx* ctx, int enable);
 
+/* ------------------------------------------------------------------ conventional-AIM comparison mode
+ * Sec. II-B: the method AIMx is compared against.  With enable = 1 the
+ * products of this EFIE context (aimx_matvec in both precisions and paths,
+ * aimx_solve, aimx_sweep, batches, aimx_matvec_noalloc) use, on the near
+ * pairs, entries recomputed at every new frequency:
+ *     j w mu [N^A(k) - k^-2 N^Phi(k)],   N(k) = L_NR(k) - L_P(k),
+ * L_NR(k) the full-wave direct integrals (static part: closed-form inner
+ * potentials and the 5 x 5 outer rule; smooth part G_d(k) = (e^{-jkR} - 1) /
+ * (4 pi R): the 5 x 5 product rule on both triangles) and L_P(k) their
+ * precorrection with the grid kernel H(k).  The far part is the unchanged grid
+ * product, so near entries equal the full-wave Galerkin entries and far ones
+ * the AIMx ones.
+ *   - The fill runs on the product's stream when the frequency changes (stage
+ *     "aim_near_fill" of aimx_profile); it synchronises that stream once.
+ *   - Preconditioners keep the static self terms; the linear-term
+ *     modification is ignored while this mode is on (the near pairs are exact).
+ *   - AIMX_E_STATE for AIMX_PMCHWT contexts.  enable = 0 returns to AIMx.
+ * Off by default. */
+int aimx_set_conventional_aim(aimx_ctx* ctx, int enable);
+
+/* The conventional-AIM near entries at freq as complex float64 pairs z [nnz][2],
+ * in the near pattern of aimx_export_setup (caller numbering, columns
+ * ascending).  AIMX_E_STATE unless the mode is on.  Synchronous. */
+int aimx_export_aim_near(aimx_ctx* ctx, double freq, double* z);
+
 /* Copy the linear-term values to host arrays in caller numbering (any output
  * pointer may be NULL): nlin = number of overlapping pairs; row_ptr int64
  * [N+1]; cols int32 [nlin] (ascending per row); na, nphi double [nlin] =

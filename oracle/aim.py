@@ -43,8 +43,14 @@ def G_d(k, R):
     return np.where(R > 0, re + 1j * im, -1j * k / (4.0 * np.pi))
 
 
-def dynamic_direct(rwg, rows, cols, k, q=Q_DYN):
+def dynamic_direct(rwg, rows, cols, k, q=Q_DYN, chunk=2000):
     """(L^A_d, L^Phi_d): int int (f_m . f_n, div f_m div' f_n) G_d(k, R) by the product rule."""
+    rows = np.asarray(rows)
+    cols = np.asarray(cols)
+    if len(rows) > chunk:
+        parts = [dynamic_direct(rwg, rows[c:c + chunk], cols[c:c + chunk], k, q, chunk)
+                 for c in range(0, len(rows), chunk)]
+        return np.concatenate([p[0] for p in parts]), np.concatenate([p[1] for p in parts])
     T, P, C, S = rwg_arrays(rwg)
     xyz, tri, area = rwg["xyz"], rwg["tri"], rwg["area"]
     bary, w = triangle_rule(q)

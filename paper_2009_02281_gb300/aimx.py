@@ -82,6 +82,8 @@ _SIGS = [
     ("aimx_set_path", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("aimx_set_linear_term", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("aimx_export_linear_term", ctypes.c_int, [ctypes.c_void_p] * 6),
+    ("aimx_set_conventional_aim", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("aimx_export_aim_near", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p]),
     ("aimx_matvec_path", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("aimx_profile", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("aimx_profile_read", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
@@ -385,6 +387,16 @@ class Context:
     def set_linear_term(self, enable=True):
         """Linear-term modification of Sec. III-A-3 on overlapping pairs (built on the first enable)."""
         self._check(self._lib.aimx_set_linear_term(self._ctx, 1 if enable else 0))
+
+    def set_conventional_aim(self, enable=True):
+        """Conventional-AIM comparison mode (Sec. II-B): near entries refilled at every new frequency."""
+        self._check(self._lib.aimx_set_conventional_aim(self._ctx, 1 if enable else 0))
+
+    def export_aim_near(self, freq):
+        """Conventional-AIM near entries at freq, complex [nnz], in export_setup's near order."""
+        z = np.zeros((self.info["near_nnz"], 2))
+        self._check(self._lib.aimx_export_aim_near(self._ctx, float(freq), _ptr(z)))
+        return z[:, 0] + 1j * z[:, 1]
 
     def export_linear_term(self):
         """{row_ptr, cols, NA, NP}: N^A_lin, N^Phi_lin on the overlapping pairs, caller numbering."""

@@ -63,6 +63,7 @@ struct PrecData {
     T* ng = nullptr;       // near Gram matrix [nnz] (surface impedance, EFIE with sigma > 0)
     T* la = nullptr;       // linear-term N^A_lin on the overlap pattern [nlin] (when enabled)
     T* lp = nullptr;       // linear-term N^Phi_lin on the overlap pattern [nlin]
+    T* zn = nullptr;       // conventional-AIM near entries j w mu (N^A(k) - k^-2 N^Phi(k)) [nnz] complex
     T* spec = nullptr;     // octant spectra [nspec][Oz][Oy][Ox] complex (2 T each)
     double spec_freq = -1.0;
     // work buffers of the generic FFT path
@@ -87,6 +88,7 @@ enum Stage {
     ST_SOLVE_RESIDUAL,
     ST_SOLVE_PRECOND,
     ST_SOLVE_REORTH,
+    ST_AIM_FILL,
     ST_COUNT
 };
 
@@ -207,6 +209,12 @@ struct aimx_ctx {
     int* d_lin_ptr = nullptr;
     int* d_lin_cols = nullptr;
     int config_gen = 0;            // bumped when a setting that changes the product's kernels changes
+    // conventional-AIM comparison mode (Sec. II-B): per-frequency near fill
+    int aim = 0;                   // 1 = products use the per-frequency near entries f32/f64.zn
+    double aim_freq = -1.0;        // frequency the zn arrays were filled for
+    int* d_aim_row_of = nullptr;   // [nnz] row of each near entry
+    double* d_aim_htab = nullptr;  // H(k) on offsets [-span, span]^3, complex
+    std::vector<double2> h_aim_htab;
     // host copies for port definitions (caller order)
     std::vector<double> h_xyz;     // [nv][3]
     std::vector<int> h_ea, h_eb, h_tp, h_tm;   // [N] edge vertices, T+ / T-
@@ -260,6 +268,9 @@ struct StaticData {
 };
 // overlap pattern and N^A_lin, N^Phi_lin (direct - precorrection), built once on demand
 void build_linterm(aimx_ctx* ctx);
+// aim.cu: conventional-AIM mode buffers, and the near fill for a frequency (no-op when current)
+void aim_enable(aimx_ctx* ctx);
+void ensure_aim_near(aimx_ctx* ctx, double freq, cudaStream_t s);
 void setup_context(aimx_ctx* ctx, const aimx_mesh* mesh, const aimx_material* mat,
                    const aimx_grid* grid, int order, const StaticData* pre = nullptr);
 

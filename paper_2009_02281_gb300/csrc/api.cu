@@ -41,7 +41,7 @@ static void free_all(aimx_ctx* c) {
                     c->d_xT,      c->d_G,       c->d_S,        c->d_part,   c->d_plane,  c->d_q5,
                     c->pc.d_ptr,  c->pc.d_idx,  c->pc.d_work,  c->pc.d_inv, c->d_wsoa,   c->f32.ng,
                     c->f64.ng,    c->d_gdiag,   c->d_lin_ptr,  c->d_lin_cols, c->f64.la, c->f64.lp,
-                    c->f32.la,    c->f32.lp};
+                    c->f32.la,    c->f32.lp,    c->f64.zn,     c->f32.zn,     c->d_aim_row_of, c->d_aim_htab};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& r : c->prof.recs) {
@@ -82,7 +82,7 @@ static const char* kStageNames[ST_COUNT] = {
     "kernel_spectra", "transpose_x", "gather_projection", "xy_fft_forward", "z_fft_mix_inverse",
     "xy_fft_inverse_interp", "near_final", "generic_projection", "generic_fft", "generic_mix",
     "generic_interp_near", "solver_vector_ops", "solver_true_residual", "solver_precond",
-    "solver_reorthogonalization"};
+    "solver_reorthogonalization", "aim_near_fill"};
 
 }  // namespace aimx
 
@@ -214,6 +214,49 @@ int aimx_set_linear_term(aimx_ctx* ctx, int enable) {
         if (enable) build_linterm(ctx);
         if (ctx->linterm != enable) ctx->config_gen++;
         ctx->linterm = enable;
+    } catch (const Error& e) {
+        return fail(ctx, e);
+    }
+    return AIMX_OK;
+}
+
+int aimx_set_conventional_aim(aimx_ctx* ctx, int enable) {
+    if (!ctx || enable < 0 || enable > 1) return AIMX_E_ARG;
+    try {
+        if (enable) aim_enable(ctx);
+        if (ctx->aim != enable) ctx->config_gen++;
+        ctx->aim = enable;
+    } catch (const Error& e) {
+        return fail(ctx, e);
+    }
+    return AIMX_OK;
+}
+
+int aimx_export_aim_near(aimx_ctx* ctx, double freq, double* z) {
+    if (!ctx || !z) return AIMX_E_ARG;
+    if (!ctx->aim) {
+        ctx->last_error = "the conventional-AIM mode is not enabled on this context";
+        return AIMX_E_STATE;
+    }
+    try {
+        ensure_aim_near(ctx, freq, 0);
+        std::vector<double2> v(ctx->nnz);
+        AIMX_CUDA_TRY(cudaMemcpy(v.data(), ctx->f64.zn, ctx->nnz * sizeof(double2), cudaMemcpyDeviceToHost));
+        const int N = ctx->N;
+        std::vector<int64_t> rp(N + 1, 0);
+        for (int i = 0; i < N; ++i) rp[ctx->perm[i] + 1] = ctx->row_ptr[i + 1] - ctx->row_ptr[i];
+        for (int i = 0; i < N; ++i) rp[i + 1] += rp[i];
+        std::vector<std::pair<int, int>> tmp;
+        for (int i = 0; i < N; ++i) {
+            tmp.clear();
+            for (int e = ctx->row_ptr[i]; e < ctx->row_ptr[i + 1]; ++e) tmp.push_back({ctx->perm[ctx->cols[e]], e});
+            std::sort(tmp.begin(), tmp.end());
+            const int64_t base = rp[ctx->perm[i]];
+            for (size_t k = 0; k < tmp.size(); ++k) {
+                z[2 * (base + k)] = v[tmp[k].second].x;
+                z[2 * (base + k) + 1] = v[tmp[k].second].y;
+            }
+        }
     } catch (const Error& e) {
         return fail(ctx, e);
     }

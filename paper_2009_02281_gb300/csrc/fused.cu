@@ -335,7 +335,8 @@ __global__ void __launch_bounds__(kThreads) k_final(const float2* __restrict__ p
                                                     const float* __restrict__ nk, const int* __restrict__ perm,
                                                     const int* __restrict__ lin_ptr, const int* __restrict__ lin_cols,
                                                     const float* __restrict__ la, const float* __restrict__ lp,
-                                                    float2* y, NearC nc, int F, int N, int nunk, int P, int B) {
+                                                    const float2* __restrict__ zn, float2* y, NearC nc, int F, int N,
+                                                    int nunk, int P, int B) {
     __shared__ float2 accE[kFinalRows][kFinalB];
     __shared__ float2 accH[kFinalRows][kFinalB];
     const int G = F / 4;
@@ -384,6 +385,23 @@ __global__ void __launch_bounds__(kThreads) k_final(const float2* __restrict__ p
             float2 aJ[2], pJ[2], kJ[2], aM[2], pM[2], kM[2];
             for (int h = 0; h < 2; ++h) aJ[h] = pJ[h] = kJ[h] = aM[h] = pM[h] = kM[h] = make_float2(0.f, 0.f);
             const int e1 = row_ptr[i + 1];
+            if (zn) {
+                // conventional-AIM mode (EFIE): complex per-frequency entries, coefficient folded in
+                for (int e = row_ptr[i]; e < e1; ++e) {
+                    const int j = cols[e];
+                    const float2 z = __ldg(zn + e);
+                    const float vk = nk ? __ldg(nk + e) : 0.f;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        int bl = lane + 32 * h;
+                        if (bl < nbc) {
+                            float2 xj = __ldg(xT + (int64_t)j * B + bc + bl);
+                            cfma(aJ[h], z, xj);
+                            if (nk) rfma(kJ[h], vk, xj);
+                        }
+                    }
+                }
+            } else
             for (int e = row_ptr[i]; e < e1; ++e) {
                 int j = cols[e];
                 float va = __ldg(na + e), vp = __ldg(np + e);
@@ -829,8 +847,10 @@ static void run_fused(aimx_ctx* ctx, const NearC& nc, int B, const float2* xb, f
     k_final<<<(N + kFinalRows - 1) / kFinalRows, kThreads, 0, s>>>(fb.part, fb.xT, ctx->d_row_ptr, ctx->d_cols,
                                                                    ctx->f32.na, ctx->f32.np,
                                                                    F == 8 ? ctx->f32.nk : ctx->f32.ng, ctx->d_perm,
-                                                                   ctx->linterm ? ctx->d_lin_ptr : nullptr,
+                                                                   ctx->linterm && !ctx->aim ? ctx->d_lin_ptr : nullptr,
                                                                    ctx->d_lin_cols, ctx->f32.la, ctx->f32.lp,
+                                                                   ctx->aim ? reinterpret_cast<const float2*>(ctx->f32.zn)
+                                                                            : nullptr,
                                                                    yb, nc, F, N, nunk, P, B);
     AIMX_CUDA_TRY(cudaGetLastError());
     delete sc;
@@ -841,6 +861,13 @@ static NearC near_c(const aimx_ctx* ctx, double freq) {
     NearC nc;
     for (int k = 0; k < 6; ++k) nc.c[k] = make_float2((float)cf.near[k].x, (float)cf.near[k].y);
     for (int k = 0; k < 4; ++k) nc.lin[k] = make_float2((float)cf.lin[k].x, (float)cf.lin[k].y);
+    if (ctx->aim) {
+        // the per-frequency entries carry j w mu and -j w mu / k^2 already; they are exact on the
+        // near pairs, so the linear-term modification does not apply
+        nc.c[0] = make_float2(1.f, 0.f);
+        nc.c[1] = make_float2(0.f, 0.f);
+        for (auto& v : nc.lin) v = make_float2(0.f, 0.f);
+    }
     return nc;
 }
 
@@ -878,6 +905,7 @@ void matvec_fused(aimx_ctx* ctx, double freq, int nrhs, const float* x, float* y
         StageScope sc(ctx, ST_KERNELGEN, s);
         ensure_spectra<float>(ctx, freq, s);
     }
+    ensure_aim_near(ctx, freq, s);
     ensure_plane_table(ctx);
     ensure_const_twiddles();
     const NearC nc = near_c(ctx, freq);
@@ -915,6 +943,7 @@ size_t fused_scratch_bytes(const aimx_ctx* ctx, int B) {
 void matvec_fused_into(aimx_ctx* ctx, double freq, int B, const float* x, float* y, cudaStream_t s,
                        unsigned char* scratch) {
     ensure_spectra<float>(ctx, freq, s);
+    ensure_aim_near(ctx, freq, s);
     const NearC nc = near_c(ctx, freq);
     const size_t NG = (size_t)ctx->n[0] * ctx->n[1] * ctx->n[2];
     const size_t F = ctx->F;

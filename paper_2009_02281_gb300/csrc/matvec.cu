@@ -116,6 +116,7 @@ __global__ void k_interp_near(const T* __restrict__ w, const int* __restrict__ a
                               const T* __restrict__ np, const T* __restrict__ nk,
                               const int* __restrict__ lin_ptr, const int* __restrict__ lin_cols,
                               const T* __restrict__ la, const T* __restrict__ lp,
+                              const cplx_t<T>* __restrict__ zn,
                               const cplx_t<T>* __restrict__ grid, const cplx_t<T>* __restrict__ x,
                               cplx_t<T>* y, NearCoefs nc, int nrhs, int F, int N, int nunk, int P,
                               int Mx, int My, int Mz) {
@@ -157,11 +158,20 @@ __global__ void k_interp_near(const T* __restrict__ w, const int* __restrict__ a
     C cA = mk((T)nc.c[0].x, (T)nc.c[0].y), cP = mk((T)nc.c[1].x, (T)nc.c[1].y);
     if (F == 4) {
         C sA = czero<T>(), sP = czero<T>(), sG = czero<T>();
-        for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
-            C xj = xb[perm[cols[e]]];
-            rfma(sA, na[e], xj);
-            rfma(sP, np[e], xj);
-            if (nk) rfma(sG, nk[e], xj);   // Gram matrix (surface impedance)
+        if (zn) {
+            // conventional-AIM mode: complex per-frequency entries, coefficient folded in (cA = 1, cP = 0)
+            for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+                C xj = xb[perm[cols[e]]];
+                cfma(sA, zn[e], xj);
+                if (nk) rfma(sG, nk[e], xj);
+            }
+        } else {
+            for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+                C xj = xb[perm[cols[e]]];
+                rfma(sA, na[e], xj);
+                rfma(sP, np[e], xj);
+                if (nk) rfma(sG, nk[e], xj);   // Gram matrix (surface impedance)
+            }
         }
         aE = aE + cA * sA + cP * sP;
         if (nk) aE = aE + mk((T)nc.c[2].x, (T)nc.c[2].y) * sG;
@@ -236,6 +246,12 @@ void matvec_generic(aimx_ctx* ctx, double freq, int nrhs, const T* x, T* y, cuda
     NearCoefs nc;
     for (int k = 0; k < 6; ++k) nc.c[k] = cf.near[k];
     for (int k = 0; k < 4; ++k) nc.lin[k] = cf.lin[k];
+    ensure_aim_near(ctx, freq, s);
+    if (ctx->aim) {
+        nc.c[0] = make_double2(1.0, 0.0);
+        nc.c[1] = make_double2(0.0, 0.0);
+        for (auto& v : nc.lin) v = make_double2(0.0, 0.0);
+    }
     const int F = ctx->F;
     const int64_t MT = (int64_t)ctx->M[0] * ctx->M[1] * ctx->M[2];
     const size_t per_rhs = (size_t)F * MT;
@@ -274,7 +290,8 @@ void matvec_generic(aimx_ctx* ctx, double freq, int nrhs, const T* x, T* y, cuda
         int64_t tn = (int64_t)ctx->N * nb;
         k_interp_near<T><<<(unsigned)((tn + 127) / 128), 128, 0, s>>>(
             pd.w, ctx->d_anc, ctx->d_perm, ctx->d_row_ptr, ctx->d_cols, pd.na, pd.np, F == 8 ? pd.nk : pd.ng,
-            ctx->linterm ? ctx->d_lin_ptr : nullptr, ctx->d_lin_cols, pd.la, pd.lp, grid,
+            ctx->linterm && !ctx->aim ? ctx->d_lin_ptr : nullptr, ctx->d_lin_cols, pd.la, pd.lp,
+            ctx->aim ? reinterpret_cast<const C*>(pd.zn) : nullptr, grid,
             xc + (int64_t)b0 * ctx->nunk, yc + (int64_t)b0 * ctx->nunk, nc, nb, F, ctx->N, ctx->nunk,
             ctx->P, ctx->M[0], ctx->M[1], ctx->M[2]);
         AIMX_CUDA_TRY(cudaGetLastError());
