@@ -258,6 +258,28 @@ def measure_config1(args, ws):
                    "aim_converged": sum(1 for q in ast if q["status"] == 0),
                    "aim_iterations_mean": round(float(np.mean([q["iterations"] for q in ast])), 1),
                    "status": arc}
+    # the same sweep with the AIMx CFIE (Sec. III-B): the closed sphere passes through its first
+    # interior resonance (ka ~ 2.74) inside the band, where the EFIE's iteration count peaks
+    cfie_cmp = None
+    if not args.no_cfie:
+        from paper_2009_02281_gb300 import CFIE
+        cc = Context(wl["xyz"], wl["tri"], wl["grid_n"], order=wl["order"], formulation=CFIE,
+                     near_radius=wl["radius"])
+        cc.solve(f, cc.rhs_planewave(f, [[0.0, 0.0, 1.0]], [[1.0, 0.0, 0.0]]), tol=1e-6, inner_precision=F64)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        _, cst, crc = cc.sweep(freqs, [[0.0, 0.0, 1.0]], [[1.0, 0.0, 0.0]], tol=1e-6, inner_precision=F64)
+        torch.cuda.synchronize()
+        cfie_s = time.perf_counter() - t
+        cc.close()
+        it_e = [q["iterations"] for q in sst]
+        it_c = [q["iterations"] for q in cst]
+        cfie_cmp = {"sweep_s": round(cfie_s, 3), "solves_per_s": round(ws * len(freqs) / cfie_s, 2),
+                    "converged": sum(1 for q in cst if q["status"] == 0), "status": crc,
+                    "iterations_mean": round(float(np.mean(it_c)), 1), "iterations_max": int(max(it_c)),
+                    "efie_iterations_max": int(max(it_e)),
+                    "efie_peak_ka": round(float(freqs[int(np.argmax(it_e))] * 2 * np.pi / C0), 3),
+                    "path": "generic (8 grid fields per RHS)", "alpha": 0.5}
     torch.cuda.synchronize()
     t = time.perf_counter()
     nsol = 5
@@ -268,7 +290,8 @@ def measure_config1(args, ws):
     ctx.close()
     return {"workload": "pec_sphere_1920", "setup_s": round(setup_s, 3), "fp64_matvec_us": round(us, 1),
             "solve_ms": round(1e3 * dt, 2), "solves_per_s": round(ws / dt, 2), "iterations": st[0]["iterations"],
-            "rel_residual": st[0]["rel_residual"], "status": rc, "sweep": sweep, "conventional_aim": aim_cmp}
+            "rel_residual": st[0]["rel_residual"], "status": rc, "sweep": sweep, "conventional_aim": aim_cmp,
+            "cfie_sweep": cfie_cmp}
 
 
 def learned_eval(args):
@@ -662,6 +685,7 @@ def main():
     ap.add_argument("--no-solves", action="store_true", help="skip the batched solve measurement")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 product measurement")
     ap.add_argument("--no-config1", action="store_true", help="skip the 1920-unknown FP64 latency measurement")
+    ap.add_argument("--no-cfie", action="store_true", help="skip the CFIE sweep of the 1920-unknown sphere")
     ap.add_argument("--no-aim", action="store_true",
                     help="skip the conventional-AIM sweep of the 1920-unknown sphere")
     ap.add_argument("--no-linear-term", action="store_true",

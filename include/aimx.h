@@ -66,6 +66,7 @@ typedef struct {
 
 #define AIMX_EFIE    0   /* PEC body in a homogeneous background (Eq. EFIEAIMx)          */
 #define AIMX_PMCHWT  1   /* penetrable body, two regions, unknowns [J ; M/eta0]            */
+#define AIMX_CFIE    2   /* closed PEC body, combined field (Sec. III-B), unknowns J       */
 
 /* Materials.  Relative permittivity / permeability of the background (region
  * 1) and, for AIMX_PMCHWT, of the body (region 2); lossless values.  sigma:
@@ -73,12 +74,24 @@ typedef struct {
  * condition (skin effect, cited in Sec. VI): the system becomes Z + Z_s(w) G
  * with Z_s = (1 + j)/(sigma delta), delta = sqrt(2/(w mu0 sigma)) and G the
  * RWG Gram matrix, a static near-region matrix like N^A.  0 = perfect
- * conductor.  Ignored for AIMX_PMCHWT. */
+ * conductor.  Ignored for AIMX_PMCHWT.
+ *
+ * AIMX_CFIE (Eqs. CFIEout, CFIEAIMx): a closed PEC surface whose triangles are
+ * ordered counter-clockwise about the outward normal.  The system is
+ *   Z_C = alpha Z_E + (1 - alpha) eta Z_M,  Z_M = G / 2 + K_g,
+ * with Z_E the EFIE matrix (including the surface impedance when sigma > 0),
+ * G the RWG Gram matrix (the residue term), (K_g)_mn = <n x f_m, PV K[f_n]>
+ * and K[X] = int grad G x X dS' (the MFIE J/2 - n x PV K[J] = n x H_inc
+ * tested with f_m); eta the background wave impedance.  cfie_alpha in (0, 1],
+ * 0 selects 1/2.  Right-hand sides: alpha <f, E_inc> + (1 - alpha) eta
+ * <f, n x H_inc>.  Products run on the generic path (aimx_matvec_path
+ * returns 1 or 2). */
 typedef struct {
     int32_t formulation;
     double eps_out, mu_out;
     double eps_in, mu_in;
     double sigma;
+    double cfie_alpha;
 } aimx_material;
 
 /* Auxiliary grid (Sec. II-B).  n: nodes per axis (required).  h: spacing per
@@ -170,6 +183,9 @@ int aimx_matvec_host(aimx_ctx* ctx, double freq, int nrhs, const void* x, void* 
                                   by the network attached with aimx_gnn_attach (not in the paper; the learned
                                   analogue of augmenting the diagonal of L_s with off-diagonal entries,
                                   Sec. III-A-2).  Linear in the vector, so GMRES stays valid. */
+/* AIMX_CFIE contexts take AIMX_PRECOND_DIAG (static self terms of all three
+ * operators and the residue) or AIMX_PRECOND_NONE; _BLOCK and _LEARNED return
+ * AIMX_E_STATE. */
 
 typedef struct {
     double tol;               /* target relative true residual |b - A x| / |b| (0 = 1e-6)            */
@@ -387,7 +403,8 @@ int aimx_sweep_ports(aimx_ctx* ctx, int nf, const double* freqs, int nport, cons
  * resolved grid, order, FP64 projection weights, precorrected near matrices
  * N^A, N^Phi, N^K and static self terms: the static part that AIMx computes
  * once for all frequencies, Sec. III-A) written to / read from a binary file
- * (native byte order, FNV-1a checksum).  aimx_load_static rebuilds the
+ * (native byte order, FNV-1a checksum; version 2 stores the CFIE weight,
+ * version 1 files still load).  aimx_load_static rebuilds the
  * topology from the stored mesh and restores the stored arrays instead of
  * recomputing the near integrals; the new context computes the same products
  * bit for bit.  Errors: AIMX_E_ARG (null arguments), AIMX_E_IO (I/O failure,

@@ -4,5 +4,5 @@ The compute path is the CUDA library ``libaimx.so`` (sources in ``csrc/``, C ABI
 ``include/aimx.h``); ``aimx`` is its thin ctypes binding.
 """
 
-from .aimx import (AimxError, Batch, Context, Gnn, Port, EFIE, PMCHWT, F32, F64, PRECOND_DIAG, PRECOND_NONE,  # noqa: F401
+from .aimx import (AimxError, Batch, Context, Gnn, Port, EFIE, PMCHWT, CFIE, F32, F64, PRECOND_DIAG, PRECOND_NONE,  # noqa: F401
                    PRECOND_BLOCK, PRECOND_LEARNED, load)

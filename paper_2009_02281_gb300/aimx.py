@@ -13,6 +13,7 @@ from . import build as _build
 
 EFIE = 0
 PMCHWT = 1
+CFIE = 2
 F32 = 0
 F64 = 1
 
@@ -35,7 +36,8 @@ class _Mesh(ctypes.Structure):
 
 class _Material(ctypes.Structure):
     _fields_ = [("formulation", ctypes.c_int32), ("eps_out", ctypes.c_double), ("mu_out", ctypes.c_double),
-                ("eps_in", ctypes.c_double), ("mu_in", ctypes.c_double), ("sigma", ctypes.c_double)]
+                ("eps_in", ctypes.c_double), ("mu_in", ctypes.c_double), ("sigma", ctypes.c_double),
+                ("cfie_alpha", ctypes.c_double)]
 
 
 class Port(ctypes.Structure):
@@ -210,14 +212,14 @@ class Context:
     """An AIMx problem on the current CUDA device (wraps aimx_setup / aimx_destroy)."""
 
     def __init__(self, xyz, tri, grid_n, order=2, formulation=EFIE, eps_out=1.0, mu_out=1.0,
-                 eps_in=1.0, mu_in=1.0, h=None, origin=None, near_radius=3, pad=None, sigma=0.0):
+                 eps_in=1.0, mu_in=1.0, h=None, origin=None, near_radius=3, pad=None, sigma=0.0, cfie_alpha=0.0):
         self._lib = load()
         self._xyz = np.ascontiguousarray(xyz, dtype=np.float64)
         self._tri = np.ascontiguousarray(tri, dtype=np.int32)
         mesh = _Mesh(len(self._xyz), len(self._tri),
                      self._xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                      self._tri.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
-        mat = _Material(formulation, eps_out, mu_out, eps_in, mu_in, sigma)
+        mat = _Material(formulation, eps_out, mu_out, eps_in, mu_in, sigma, cfie_alpha)
         g = _Grid()
         for a in range(3):
             g.n[a] = int(grid_n[a])

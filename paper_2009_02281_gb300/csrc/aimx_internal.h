@@ -57,6 +57,7 @@ struct DArray {
 template <class T>
 struct PrecData {
     T* w = nullptr;        // projection weights [N][U][4] (internal order)
+    T* wg = nullptr;       // CFIE: moments of n x f, [N][U][3] (internal order)
     T* na = nullptr;       // near N^A  [nnz]
     T* np = nullptr;       // near N^Phi[nnz]
     T* nk = nullptr;       // near N^K  [nnz]
@@ -171,7 +172,8 @@ struct aimx_ctx {
     double origin[3] = {0, 0, 0};
     int radius = 3;
     double eps_out = 1, mu_out = 1, eps_in = 1, mu_in = 1;
-    double sigma = 0;      // conductivity for the surface impedance (EFIE), 0 = PEC
+    double sigma = 0;      // conductivity for the surface impedance (EFIE, CFIE), 0 = PEC
+    double cfie_alpha = 0.5;  // EFIE weight of the CFIE
     int F = 4;             // grid fields per RHS (4 EFIE, 8 PMCHWT)
     int nspec = 2;         // spectra per frequency (2 EFIE, 7 PMCHWT)
     int64_t nnz = 0;
@@ -266,6 +268,9 @@ struct StaticData {
     std::vector<double> na, np, nk;  // [nnz] near matrices N^A, N^Phi, N^K
     std::vector<double> diag;  // [N][3] static self terms
 };
+// formulations with one unknown block (EFIE, CFIE) vs two (PMCHWT)
+inline bool two_blocks(int form) { return form == AIMX_PMCHWT; }
+
 // overlap pattern and N^A_lin, N^Phi_lin (direct - precorrection), built once on demand
 void build_linterm(aimx_ctx* ctx);
 // aim.cu: conventional-AIM mode buffers, and the near fill for a frequency (no-op when current)
@@ -288,7 +293,8 @@ template <class T>
 void ensure_spectra(aimx_ctx* ctx, double freq, cudaStream_t s);
 struct Coefs {
     // near-matrix coefficients; EFIE: aA, aPhi, Z_s (Gram, 0 without a surface
-    // impedance); PMCHWT: aA, aPhi, aK, bK, bA, bPhi
+    // impedance); PMCHWT: aA, aPhi, aK, bK, bA, bPhi; CFIE: aA, aPhi, aKg (of K_g),
+    // aG (of the Gram matrix: the residue term plus the surface impedance)
     double2 near[6];
     // linear-term coefficients of N^A_lin and N^Phi_lin x, J rows then M rows
     // (zero while the modification is off)

@@ -397,7 +397,7 @@ int aimx_export_setup(const aimx_ctx* ctx, int32_t* anchors, double* weights, in
 namespace {
 
 constexpr char kMagic[8] = {'A', 'I', 'M', 'X', 'S', 'T', 'A', 'T'};
-constexpr int32_t kStaticVersion = 1;
+constexpr int32_t kStaticVersion = 2;   // 2 adds the CFIE weight after sigma
 
 struct Fnv {
     uint64_t h = 1469598103934665603ull;
@@ -492,6 +492,7 @@ int aimx_save_static(const aimx_ctx* ctx, const char* path) {
         wr.val(ctx->eps_in);
         wr.val(ctx->mu_in);
         wr.val(ctx->sigma);
+        wr.val(ctx->cfie_alpha);
         for (int a = 0; a < 3; ++a) wr.val(ctx->h[a]);
         for (int a = 0; a < 3; ++a) wr.val(ctx->origin[a]);
         wr.vec(xyz);
@@ -537,13 +538,14 @@ int aimx_load_static(const char* path, aimx_ctx** out) {
     mat.eps_in = rd.val<double>();
     mat.mu_in = rd.val<double>();
     mat.sigma = rd.val<double>();
+    if (version >= 2) mat.cfie_alpha = rd.val<double>();
     for (int a = 0; a < 3; ++a) grid.h[a] = rd.val<double>();
     for (int a = 0; a < 3; ++a) grid.origin[a] = rd.val<double>();
     std::vector<double> xyz;
     std::vector<int> tri;
     StaticData st;
     const int U = (order + 1) * (order + 1) * (order + 1);
-    const bool sane = rd.ok && version == kStaticVersion && nv > 0 && nt > 0 && N > 0 && nnz > 0 && order >= 1 &&
+    const bool sane = rd.ok && (version == 1 || version == kStaticVersion) && nv > 0 && nt > 0 && N > 0 && nnz > 0 && order >= 1 &&
                       order <= 3;
     if (sane) {
         rd.vec(xyz, 3 * (size_t)nv);

@@ -317,7 +317,7 @@ struct Mats {
 static Mats materials(const aimx_ctx* ctx, double freq) {
     Mats m;
     m.w = 2.0 * kPi * freq;
-    m.nreg = ctx->form == AIMX_EFIE ? 1 : 2;
+    m.nreg = two_blocks(ctx->form) ? 2 : 1;
     m.mu[0] = kMu0 * ctx->mu_out;
     m.eps[0] = kEps0 * ctx->eps_out;
     m.mu[1] = kMu0 * ctx->mu_in;
@@ -334,26 +334,37 @@ Coefs near_coefs(const aimx_ctx* ctx, double freq) {
     Coefs c;
     for (auto& v : c.near) v = make_double2(0, 0);
     for (auto& v : c.lin) v = make_double2(0, 0);
+    // EFIE weight of the CFIE (1 for the other formulations)
+    const double ea = ctx->form == AIMX_CFIE ? ctx->cfie_alpha : 1.0;
     if (ctx->linterm) {
         // L = L^A - k^-2 L^Phi gains k^2 (N^A_lin - k^-2 N^Phi_lin) = k^2 N^A_lin - N^Phi_lin,
         // scaled like L in each region's rows
         for (int g = 0; g < m.nreg; ++g) {
             const double k2 = m.k[g] * m.k[g];
-            c.lin[0] = c.lin[0] + jmul(m.w * m.mu[g] * k2);
-            c.lin[1] = c.lin[1] + jmul(-m.w * m.mu[g]);
+            c.lin[0] = c.lin[0] + jmul(ea * m.w * m.mu[g] * k2);
+            c.lin[1] = c.lin[1] + jmul(-ea * m.w * m.mu[g]);
             if (ctx->form == AIMX_PMCHWT) {
                 c.lin[2] = c.lin[2] + jmul(kEta0 * kEta0 * m.w * m.eps[g] * k2);
                 c.lin[3] = c.lin[3] + jmul(-kEta0 * kEta0 * m.w * m.eps[g]);
             }
         }
     }
-    if (ctx->form == AIMX_EFIE) {
-        c.near[0] = jmul(m.w * m.mu[0]);
-        c.near[1] = jmul(-m.w * m.mu[0] / (m.k[0] * m.k[0]));
+    if (ctx->form == AIMX_EFIE || ctx->form == AIMX_CFIE) {
+        c.near[0] = jmul(ea * m.w * m.mu[0]);
+        c.near[1] = jmul(-ea * m.w * m.mu[0] / (m.k[0] * m.k[0]));
+        double2 zs = make_double2(0, 0);
         if (ctx->sigma > 0) {
             // surface impedance Z_s = (1 + j) / (sigma delta), delta = sqrt(2 / (w mu0 sigma))
             const double delta = std::sqrt(2.0 / (m.w * kMu0 * ctx->sigma));
-            c.near[2] = make_double2(1.0 / (ctx->sigma * delta), 1.0 / (ctx->sigma * delta));
+            zs = make_double2(1.0 / (ctx->sigma * delta), 1.0 / (ctx->sigma * delta));
+        }
+        if (ctx->form == AIMX_EFIE) {
+            c.near[2] = zs;
+        } else {
+            // CFIE: (1 - alpha) eta (G / 2 + K_g) with eta = w mu / k the background impedance
+            const double eta = m.w * m.mu[0] / m.k[0];
+            c.near[2] = make_double2((1.0 - ea) * eta, 0.0);
+            c.near[3] = make_double2((1.0 - ea) * eta * 0.5, 0.0) + ea * zs;
         }
     } else {
         for (int g = 0; g < 2; ++g) {
@@ -373,7 +384,7 @@ void ensure_spectra(aimx_ctx* ctx, double freq, cudaStream_t s) {
     if (prec<T>(ctx).spec_freq == freq && prec<T>(ctx).spec) return;
     if (!(freq > 0.0)) throw Error{AIMX_E_ARG, "frequency must be positive"};
     Mats m = materials(ctx, freq);
-    const int want_grad = ctx->form == AIMX_PMCHWT;
+    const int want_grad = ctx->form != AIMX_EFIE;
     const int nreg = m.nreg;
     const int narr = nreg + (want_grad ? 3 : 0);
     const int64_t MT = (int64_t)ctx->M[0] * ctx->M[1] * ctx->M[2];
@@ -386,7 +397,11 @@ void ensure_spectra(aimx_ctx* ctx, double freq, cudaStream_t s) {
     }
     if (!ctx->f64.spec) ctx->f64.spec = (double*)dev_alloc(ctx, sizeof(double2) * ctx->nspec * OT);
     if (!ctx->f32.spec) ctx->f32.spec = (float*)dev_alloc(ctx, sizeof(float2) * ctx->nspec * OT);
-    Region r0{m.k[0], want_grad ? kEta0 : 0.0}, r1{m.k[1], want_grad ? kEta0 : 0.0};
+    // gradient samples: eta0 for PMCHWT; (1 - alpha) eta for the K_g part of the CFIE
+    double gs = 0.0;
+    if (ctx->form == AIMX_PMCHWT) gs = kEta0;
+    if (ctx->form == AIMX_CFIE) gs = (1.0 - ctx->cfie_alpha) * m.w * m.mu[0] / m.k[0];
+    Region r0{m.k[0], gs}, r1{m.k[1], gs};
     double2* full = reinterpret_cast<double2*>(ctx->d_kgen);
     k_sample<<<(unsigned)((MT + 255) / 256), 256, 0, s>>>(full, nreg, want_grad, r0, r1, ctx->M[0],
                                                           ctx->M[1], ctx->M[2], ctx->n[0], ctx->n[1],
@@ -397,10 +412,11 @@ void ensure_spectra(aimx_ctx* ctx, double freq, cudaStream_t s) {
     for (auto& row : cf.c)
         for (auto& v : row) v = make_double2(0, 0);
     int nscal;
-    if (ctx->form == AIMX_EFIE) {
+    if (!two_blocks(ctx->form)) {
+        const double ea = ctx->form == AIMX_CFIE ? ctx->cfie_alpha : 1.0;
         nscal = 2;
-        cf.c[0][0] = jmul(m.w * m.mu[0]);
-        cf.c[1][0] = jmul(-m.w * m.mu[0] / (m.k[0] * m.k[0]));
+        cf.c[0][0] = jmul(ea * m.w * m.mu[0]);
+        cf.c[1][0] = jmul(-ea * m.w * m.mu[0] / (m.k[0] * m.k[0]));
     } else {
         nscal = 4;
         for (int g = 0; g < 2; ++g) {

@@ -40,6 +40,7 @@ constexpr int kFinalRows = 32;
 constexpr int kFinalB = 64;
 
 bool fused_supported(const aimx_ctx* ctx) {
+    if (ctx->form == AIMX_CFIE) return false;   // the CFIE's K_g interpolation runs on the generic path
     for (int a = 0; a < 3; ++a) {
         if (!pow2(ctx->n[a]) || ctx->M[a] != 2 * ctx->n[a] || ctx->n[a] < 2) return false;
     }

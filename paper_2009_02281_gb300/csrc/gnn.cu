@@ -888,6 +888,8 @@ static T* galloc(aimx_ctx* ctx, std::vector<void*>& own, size_t n) {
 
 // near-graph topology and the static (frequency-independent) bases, once per context
 static void gnn_topology(aimx_ctx* ctx, cudaStream_t s) {
+    if (ctx->form == AIMX_CFIE)
+        throw Error{AIMX_E_STATE, "the learned preconditioner covers EFIE and PMCHWT contexts"};
     GnnGraph& G = ctx->gnn;
     if (G.d_rows) return;
     const int N = ctx->N;
@@ -1346,6 +1348,7 @@ int aimx_gnn_get_params(const aimx_gnn* net, float* host, int64_t n) {
 
 static int check_pair(const aimx_gnn* net, const aimx_ctx* ctx) {
     if (!net || !ctx) return AIMX_E_ARG;
+    if (ctx->form == AIMX_CFIE) return AIMX_E_STATE;   // the learned preconditioner covers EFIE and PMCHWT
     if ((ctx->form == AIMX_EFIE) != (net->K == 2)) return AIMX_E_ARG;
     return AIMX_OK;
 }

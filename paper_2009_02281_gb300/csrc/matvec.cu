@@ -22,11 +22,12 @@ struct NearCoefs {
 };
 
 // Fields per RHS: EFIE (Jx, Jy, Jz, rho); PMCHWT adds (Mx, My, Mz, rho_M).
-// Field f uses weight component f % 4 and unknown block f / 4.
+// Field f uses weight component f % 4 and unknown block f / 4.  F fields are
+// projected into grids of Fg fields per RHS (CFIE: 4 of 8; the rest stay zero).
 template <class T>
 __global__ void k_project(const T* __restrict__ w, const int* __restrict__ node_ptr,
                           const int* __restrict__ node_w, const int* __restrict__ node_x,
-                          const cplx_t<T>* __restrict__ x, cplx_t<T>* grid, int nrhs, int F, int N,
+                          const cplx_t<T>* __restrict__ x, cplx_t<T>* grid, int nrhs, int F, int Fg, int N,
                           int nunk, int nx, int ny, int nz, int Mx, int My, int Mz) {
     using C = cplx_t<T>;
     int64_t NG = (int64_t)nx * ny * nz;
@@ -49,7 +50,7 @@ __global__ void k_project(const T* __restrict__ w, const int* __restrict__ node_
         }
     }
     int64_t SB = (int64_t)Mx * My * Mz;
-    C* gb = grid + (int64_t)b * F * SB + ((int64_t)gz * My + gy) * Mx + gx;
+    C* gb = grid + (int64_t)b * Fg * SB + ((int64_t)gz * My + gy) * Mx + gx;
     for (int f = 0; f < F; ++f) gb[f * SB] = acc[f];
 }
 
@@ -61,7 +62,7 @@ __device__ inline cplx_t<T> load_spec(const cplx_t<T>* spec, int s, int64_t OT, 
 // Per spectral point: out = mix(in) with the octant spectra (EFIE: 2 scalar,
 // PMCHWT: 4 scalar + gradient vector V with odd symmetry per component).
 template <class T>
-__global__ void k_mix(cplx_t<T>* grid, const cplx_t<T>* __restrict__ spec, int nrhs, int F, int Mx,
+__global__ void k_mix(cplx_t<T>* grid, const cplx_t<T>* __restrict__ spec, int nrhs, int F, int cfie, int Mx,
                       int My, int Mz) {
     using C = cplx_t<T>;
     int64_t MT = (int64_t)Mx * My * Mz;
@@ -74,7 +75,27 @@ __global__ void k_mix(cplx_t<T>* grid, const cplx_t<T>* __restrict__ spec, int n
     int Ox = Mx / 2 + 1, Oy = My / 2 + 1, Oz = Mz / 2 + 1;
     int64_t OT = (int64_t)Ox * Oy * Oz;
     int64_t oi = ((int64_t)oz * Oy + oy) * Ox + ox;
-    if (F == 4) {
+    if (cfie) {
+        // (A, Phi) of J and the K part V x J (V = (1 - alpha) eta grad G spectra, odd per component)
+        C s1 = load_spec<T>(spec, 0, OT, oi), s2 = load_spec<T>(spec, 1, OT, oi);
+        C vx = load_spec<T>(spec, 2, OT, oi), vy = load_spec<T>(spec, 3, OT, oi),
+          vz = load_spec<T>(spec, 4, OT, oi);
+        if (kx > Mx / 2) vx = -vx;
+        if (ky > My / 2) vy = -vy;
+        if (kz > Mz / 2) vz = -vz;
+        for (int b = 0; b < nrhs; ++b) {
+            C* g = grid + (int64_t)b * 8 * MT + t;
+            C jx = g[0], jy = g[MT], jz = g[2 * MT];
+            g[0] = s1 * jx;
+            g[MT] = s1 * jy;
+            g[2 * MT] = s1 * jz;
+            g[3 * MT] = s2 * g[3 * MT];
+            g[4 * MT] = vy * jz - vz * jy;
+            g[5 * MT] = vz * jx - vx * jz;
+            g[6 * MT] = vx * jy - vy * jx;
+            g[7 * MT] = czero<T>();
+        }
+    } else if (F == 4) {
         C s1 = load_spec<T>(spec, 0, OT, oi), s2 = load_spec<T>(spec, 1, OT, oi);
         for (int b = 0; b < nrhs; ++b) {
             C* g = grid + (int64_t)b * 4 * MT + t;
@@ -109,16 +130,20 @@ __global__ void k_mix(cplx_t<T>* grid, const cplx_t<T>* __restrict__ spec, int n
 }
 
 // y[b][perm i] (and y[b][N + perm i]) = W-gather of the output fields + near correction.
+// Output fields: EFIE (A, Phi) with Lambda; PMCHWT E rows (fields 0-3) and H rows
+// (4-7) with Lambda; CFIE (A, Phi) with Lambda and K[J] (fields 4-6) with the
+// moments of n x f (wg).  Near part: N^A, N^Phi, and nk = N^K (PMCHWT) or N^{K_g}
+// (CFIE); ng = the Gram matrix (surface impedance, CFIE residue term) or null.
 template <class T>
-__global__ void k_interp_near(const T* __restrict__ w, const int* __restrict__ anc,
+__global__ void k_interp_near(const T* __restrict__ w, const T* __restrict__ wg, const int* __restrict__ anc,
                               const int* __restrict__ perm, const int* __restrict__ row_ptr,
                               const int* __restrict__ cols, const T* __restrict__ na,
-                              const T* __restrict__ np, const T* __restrict__ nk,
+                              const T* __restrict__ np, const T* __restrict__ nk, const T* __restrict__ ng,
                               const int* __restrict__ lin_ptr, const int* __restrict__ lin_cols,
                               const T* __restrict__ la, const T* __restrict__ lp,
                               const cplx_t<T>* __restrict__ zn,
                               const cplx_t<T>* __restrict__ grid, const cplx_t<T>* __restrict__ x,
-                              cplx_t<T>* y, NearCoefs nc, int nrhs, int F, int N, int nunk, int P,
+                              cplx_t<T>* y, NearCoefs nc, int nrhs, int F, int two, int N, int nunk, int P,
                               int Mx, int My, int Mz) {
     using C = cplx_t<T>;
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -129,12 +154,15 @@ __global__ void k_interp_near(const T* __restrict__ w, const int* __restrict__ a
     int64_t MT = (int64_t)Mx * My * Mz;
     const C* gb = grid + (int64_t)b * F * MT;
     const T* wi = w + (int64_t)i * U * 4;
+    const T* wgi = wg ? wg + (int64_t)i * U * 3 : nullptr;
     C aE = czero<T>(), aH = czero<T>();
     int sx = anc[3 * i], sy = anc[3 * i + 1], sz = anc[3 * i + 2];
     for (int u = 0; u < U; ++u) {
         int64_t node = ((int64_t)(sz + u / (P * P)) * My + (sy + (u / P) % P)) * Mx + (sx + u % P);
         for (int f = 0; f < 4; ++f) rfma(aE, wi[4 * u + f], gb[f * MT + node]);
-        if (F == 8)
+        if (wgi)
+            for (int c = 0; c < 3; ++c) rfma(aE, wgi[3 * u + c], gb[(4 + c) * MT + node]);
+        else if (two)
             for (int f = 0; f < 4; ++f) rfma(aH, wi[4 * u + f], gb[(4 + f) * MT + node]);
     }
     const C* xb = x + (int64_t)b * nunk;
@@ -147,34 +175,39 @@ __global__ void k_interp_near(const T* __restrict__ w, const int* __restrict__ a
             const int j = perm[lin_cols[e]];
             rfma(sA, la[e], xb[j]);
             rfma(sP, lp[e], xb[j]);
-            if (F == 8) {
+            if (two) {
                 rfma(tA, la[e], xb[N + j]);
                 rfma(tP, lp[e], xb[N + j]);
             }
         }
         aE = aE + lA * sA + lP * sP;
-        if (F == 8) aH = aH + mA * tA + mP * tP;
+        if (two) aH = aH + mA * tA + mP * tP;
     }
     C cA = mk((T)nc.c[0].x, (T)nc.c[0].y), cP = mk((T)nc.c[1].x, (T)nc.c[1].y);
-    if (F == 4) {
-        C sA = czero<T>(), sP = czero<T>(), sG = czero<T>();
+    if (!two) {
+        C sA = czero<T>(), sP = czero<T>(), sK = czero<T>(), sG = czero<T>();
         if (zn) {
             // conventional-AIM mode: complex per-frequency entries, coefficient folded in (cA = 1, cP = 0)
             for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
                 C xj = xb[perm[cols[e]]];
                 cfma(sA, zn[e], xj);
-                if (nk) rfma(sG, nk[e], xj);
+                if (ng) rfma(sG, ng[e], xj);
             }
         } else {
             for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
                 C xj = xb[perm[cols[e]]];
                 rfma(sA, na[e], xj);
                 rfma(sP, np[e], xj);
-                if (nk) rfma(sG, nk[e], xj);   // Gram matrix (surface impedance)
+                if (nk) rfma(sK, nk[e], xj);
+                if (ng) rfma(sG, ng[e], xj);
             }
         }
         aE = aE + cA * sA + cP * sP;
-        if (nk) aE = aE + mk((T)nc.c[2].x, (T)nc.c[2].y) * sG;
+        if (nk) aE = aE + mk((T)nc.c[2].x, (T)nc.c[2].y) * sK;            // CFIE: K_g
+        if (ng) {
+            const int g = nk ? 3 : 2;                                      // Gram: c[3] (CFIE), c[2] (EFIE)
+            aE = aE + mk((T)nc.c[g].x, (T)nc.c[g].y) * sG;
+        }
         y[(int64_t)b * nunk + perm[i]] = aE;
     } else {
         C cK = mk((T)nc.c[2].x, (T)nc.c[2].y), dK = mk((T)nc.c[3].x, (T)nc.c[3].y);
@@ -253,6 +286,7 @@ void matvec_generic(aimx_ctx* ctx, double freq, int nrhs, const T* x, T* y, cuda
         for (auto& v : nc.lin) v = make_double2(0.0, 0.0);
     }
     const int F = ctx->F;
+    const bool two = two_blocks(ctx->form);
     const int64_t MT = (int64_t)ctx->M[0] * ctx->M[1] * ctx->M[2];
     const size_t per_rhs = (size_t)F * MT;
     const size_t budget = (size_t)4 << 30;  // bytes of padded-grid work buffer
@@ -274,14 +308,15 @@ void matvec_generic(aimx_ctx* ctx, double freq, int nrhs, const T* x, T* y, cuda
         int64_t tot = NG * nb;
         k_project<T><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
             pd.w, ctx->d_node_ptr, ctx->d_node_w, ctx->d_node_x, xc + (int64_t)b0 * ctx->nunk, grid, nb,
-            F, ctx->N, ctx->nunk, ctx->n[0], ctx->n[1], ctx->n[2], ctx->M[0], ctx->M[1], ctx->M[2]);
+            two ? 8 : 4, F, ctx->N, ctx->nunk, ctx->n[0], ctx->n[1], ctx->n[2], ctx->M[0], ctx->M[1], ctx->M[2]);
         AIMX_CUDA_TRY(cudaGetLastError());
         if (ctx->path == 2)
             cufft_padded<T>(ctx, grid, nb * F, CUFFT_FORWARD, s);
         else
             fft3d_padded<T>(reinterpret_cast<T*>(grid), nb * F, ctx->M, act, false, s);
         k_mix<T><<<(unsigned)((MT + 255) / 256), 256, 0, s>>>(
-            grid, reinterpret_cast<const C*>(pd.spec), nb, F, ctx->M[0], ctx->M[1], ctx->M[2]);
+            grid, reinterpret_cast<const C*>(pd.spec), nb, F, ctx->form == AIMX_CFIE ? 1 : 0, ctx->M[0], ctx->M[1],
+            ctx->M[2]);
         AIMX_CUDA_TRY(cudaGetLastError());
         if (ctx->path == 2)
             cufft_padded<T>(ctx, grid, nb * F, CUFFT_INVERSE, s);
@@ -289,10 +324,11 @@ void matvec_generic(aimx_ctx* ctx, double freq, int nrhs, const T* x, T* y, cuda
             fft3d_padded<T>(reinterpret_cast<T*>(grid), nb * F, ctx->M, act, true, s);
         int64_t tn = (int64_t)ctx->N * nb;
         k_interp_near<T><<<(unsigned)((tn + 127) / 128), 128, 0, s>>>(
-            pd.w, ctx->d_anc, ctx->d_perm, ctx->d_row_ptr, ctx->d_cols, pd.na, pd.np, F == 8 ? pd.nk : pd.ng,
+            pd.w, ctx->form == AIMX_CFIE ? pd.wg : nullptr, ctx->d_anc, ctx->d_perm, ctx->d_row_ptr, ctx->d_cols,
+            pd.na, pd.np, ctx->form == AIMX_EFIE ? nullptr : pd.nk, two ? nullptr : pd.ng,
             ctx->linterm && !ctx->aim ? ctx->d_lin_ptr : nullptr, ctx->d_lin_cols, pd.la, pd.lp,
             ctx->aim ? reinterpret_cast<const C*>(pd.zn) : nullptr, grid,
-            xc + (int64_t)b0 * ctx->nunk, yc + (int64_t)b0 * ctx->nunk, nc, nb, F, ctx->N, ctx->nunk,
+            xc + (int64_t)b0 * ctx->nunk, yc + (int64_t)b0 * ctx->nunk, nc, nb, F, two ? 1 : 0, ctx->N, ctx->nunk,
             ctx->P, ctx->M[0], ctx->M[1], ctx->M[2]);
         AIMX_CUDA_TRY(cudaGetLastError());
     }

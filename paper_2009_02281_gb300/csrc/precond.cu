@@ -295,6 +295,8 @@ static void region_tables(const aimx_ctx* ctx, double freq, int span, std::vecto
 }
 
 void precond_block_prepare(aimx_ctx* ctx, double freq, cudaStream_t s) {
+    if (ctx->form == AIMX_CFIE)
+        throw Error{AIMX_E_STATE, "the block preconditioner covers EFIE and PMCHWT contexts"};
     build_partition(ctx);
     if (ctx->pc.freq == freq && ctx->pc.d_inv) return;
     const int D = ctx->pc.D, nblk = ctx->pc.nblk;

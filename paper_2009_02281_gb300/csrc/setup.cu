@@ -115,8 +115,46 @@ __global__ void k_weights(GeomView g, const int* anc, int N, int P, int nq, doub
     for (int k = 0; k < 4; ++k) w[(size_t)t * 4 + k] = acc[k];
 }
 
+// CFIE testing moments Lambda_g[u, i] = int (n x f_i) l_u dS (n the triangle's unit normal), one
+// thread per (i, u), the rule of the projection weights.
+__global__ void k_weights_g(GeomView g, const int* anc, int N, int P, int nq, double ox, double oy, double oz,
+                            double hx, double hy, double hz, double* wg) {
+    int U = P * P * P;
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N * U) return;
+    int i = t / U, u = t % U;
+    int sel[3] = {u % P, (u / P) % P, u / (P * P)};
+    double acc[3] = {0, 0, 0};
+    for (int side = 0; side < 2; ++side) {
+        int tr = g.btri[2 * i + side];
+        double sg = side == 0 ? 1.0 : -1.0;
+        double A = g.area[tr];
+        double c = g.blen[i] / (2.0 * A);
+        V3 p = load3(g.xyz + 3 * g.bfree[2 * i + side]);
+        V3 a = vtx(g, tr, 0), b = vtx(g, tr, 1), cc = vtx(g, tr, 2);
+        const V3 ncr = cross(b - a, cc - a);
+        const V3 n = (1.0 / norm3(ncr)) * ncr;
+        for (int q = 0; q < nq; ++q) {
+            V3 r = c_qproj[4 * q] * a + c_qproj[4 * q + 1] * b + c_qproj[4 * q + 2] * cc;
+            double W = c_qproj[4 * q + 3] * A;
+            double xi[3] = {(r.x - ox) / hx - anc[3 * i], (r.y - oy) / hy - anc[3 * i + 1],
+                            (r.z - oz) / hz - anc[3 * i + 2]};
+            double ell = 1.0;
+            for (int ax = 0; ax < 3; ++ax)
+                for (int m = 0; m < P; ++m)
+                    if (m != sel[ax]) ell *= (xi[ax] - m) / double(sel[ax] - m);
+            V3 gf = cross(n, (sg * c) * (r - p));
+            acc[0] += W * gf.x * ell;
+            acc[1] += W * gf.y * ell;
+            acc[2] += W * gf.z * ell;
+        }
+    }
+    for (int k = 0; k < 3; ++k) wg[(size_t)t * 3 + k] = acc[k];
+}
+
 // Static near integrals for every stored pair (row i, column j), one thread per pair.
-__global__ void k_near_static(GeomView g, const int* row_of, const int* cols, int64_t nnz, int nq,
+// rot = 1 (CFIE): the K integral is tested with n x f_i (n the testing triangle's normal).
+__global__ void k_near_static(GeomView g, const int* row_of, const int* cols, int64_t nnz, int nq, int rot,
                               double* LA, double* LP, double* KK) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= nnz) return;
@@ -136,6 +174,8 @@ __global__ void k_near_static(GeomView g, const int* row_of, const int* cols, in
             double co = g.blen[i] / (2.0 * Ao);
             V3 po = load3(g.xyz + 3 * g.bfree[2 * i + so]);
             V3 a = vtx(g, to, 0), b = vtx(g, to, 1), c = vtx(g, to, 2);
+            const V3 ncr = cross(b - a, c - a);
+            const V3 no = (1.0 / norm3(ncr)) * ncr;
             for (int q = 0; q < nq; ++q) {
                 V3 r = c_qnear[4 * q] * a + c_qnear[4 * q + 1] * b + c_qnear[4 * q + 2] * c;
                 double W = c_qnear[4 * q + 3] * Ao;
@@ -147,7 +187,7 @@ __global__ void k_near_static(GeomView g, const int* row_of, const int* cols, in
                 la += W * dot(fo, vp);
                 lp += W * (sgo * 2.0 * co) * (sgs * 2.0 * cs) * I1;
                 V3 kv = (sgs * cs) * cross(G, r - ps);
-                kk += W * dot(fo, kv);
+                kk += W * dot(rot ? cross(no, fo) : fo, kv);
             }
         }
     }
@@ -159,7 +199,8 @@ __global__ void k_near_static(GeomView g, const int* row_of, const int* cols, in
 
 // Precorrection with the static grid kernel between the two stencils, then
 // N = direct - precorrection; FP64 and FP32 copies.
-__global__ void k_precorrect(const double* w, const int* anc, const int* row_of, const int* cols,
+// wg (CFIE, else null): the K precorrection takes the testing side's moments of n x f.
+__global__ void k_precorrect(const double* w, const double* wg, const int* anc, const int* row_of, const int* cols,
                              int64_t nnz, int P, int span, const double* hs_tab, const double* hg_tab,
                              const double* LA, const double* LP, const double* KK, double* NA,
                              double* NP, double* NK, float* NA32, float* NP32, float* NK32) {
@@ -176,6 +217,13 @@ __global__ void k_precorrect(const double* w, const int* anc, const int* row_of,
     for (int u = 0; u < U; ++u) {
         int ux = u % P, uy = (u / P) % P, uz = u / (P * P);
         double a0 = wi[4 * u], a1 = wi[4 * u + 1], a2 = wi[4 * u + 2], a3 = wi[4 * u + 3];
+        double k0 = a0, k1 = a1, k2 = a2;
+        if (wg) {
+            const double* gi = wg + ((size_t)i * U + u) * 3;
+            k0 = gi[0];
+            k1 = gi[1];
+            k2 = gi[2];
+        }
         for (int v = 0; v < U; ++v) {
             int vx = v % P, vy = (v / P) % P, vz = v / (P * P);
             int ix = dx0 + ux - vx + span, iy = dy0 + uy - vy + span, iz = dz0 + uz - vz + span;
@@ -185,8 +233,8 @@ __global__ void k_precorrect(const double* w, const int* anc, const int* row_of,
             double b0 = wj[4 * v], b1 = wj[4 * v + 1], b2 = wj[4 * v + 2], b3 = wj[4 * v + 3];
             pa += hs * (a0 * b0 + a1 * b1 + a2 * b2);
             pp += hs * a3 * b3;
-            // a . (g x b)
-            pk += a0 * (gy * b2 - gz * b1) + a1 * (gz * b0 - gx * b2) + a2 * (gx * b1 - gy * b0);
+            // a . (g x b), a the testing moments (of f, or of n x f for the CFIE)
+            pk += k0 * (gy * b2 - gz * b1) + k1 * (gz * b0 - gx * b2) + k2 * (gx * b1 - gy * b0);
         }
     }
     double na = LA[e] - pa, np_ = LP[e] - pp, nk = KK[e] - pk;
@@ -345,7 +393,7 @@ static int next_pow2(int v) {
 
 // Gram values on the near pattern (FP64 and FP32) and their self terms, when a surface impedance is set
 static void build_gram(aimx_ctx* ctx, const GeomView& gv, const int* d_row_of) {
-    if (!(ctx->sigma > 0)) return;
+    if (!(ctx->sigma > 0) && ctx->form != AIMX_CFIE) return;
     const int64_t nnz = ctx->nnz;
     ctx->f64.ng = (double*)dev_alloc(ctx, sizeof(double) * nnz);
     ctx->f32.ng = (float*)dev_alloc(ctx, sizeof(float) * nnz);
@@ -405,8 +453,10 @@ void setup_context(aimx_ctx* ctx, const aimx_mesh* mesh, const aimx_material* ma
     if (!mesh || !mat || !grid || !mesh->xyz || !mesh->tri || mesh->nv < 3 || mesh->nt < 1)
         throw Error{AIMX_E_ARG, "null or empty mesh/material/grid"};
     if (order < 1 || order > 3) throw Error{AIMX_E_ARG, "order must be 1..3"};
-    if (mat->formulation != AIMX_EFIE && mat->formulation != AIMX_PMCHWT)
+    if (mat->formulation != AIMX_EFIE && mat->formulation != AIMX_PMCHWT && mat->formulation != AIMX_CFIE)
         throw Error{AIMX_E_ARG, "unknown formulation"};
+    if (mat->formulation == AIMX_CFIE && !(mat->cfie_alpha >= 0.0 && mat->cfie_alpha <= 1.0))
+        throw Error{AIMX_E_ARG, "cfie_alpha must lie in (0, 1] (0 selects 1/2)"};
     for (int a = 0; a < 3; ++a)
         if (grid->n[a] < order + 2) throw Error{AIMX_E_ARG, "grid has too few nodes"};
     ctx->form = mat->formulation;
@@ -414,13 +464,15 @@ void setup_context(aimx_ctx* ctx, const aimx_mesh* mesh, const aimx_material* ma
     ctx->mu_out = mat->mu_out > 0 ? mat->mu_out : 1.0;
     ctx->eps_in = mat->eps_in > 0 ? mat->eps_in : 1.0;
     ctx->mu_in = mat->mu_in > 0 ? mat->mu_in : 1.0;
-    ctx->sigma = (mat->formulation == AIMX_EFIE && mat->sigma > 0) ? mat->sigma : 0.0;
+    ctx->sigma = (mat->formulation != AIMX_PMCHWT && mat->sigma > 0) ? mat->sigma : 0.0;
+    ctx->cfie_alpha = mat->formulation == AIMX_CFIE && mat->cfie_alpha > 0 ? mat->cfie_alpha : 0.5;
     ctx->order = order;
     ctx->P = order + 1;
     ctx->U = ctx->P * ctx->P * ctx->P;
     ctx->radius = grid->near_radius > 0 ? grid->near_radius : 3;
+    // grid fields per RHS: EFIE (J, rho); PMCHWT (J, rho, M, rho_M); CFIE (J, rho, K[J], unused)
     ctx->F = ctx->form == AIMX_EFIE ? 4 : 8;
-    ctx->nspec = ctx->form == AIMX_EFIE ? 2 : 7;
+    ctx->nspec = ctx->form == AIMX_EFIE ? 2 : (ctx->form == AIMX_CFIE ? 5 : 7);
 
     const int nv = mesh->nv, nt = mesh->nt;
     ctx->nv = nv;
@@ -501,7 +553,7 @@ void setup_context(aimx_ctx* ctx, const aimx_mesh* mesh, const aimx_material* ma
     ctx->h_tp = tp;
     ctx->h_tm = tm;
     ctx->h_cen = cen;
-    ctx->nunk = ctx->form == AIMX_EFIE ? N : 2 * N;
+    ctx->nunk = two_blocks(ctx->form) ? 2 * N : N;
 
     // grid
     const int m = (order + 1) / 2;
@@ -704,6 +756,16 @@ void setup_context(aimx_ctx* ctx, const aimx_mesh* mesh, const aimx_material* ma
         ctx->d_wsoa = (float*)dev_alloc(ctx, sizeof(float) * n4);
         k_weights_soa<<<(unsigned)((n4 + 255) / 256), 256>>>(ctx->f64.w, ctx->d_wsoa, N, U);
         AIMX_CUDA_TRY(cudaGetLastError());
+        if (ctx->form == AIMX_CFIE) {
+            const size_t n3 = (size_t)N * U * 3;
+            ctx->f64.wg = (double*)dev_alloc(ctx, sizeof(double) * n3);
+            ctx->f32.wg = (float*)dev_alloc(ctx, sizeof(float) * n3);
+            k_weights_g<<<(unsigned)((tot + threads - 1) / threads), threads>>>(
+                gv, ctx->d_anc, N, P, nq_proj, ctx->origin[0], ctx->origin[1], ctx->origin[2], ctx->h[0],
+                ctx->h[1], ctx->h[2], ctx->f64.wg);
+            k_to_float<<<(unsigned)((n3 + 255) / 256), 256>>>(ctx->f64.wg, ctx->f32.wg, n3);
+            AIMX_CUDA_TRY(cudaGetLastError());
+        }
     }
 
     // static near integrals + precorrection
@@ -737,7 +799,7 @@ void setup_context(aimx_ctx* ctx, const aimx_mesh* mesh, const aimx_material* ma
     {
         int threads = 128;
         k_near_static<<<(unsigned)((nnz + threads - 1) / threads), threads>>>(
-            gv, d_row_of, ctx->d_cols, nnz, nq_near, d_LA, d_LP, d_KK);
+            gv, d_row_of, ctx->d_cols, nnz, nq_near, ctx->form == AIMX_CFIE ? 1 : 0, d_LA, d_LP, d_KK);
         AIMX_CUDA_TRY(cudaGetLastError());
     }
     // static grid kernel tables over offsets [-span, span]^3
@@ -767,7 +829,7 @@ void setup_context(aimx_ctx* ctx, const aimx_mesh* mesh, const aimx_material* ma
     {
         int threads = 128;
         k_precorrect<<<(unsigned)((nnz + threads - 1) / threads), threads>>>(
-            ctx->f64.w, ctx->d_anc, d_row_of, ctx->d_cols, nnz, P, span, d_hs, d_hg, d_LA, d_LP, d_KK,
+            ctx->f64.w, ctx->f64.wg, ctx->d_anc, d_row_of, ctx->d_cols, nnz, P, span, d_hs, d_hg, d_LA, d_LP, d_KK,
             ctx->f64.na, ctx->f64.np, ctx->f64.nk, ctx->f32.na, ctx->f32.np, ctx->f32.nk);
         AIMX_CUDA_TRY(cudaGetLastError());
     }

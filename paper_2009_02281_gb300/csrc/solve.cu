@@ -203,7 +203,7 @@ __global__ void k_precond(const double2* __restrict__ v, cplx_t<T>* z, const dou
     const int b = (int)(t / N), i = (int)(t % N);
     const double2* vb = v + (int64_t)b * vstride;
     cplx_t<T>* zb = z + (int64_t)b * nunk;
-    if (form == AIMX_EFIE) {
+    if (form != AIMX_PMCHWT) {
         double2 r = minv[i] * vb[i];
         zb[i] = mk((T)r.x, (T)r.y);
     } else {
@@ -221,7 +221,7 @@ __global__ void k_precond_inplace(double2* v, const double2* __restrict__ minv, 
     if (t >= (int64_t)N * nrhs) return;
     const int b = (int)(t / N), i = (int)(t % N);
     double2* vb = v + (int64_t)b * nunk;
-    if (form == AIMX_EFIE) {
+    if (form != AIMX_PMCHWT) {
         vb[i] = minv[i] * vb[i];
     } else {
         const double2* m = minv + 4 * (int64_t)i;
@@ -249,9 +249,14 @@ __global__ void k_build_precond(const double* __restrict__ diag, const double* _
     if (i >= N) return;
     const double la = diag[3 * i], lp = diag[3 * i + 1], kk = diag[3 * i + 2];
     const int o = perm[i];
-    if (form == AIMX_EFIE) {
+    if (form != AIMX_PMCHWT) {
         double2 d = la * aA + lp * aP;
-        if (gdiag) d = d + gdiag[i] * aK;   // surface impedance: aK holds Z_s
+        if (form == AIMX_CFIE) {
+            d = d + kk * aK;                     // K_g self term
+            if (gdiag) d = d + gdiag[i] * bK;    // residue (G / 2) and surface impedance
+        } else if (gdiag) {
+            d = d + gdiag[i] * aK;               // surface impedance: aK holds Z_s
+        }
         double den = d.x * d.x + d.y * d.y;
         minv[o] = den > 0 ? make_double2(d.x / den, -d.y / den) : make_double2(1.0, 0.0);
     } else {
@@ -421,7 +426,7 @@ extern "C" int aimx_solve(aimx_ctx* ctx, double freq, int nrhs, const void* bdev
         if (o.precond == AIMX_PRECOND_NONE || block || learned) {
             std::vector<double2> one(4 * (size_t)N, make_double2(0, 0));
             for (int i = 0; i < N; ++i) {
-                if (ctx->form == AIMX_EFIE) {
+                if (ctx->form != AIMX_PMCHWT) {
                     one[i] = make_double2(1, 0);
                 } else {
                     one[4 * i] = make_double2(1, 0);
@@ -657,7 +662,8 @@ __global__ void k_rhs_planewave(const double* __restrict__ xyz, const int* __res
                                 const double* __restrict__ area, const int* __restrict__ btri,
                                 const int* __restrict__ bfree, const double* __restrict__ blen,
                                 const int* __restrict__ perm, const double* __restrict__ q5, const Wave* __restrict__ waves,
-                                int nwave, int N, int nunk, int form, double k, double inv_eta, double2* out) {
+                                int nwave, int N, int nunk, int form, double k, double inv_eta, double alpha,
+                                double2* out) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= (int64_t)N * nwave) return;
     const int i = (int)(t % N), wv = (int)(t / N);
@@ -674,6 +680,18 @@ __global__ void k_rhs_planewave(const double* __restrict__ xyz, const int* __res
         const double* v0 = xyz + 3 * tri[3 * tr];
         const double* v1 = xyz + 3 * tri[3 * tr + 1];
         const double* v2 = xyz + 3 * tri[3 * tr + 2];
+        // CFIE: n x H_inc tested with f, n the triangle's unit normal
+        double nh[3] = {0, 0, 0};
+        if (form == AIMX_CFIE) {
+            const double e1[3] = {v1[0] - v0[0], v1[1] - v0[1], v1[2] - v0[2]};
+            const double e2[3] = {v2[0] - v0[0], v2[1] - v0[1], v2[2] - v0[2]};
+            double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+            const double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+            for (double& v : n) v /= nn;
+            nh[0] = n[1] * h[2] - n[2] * h[1];
+            nh[1] = n[2] * h[0] - n[0] * h[2];
+            nh[2] = n[0] * h[1] - n[1] * h[0];
+        }
         for (int q = 0; q < 25; ++q) {
             const double l1 = q5[4 * q], l2 = q5[4 * q + 1], l3 = q5[4 * q + 2], wq = q5[4 * q + 3] * A;
             double r[3], f[3];
@@ -689,11 +707,17 @@ __global__ void k_rhs_planewave(const double* __restrict__ xyz, const int* __res
             if (form == AIMX_PMCHWT) {
                 const double fh = f[0] * h[0] + f[1] * h[1] + f[2] * h[2];
                 vh = vh + (wq * fh) * ph;
+            } else if (form == AIMX_CFIE) {
+                const double fh = f[0] * nh[0] + f[1] * nh[1] + f[2] * nh[2];
+                vh = vh + (wq * fh) * ph;
             }
         }
     }
     double2* ob = out + (int64_t)wv * nunk;
-    ob[perm[i]] = ve;
+    if (form == AIMX_CFIE)
+        ob[perm[i]] = alpha * ve + ((1.0 - alpha) / inv_eta) * vh;   // alpha <f, E> + (1 - alpha) eta <f, n x H>
+    else
+        ob[perm[i]] = ve;
     if (form == AIMX_PMCHWT) ob[N + perm[i]] = kEta0 * vh;
 }
 
@@ -790,7 +814,7 @@ extern "C" int aimx_rhs_planewave(aimx_ctx* ctx, double freq, int nwave, const d
         const int64_t tot = (int64_t)ctx->N * nwave;
         k_rhs_planewave<<<nblk(tot, 128), 128, 0, s>>>(ctx->d_xyz, ctx->d_tri, ctx->d_area, ctx->d_btri, ctx->d_bfree,
                                                       ctx->d_blen, ctx->d_perm, ctx->d_q5, dw, nwave, ctx->N, ctx->nunk,
-                                                      ctx->form, k, 1.0 / eta1, (double2*)b);
+                                                      ctx->form, k, 1.0 / eta1, ctx->cfie_alpha, (double2*)b);
         AIMX_CUDA_TRY(cudaGetLastError());
         AIMX_CUDA_TRY(cudaStreamSynchronize(s));
         dev_free(ctx, dw);
@@ -916,7 +940,7 @@ extern "C" int aimx_precond_apply(aimx_ctx* ctx, double freq, int precond, int n
             if (precond == AIMX_PRECOND_NONE) {
                 std::vector<double2> one(4 * (size_t)N, make_double2(0, 0));
                 for (int i = 0; i < N; ++i) {
-                    if (ctx->form == AIMX_EFIE) {
+                    if (ctx->form != AIMX_PMCHWT) {
                         one[i] = make_double2(1, 0);
                     } else {
                         one[4 * i] = make_double2(1, 0);
