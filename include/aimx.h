@@ -314,6 +314,42 @@ int aimx_export_aim_near(aimx_ctx* ctx, double freq, double* z);
 int aimx_export_linear_term(const aimx_ctx* ctx, int64_t* nlin, int64_t* row_ptr, int32_t* cols,
                             double* na, double* nphi);
 
+/* ------------------------------------------------------------------ product schedule and autotuner
+ * How FP32 products of a context are scheduled (not part of the method; the
+ * same product in every case, to rounding):
+ *   variant 0  plane-fused kernels, lines held in registers where the grid
+ *              allows (square 8..64 planes, 8..64 z nodes), else in shared memory
+ *   variant 1  plane-fused kernels with lines in shared memory
+ *   variant 2  generic path (projection, radix-2 3-D FFT, interpolation)
+ *   pass       right-hand sides per pass through the work buffers (0 = as many
+ *              as the work-buffer budget allows); also bounds the generic
+ *              path's chunk and the FP64 products' chunk.
+ * The schedule applies when aimx_set_path is 0; variant 1 needs a grid the
+ * plane-fused path supports (aimx_matvec_path 0), else AIMX_E_ARG.  Default
+ * {0, 0}.  Changing it makes batches recapture their graphs. */
+typedef struct {
+    int32_t variant;
+    int32_t pass;
+    double ms;      /* autotune: measured milliseconds per product (0 elsewhere) */
+} aimx_schedule;
+int aimx_set_schedule(aimx_ctx* ctx, const aimx_schedule* s);
+int aimx_get_schedule(const aimx_ctx* ctx, aimx_schedule* s);
+
+/* Time the FP32 product of nrhs right-hand sides at freq under every candidate
+ * schedule (the variants the grid allows x passes {all, nrhs/2, nrhs/4 with at
+ * least 4}), two untimed and three timed products each with CUDA events on
+ * `stream`, and keep the fastest on the context (the default variant with all
+ * RHS in one pass stays unless another is more than 5% faster).  cache_path (may be NULL): a
+ * text file of earlier choices keyed by device, grid, padded sizes, fields,
+ * bases, near pairs, order, formulation and nrhs; a matching line is applied
+ * without timing, and a new choice is appended.  best: the chosen schedule;
+ * tried: up to max_tried timed candidates, their count in *ntried (0 on a
+ * cache hit).  Allocates two [nrhs][n_unknowns] FP32 work vectors for the
+ * duration of the call.  Synchronous.  Errors: AIMX_E_ARG, AIMX_E_IO (cache
+ * not writable), AIMX_E_NOMEM, AIMX_E_CUDA; the schedule is unchanged on error. */
+int aimx_autotune(aimx_ctx* ctx, double freq, int nrhs, const char* cache_path, aimx_schedule* best,
+                  aimx_schedule* tried, int max_tried, int* ntried, void* stream);
+
 /* ------------------------------------------------------------------ profiling
  * Per-stage timing with CUDA events recorded on the stream each stage is
  * launched on (the paper's per-phase accounting, Table II, at kernel level).

@@ -40,6 +40,14 @@ class _Material(ctypes.Structure):
                 ("cfie_alpha", ctypes.c_double)]
 
 
+class Schedule(ctypes.Structure):
+    """Product schedule (aimx_schedule): variant 0 fused/register, 1 fused/shared memory, 2 generic."""
+    _fields_ = [("variant", ctypes.c_int32), ("pass_", ctypes.c_int32), ("ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {"variant": int(self.variant), "pass": int(self.pass_), "ms": float(self.ms)}
+
+
 class Port(ctypes.Structure):
     """Delta-gap port: plane (point, normal) restricted to the box [box_lo, box_hi] (aimx_port)."""
     _fields_ = [("point", ctypes.c_double * 3), ("normal", ctypes.c_double * 3), ("box_lo", ctypes.c_double * 3),
@@ -85,6 +93,10 @@ _SIGS = [
     ("aimx_set_linear_term", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("aimx_export_linear_term", ctypes.c_int, [ctypes.c_void_p] * 6),
     ("aimx_set_conventional_aim", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("aimx_set_schedule", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("aimx_get_schedule", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("aimx_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_char_p, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     ("aimx_export_aim_near", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p]),
     ("aimx_matvec_path", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("aimx_profile", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
@@ -389,6 +401,28 @@ class Context:
     def set_linear_term(self, enable=True):
         """Linear-term modification of Sec. III-A-3 on overlapping pairs (built on the first enable)."""
         self._check(self._lib.aimx_set_linear_term(self._ctx, 1 if enable else 0))
+
+    def set_schedule(self, variant, pass_=0):
+        """Product schedule: variant 0 fused/register, 1 fused/shared memory, 2 generic; RHS per pass (0 = all)."""
+        sch = Schedule(int(variant), int(pass_), 0.0)
+        self._check(self._lib.aimx_set_schedule(self._ctx, ctypes.byref(sch)))
+
+    def get_schedule(self):
+        sch = Schedule()
+        self._check(self._lib.aimx_get_schedule(self._ctx, ctypes.byref(sch)))
+        return sch.as_dict()
+
+    def autotune(self, freq, nrhs, cache_path=None, stream=None):
+        """Time the candidate schedules of an FP32 product of nrhs RHS and keep the fastest.
+
+        Returns {"best": schedule, "tried": [schedules with ms]} ("tried" is empty on a cache hit)."""
+        best = Schedule()
+        tried = (Schedule * 32)()
+        n = ctypes.c_int(0)
+        path = None if cache_path is None else str(cache_path).encode()
+        self._check(self._lib.aimx_autotune(self._ctx, float(freq), int(nrhs), path, ctypes.byref(best), tried, 32,
+                                            ctypes.byref(n), _stream_handle(stream)))
+        return {"best": best.as_dict(), "tried": [tried[i].as_dict() for i in range(n.value)]}
 
     def set_conventional_aim(self, enable=True):
         """Conventional-AIM comparison mode (Sec. II-B): near entries refilled at every new frequency."""

@@ -247,6 +247,12 @@ struct aimx_ctx {
     int cufft_plan[2] = {0, 0};    // cached cuFFT plans (FP32, FP64) of the comparison path
     int cufft_batch[2] = {0, 0};   // batch each plan was made for
 
+    // product schedule (autotuner): variant 0 = plane-fused with register-resident lines
+    // where the grid allows, 1 = plane-fused with shared-memory lines, 2 = generic path;
+    // pass = right-hand sides per pass (0 = all that fit the work-buffer budget)
+    int sched_variant = 0;
+    int sched_pass = 0;
+
     aimx::Profiler prof;
     aimx::PrecondBlocks pc;
     aimx::GnnGraph gnn;
@@ -325,6 +331,12 @@ struct StageScope {
 
 // fused.cu
 bool fused_supported(const aimx_ctx* ctx);
+// the plane-fused kernels with register-resident lines apply to this grid
+bool fused_reg_supported(const aimx_ctx* ctx);
+// FP32 products of this context take the plane-fused path (path setting and schedule)
+inline bool use_fused(const aimx_ctx* ctx) {
+    return ctx->path == 0 && ctx->sched_variant != 2 && fused_supported(ctx);
+}
 void matvec_fused(aimx_ctx* ctx, double freq, int nrhs, const float* x, float* y, cudaStream_t s);
 
 // precond.cu

@@ -164,7 +164,7 @@ int aimx_matvec(aimx_ctx* ctx, double freq, int nrhs, const void* x, void* y, in
     if (precision != AIMX_F32 && precision != AIMX_F64) return fail(ctx, Error{AIMX_E_ARG, "bad precision"});
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     try {
-        if (precision == AIMX_F32 && ctx->path == 0 && fused_supported(ctx))
+        if (precision == AIMX_F32 && use_fused(ctx))
             matvec_fused(ctx, freq, nrhs, (const float*)x, (float*)y, s);
         else if (precision == AIMX_F32)
             matvec_generic<float>(ctx, freq, nrhs, (const float*)x, (float*)y, s);
@@ -305,7 +305,7 @@ int aimx_export_linear_term(const aimx_ctx* ctx, int64_t* nlin, int64_t* row_ptr
 
 int aimx_matvec_path(const aimx_ctx* ctx, int precision) {
     if (!ctx) return AIMX_E_ARG;
-    if (precision == AIMX_F32 && ctx->path == 0 && fused_supported(ctx)) return 0;
+    if (precision == AIMX_F32 && use_fused(ctx)) return 0;
     return ctx->path == 2 ? 2 : 1;
 }
 

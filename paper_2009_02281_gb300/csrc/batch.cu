@@ -34,7 +34,7 @@ struct aimx_batch {
 namespace {
 
 void member_matvec(aimx_ctx* c, double freq, int nrhs, const void* x, void* y, cudaStream_t s) {
-    if (c->path == 0 && fused_supported(c))
+    if (use_fused(c))
         matvec_fused(c, freq, nrhs, static_cast<const float*>(x), static_cast<float*>(y), s);
     else
         matvec_generic<float>(c, freq, nrhs, static_cast<const float*>(x), static_cast<float*>(y), s);

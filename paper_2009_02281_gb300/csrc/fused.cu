@@ -692,14 +692,21 @@ __global__ void __launch_bounds__(2 * N) k_xy_inv_reg(const float2* __restrict__
 
 // ------------------------------------------------------------------ host driver
 
-static bool reg_path(const aimx_ctx* ctx) {
+static bool reg_shape(const aimx_ctx* ctx) {
     const int N = ctx->n[0];
     if (ctx->n[1] != N) return false;
     if (N != 8 && N != 16 && N != 32 && N != 64) return false;
     const int Nz = ctx->n[2];
     if (Nz != 8 && Nz != 16 && Nz != 32 && Nz != 64) return false;
-    return (size_t)(2 * N * (N + 1) + 2 * ctx->max_plane_bases) * sizeof(float2) <= 200 * 1024;
+    int mpb = 0;
+    for (size_t z = 0; z < ctx->plane_lo.size(); ++z) mpb = std::max(mpb, ctx->plane_hi[z] - ctx->plane_lo[z]);
+    return (size_t)(2 * N * (N + 1) + 2 * mpb) * sizeof(float2) <= 200 * 1024;
 }
+
+bool fused_reg_supported(const aimx_ctx* ctx) { return fused_supported(ctx) && reg_shape(ctx); }
+
+// register kernels unless the schedule asks for the shared-memory ones
+static bool reg_path(const aimx_ctx* ctx) { return ctx->sched_variant != 1 && reg_shape(ctx); }
 
 static void ensure_const_twiddles() {
     static bool done[64] = {};
@@ -915,7 +922,8 @@ void matvec_fused(aimx_ctx* ctx, double freq, int nrhs, const float* x, float* y
     // RHS per pass bounded by an 8 GiB work-buffer budget
     const size_t per_rhs =
         sizeof(float2) * ((size_t)ctx->nunk + (size_t)F * NG * 5 + (size_t)(F / 4) * ctx->P * ctx->N);
-    const int cap = (int)std::max<size_t>(1, std::min<size_t>(nrhs, ((size_t)8 << 30) / per_rhs));
+    int cap = (int)std::max<size_t>(1, std::min<size_t>(nrhs, ((size_t)8 << 30) / per_rhs));
+    if (ctx->sched_pass > 0) cap = std::min(cap, ctx->sched_pass);
     ensure_fused_buffers(ctx, cap);
     FusedBufs fb{reinterpret_cast<float2*>(ctx->d_xT), reinterpret_cast<float2*>(ctx->d_G),
                  reinterpret_cast<float2*>(ctx->d_S), reinterpret_cast<float2*>(ctx->d_part)};

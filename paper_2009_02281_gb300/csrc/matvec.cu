@@ -291,6 +291,7 @@ void matvec_generic(aimx_ctx* ctx, double freq, int nrhs, const T* x, T* y, cuda
     const size_t per_rhs = (size_t)F * MT;
     const size_t budget = (size_t)4 << 30;  // bytes of padded-grid work buffer
     int chunk = (int)std::max<size_t>(1, std::min<size_t>(nrhs, budget / (per_rhs * sizeof(C))));
+    if (ctx->sched_pass > 0) chunk = std::min(chunk, ctx->sched_pass);
     if (pd.grid_elems < per_rhs * chunk) {
         if (pd.grid) dev_free(ctx, pd.grid);
         pd.grid = (T*)dev_alloc(ctx, sizeof(C) * per_rhs * chunk);

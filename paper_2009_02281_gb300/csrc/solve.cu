@@ -307,7 +307,7 @@ struct SolveWork {
 
 static void matvec_any(aimx_ctx* ctx, double freq, int nrhs, const void* x, void* y, int prec, cudaStream_t s) {
     if (prec == AIMX_F32) {
-        if (ctx->path == 0 && fused_supported(ctx))
+        if (use_fused(ctx))
             matvec_fused(ctx, freq, nrhs, (const float*)x, (float*)y, s);
         else
             matvec_generic<float>(ctx, freq, nrhs, (const float*)x, (float*)y, s);

@@ -1,0 +1,99 @@
+"""Product schedules and the autotuner: every schedule computes the same product
+(FP32 parity 1e-5 against the FP64 oracle), the tuner keeps the fastest timed
+candidate, and a cache hit applies the stored choice without timing."""
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+C0 = 299792458.0
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2009_02281_gb300 import build
+    build.build()
+    return torch
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("form", ["efie", "pmchwt"])
+def test_every_schedule_computes_the_product(torch_cuda, form):
+    torch = torch_cuda
+    from synth import icosphere, random_complex
+    from oracle import operator as op
+    from paper_2009_02281_gb300 import Context, EFIE, PMCHWT
+    xyz, tri = icosphere(2)
+    grid = (16, 16, 16)
+    kw = dict(formulation=EFIE) if form == "efie" else dict(formulation=PMCHWT, eps_out=1.0, eps_in=3.0)
+    ctx = Context(xyz, tri, grid, order=2, **kw)
+    prob = op.setup(xyz, tri, 2, grid, radius=3)
+    f = 1.2 * C0 / (2 * np.pi)
+    x = random_complex((8, ctx.nunk), seed=14)
+    if form == "efie":
+        ref = np.stack([op.matvec_efie(prob, f, v) for v in x])
+    else:
+        ref = np.stack([op.matvec_pmchwt(prob, f, v, 1.0, 3.0) for v in x])
+    xt = torch.tensor(x, dtype=torch.complex64, device="cuda")
+    for variant, expect_path in ((0, 0), (1, 0), (2, 1)):
+        for p in (0, 3):
+            ctx.set_schedule(variant, p)
+            assert ctx.get_schedule() == {"variant": variant, "pass": p, "ms": 0.0}
+            assert ctx.matvec_path() == expect_path
+            y = ctx.matvec(f, xt).cpu().numpy()
+            assert _rel(y, ref) <= 1e-5, (variant, p)
+    ctx.set_schedule(0, 0)
+    ctx.close()
+
+
+def test_autotune_picks_fastest_and_caches(torch_cuda, tmp_path):
+    from synth import icosphere
+    from paper_2009_02281_gb300 import Context, EFIE
+    xyz, tri = icosphere(2)
+    f = 1.2 * C0 / (2 * np.pi)
+    cache = tmp_path / "tune.txt"
+    a = Context(xyz, tri, (16, 16, 16), order=2, formulation=EFIE)
+    r = a.autotune(f, 16, cache_path=cache)
+    assert len(r["tried"]) >= 3
+    fastest = min(t["ms"] for t in r["tried"])
+    default = [t for t in r["tried"] if t["variant"] == 0 and t["pass"] == 0][0]["ms"]
+    # the fastest, unless the default is within 5% of it
+    assert r["best"]["ms"] == fastest or (r["best"]["ms"] == default and fastest > 0.95 * default)
+    assert {t["variant"] for t in r["tried"]} == {0, 1, 2}
+    chosen = a.get_schedule()
+    assert (chosen["variant"], chosen["pass"]) == (r["best"]["variant"], r["best"]["pass"])
+    assert cache.read_text().count("\n") == 1
+    b = Context(xyz, tri, (16, 16, 16), order=2, formulation=EFIE)
+    r2 = b.autotune(f, 16, cache_path=cache)
+    assert r2["tried"] == []
+    assert (r2["best"]["variant"], r2["best"]["pass"]) == (r["best"]["variant"], r["best"]["pass"])
+    # another RHS count is another key
+    r3 = b.autotune(f, 8, cache_path=cache)
+    assert len(r3["tried"]) >= 3
+    a.close()
+    b.close()
+
+
+def test_schedule_errors(torch_cuda):
+    from synth import icosphere
+    from paper_2009_02281_gb300 import AimxError, Context, CFIE, EFIE
+    xyz, tri = icosphere(1)
+    c = Context(xyz, tri, (8, 8, 8), formulation=CFIE)
+    with pytest.raises(AimxError) as e:
+        c.set_schedule(1, 0)                 # the CFIE runs on the generic path only
+    assert e.value.code == -1
+    c.set_schedule(2, 4)
+    c.close()
+    e2 = Context(xyz, tri, (8, 8, 8), formulation=EFIE)
+    for bad in ((3, 0), (0, -1)):
+        with pytest.raises(AimxError) as e:
+            e2.set_schedule(*bad)
+        assert e.value.code == -1
+    e2.close()
