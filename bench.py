@@ -176,20 +176,20 @@ def measure_solves(ctx, wl, args):
     frequency (training reported as a one-time cost, like setup)."""
     import torch
     from synth import planewave_batch
-    from paper_2009_02281_gb300 import Gnn, PRECOND_DIAG, PRECOND_LEARNED
+    from paper_2009_02281_gb300 import Gnn, PRECOND_DIAG, PRECOND_LEARNED, F64
     freq, B = wl["freq"], wl["nrhs"]
     dirs, pols = planewave_batch(B, seed=0)
     b = ctx.rhs_planewave(freq, dirs, pols)
 
-    def solve(pc):
+    def solve(pc, rhs=b, **kw):
         torch.cuda.synchronize()
         t = time.perf_counter()
-        _, st, rc = ctx.solve(freq, b, tol=args.solve_tol, restart=100, max_iter=4000, precond=pc)
+        _, st, rc = ctx.solve(freq, rhs, tol=args.solve_tol, restart=100, max_iter=4000, precond=pc, **kw)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t
         it = [s["iterations"] for s in st]
         ok = sum(1 for s in st if s["rel_residual"] <= args.solve_tol)
-        return {"solves_per_s": round(ok / dt, 3), "wall_s": round(dt, 3), "converged": ok, "rhs": B,
+        return {"solves_per_s": round(ok / dt, 3), "wall_s": round(dt, 3), "converged": ok, "rhs": rhs.shape[0],
                 "iterations_mean": round(float(np.mean(it)), 1), "iterations_max": int(max(it)),
                 "max_rel_residual": max(s["rel_residual"] for s in st)}
 
@@ -210,6 +210,21 @@ def measure_solves(ctx, wl, args):
                                    "ms_per_step": round(1e3 * dt / args.gnn_steps, 2),
                                    "loss_first": round(losses[0], 4),
                                    "loss_last": round(float(np.mean(losses[-20:])), 4)}
+    # the plain FP64 cuFFT-based AIM solve on the same GPU (generic projection and interpolation,
+    # cuFFT transforms of the full padded grids, FP64 products throughout, diagonal
+    # preconditioner) on a bounded sample of the right-hand sides; solves/s per converged RHS
+    if args.plain_rhs > 0:
+        nb = min(args.plain_rhs, B)
+        ctx.set_path(2)
+        try:
+            plain = solve(PRECOND_DIAG, rhs=b[:nb].contiguous(), inner_precision=F64)
+        finally:
+            ctx.set_path(args.path)
+        plain["path"] = "generic + cuFFT, FP64 products, diagonal preconditioner"
+        out["plain_fp64_cufft"] = plain
+        best = max(out["diag"]["solves_per_s"], out.get("learned", {}).get("solves_per_s", 0.0))
+        if plain["solves_per_s"] > 0:
+            out["speedup_vs_plain_fp64_cufft"] = round(best / plain["solves_per_s"], 2)
     return out
 
 
@@ -750,7 +765,9 @@ def main():
     ap.add_argument("--batch-members", type=int, default=16,
                     help="members of the seeded uneven batch to time (0 = skip; 48 = the full batch)")
     ap.add_argument("--path", type=int, default=0, choices=[0, 1], help="product path for the timed steps (aimx_set_path)")
-    ap.add_argument("--solve-tol", type=float, default=1e-4)
+    ap.add_argument("--solve-tol", type=float, default=1e-5)
+    ap.add_argument("--plain-rhs", type=int, default=4,
+                    help="right-hand sides of the plain FP64 cuFFT solve comparison (0 skips it)")
     ap.add_argument("--gnn-steps", type=int, default=600, help="training steps of the learned preconditioner")
     args = ap.parse_args()
     if args.warmup < 3:
