@@ -326,6 +326,46 @@ def measure_config1(args, ws):
             "cfie_sweep": cfie_cmp}
 
 
+def measure_config3(args, ws):
+    """The copper-bar sweep workload (8 bars, SIBC, eps_r 3.5 background): setup and the FP32
+    product of its 8 port right-hand sides at three frequencies of the sweep, on the
+    autotuned schedule.  Solves are not timed here: plain-EFIE GMRES stalls on this mesh."""
+    import torch
+    from synth import workloads, random_complex
+    from paper_2009_02281_gb300 import Context, EFIE
+    wl = workloads.conductor_bars()
+    t0 = time.time()
+    ctx = Context(wl["xyz"], wl["tri"], wl["grid_n"], order=wl["order"], formulation=EFIE, eps_out=wl["eps_out"],
+                  near_radius=wl["radius"], sigma=wl["sigma"])
+    torch.cuda.synchronize()
+    setup_s = time.time() - t0
+    nrhs = len(wl["ports"])
+    x = torch.tensor(random_complex((nrhs, ctx.nunk), seed=33).astype(np.complex64), device="cuda")
+    y = torch.empty_like(x)
+    freqs = [float(wl["freqs"][k]) for k in (0, 50, 99)]
+    tune = ctx.autotune(freqs[-1], nrhs) if not args.no_autotune else None
+    stream = torch.cuda.current_stream()
+    per = []
+    for f in freqs:
+        ctx.matvec(f, x, y)                  # spectra for this frequency
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(5):
+            ctx.matvec(f, x, y)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        per.append(e0.elapsed_time(e1) / 5)
+    ms = float(np.median(per))
+    info = ctx.info
+    ctx.close()
+    return {"workload": wl["name"], "n_unknowns": info["n_unknowns"], "near_nnz": info["near_nnz"],
+            "grid": list(info["grid_n"]), "padded": list(info["pad"]), "setup_s": round(setup_s, 2),
+            "rhs": nrhs, "ms_per_product": round(ms, 3), "value": round(ws * nrhs / (ms * 1e-3), 2), "unit": UNIT,
+            "freqs_hz": freqs, "schedule": tune["best"] if tune else None,
+            "solves": "not timed: plain-EFIE GMRES stalls on this mesh (see the design notes)"}
+
+
 def learned_eval(args):
     """Learned preconditioner trained on seeded small copper-block layouts (10 mm
     region, 1-4 mm blocks, several frequencies) and evaluated on held-out larger
@@ -665,6 +705,8 @@ def run_ours(args):
         out["uneven_batch"] = measure_batch(args, ws)
     if not args.no_config1:
         out["pec_sphere_1920"] = measure_config1(args, ws)
+    if not args.no_config3:
+        out["conductor_bars"] = measure_config3(args, ws)
     if not args.no_learned_eval:
         out["learned_generalisation"] = learned_eval(args)
     if rank == 0 and not args.no_cpu_baseline:
@@ -754,6 +796,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 product measurement")
     ap.add_argument("--no-config1", action="store_true", help="skip the 1920-unknown FP64 latency measurement")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default product schedules")
+    ap.add_argument("--no-config3", action="store_true", help="skip the copper-bar product measurement")
     ap.add_argument("--no-cfie", action="store_true", help="skip the CFIE sweep of the 1920-unknown sphere")
     ap.add_argument("--no-aim", action="store_true",
                     help="skip the conventional-AIM sweep of the 1920-unknown sphere")
