@@ -528,7 +528,13 @@ __global__ void __launch_bounds__(2 * F * 8) k_zpass_reg(float2* S, const float2
     const int64_t OT = (int64_t)Ox * Oy * Oz;
     const int ky = 2 * kyp + py;
     const int oy = ky <= My / 2 ? ky : My - ky;
-    for (int pt = threadIdx.x; pt < TC * MZ; pt += blockDim.x) {
+    // compile-time trip count (blockDim.x = 2 F TC divides TC MZ): the loop unrolls and every
+    // point's spectrum loads issue together instead of one L2 round trip per point
+    constexpr int NT = 2 * F * TC;
+    static_assert((TC * MZ) % NT == 0, "mix points must split evenly over the block");
+#pragma unroll
+    for (int it = 0; it < TC * MZ / NT; ++it) {
+        const int pt = threadIdx.x + it * NT;
         const int cc = pt % TC, kz = pt / TC;
         const int kx = 2 * (kx0 + cc) + px;
         const int ox = kx <= Mx / 2 ? kx : Mx - kx;
