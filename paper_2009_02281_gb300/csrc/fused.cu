@@ -651,32 +651,42 @@ __global__ void __launch_bounds__(2 * N) k_xy_inv_reg(const float2* __restrict__
             for (int x = 0; x < N; ++x) O[r * PITCH + x] = O[r * PITCH + x] + v[x];
         }
         __syncthreads();
+        if (P == 3) {
+            // four bases per iteration so that their 36 weight gathers are in flight together
+            // (the transform's registers are free in this phase)
+            const int bd = blockDim.x;
+            for (int k = threadIdx.x; k < nb; k += 4 * bd) {
+                int kk[4];
+                int2 m[4];
+                float a[4][9];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    kk[j] = k + j * bd;
+                    m[j] = meta[kk[j] < nb ? kk[j] : k];
+                    // field-major weights ws[fl][u][i]: neighbouring bases of one slot are adjacent
+                    const float* wj = w + (int64_t)fl * U * Ntot + m[j].y;
+#pragma unroll
+                    for (int u = 0; u < 9; ++u) a[j][u] = __ldg(wj + (int64_t)u * Ntot);
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    float2 sj = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int uy = 0; uy < 3; ++uy)
+#pragma unroll
+                        for (int ux = 0; ux < 3; ++ux) rfma(sj, a[j][uy * 3 + ux], O[m[j].x + uy * PITCH + ux]);
+                    if (kk[j] < nb) acc[kk[j]] = acc[kk[j]] + sj;
+                }
+            }
+        } else
         // two bases per iteration so that both weight gathers are in flight together
         for (int k = threadIdx.x; k < nb; k += 2 * blockDim.x) {
             const int k2 = k + blockDim.x;
             const bool two = k2 < nb;
             const int2 m0 = meta[k], m1 = two ? meta[k2] : m0;
-            // field-major weights ws[fl][u][i]: neighbouring bases of one slot are adjacent
             const float* w0 = w + (int64_t)fl * U * Ntot + m0.y;
             const float* w1 = w + (int64_t)fl * U * Ntot + m1.y;
-            float a0[9], a1[9];
-            if (P == 3) {
-#pragma unroll
-                for (int u = 0; u < 9; ++u) {
-                    a0[u] = __ldg(w0 + (int64_t)u * Ntot);
-                    a1[u] = __ldg(w1 + (int64_t)u * Ntot);
-                }
-                float2 s0 = make_float2(0.f, 0.f), s1 = make_float2(0.f, 0.f);
-#pragma unroll
-                for (int uy = 0; uy < 3; ++uy)
-#pragma unroll
-                    for (int ux = 0; ux < 3; ++ux) {
-                        rfma(s0, a0[uy * 3 + ux], O[m0.x + uy * PITCH + ux]);
-                        rfma(s1, a1[uy * 3 + ux], O[m1.x + uy * PITCH + ux]);
-                    }
-                acc[k] = acc[k] + s0;
-                if (two) acc[k2] = acc[k2] + s1;
-            } else {
+            {
                 float2 s0 = make_float2(0.f, 0.f), s1 = make_float2(0.f, 0.f);
                 for (int uy = 0; uy < P; ++uy)
                     for (int ux = 0; ux < P; ++ux) {
