@@ -321,6 +321,10 @@ int aimx_export_linear_term(const aimx_ctx* ctx, int64_t* nlin, int64_t* row_ptr
  *              allows (square 8..64 planes, 8..64 z nodes), else in shared memory
  *   variant 1  plane-fused kernels with lines in shared memory
  *   variant 2  generic path (projection, radix-2 3-D FFT, interpolation)
+ *   variant 3  as variant 0, with the z transforms in a persistent kernel whose
+ *              tiles are copied into shared memory by the tensor-memory
+ *              accelerator (cp.async.bulk.tensor) while the previous tile is
+ *              transformed; needs the register-line grids of variant 0
  *   pass       right-hand sides per pass through the work buffers (0 = as many
  *              as the work-buffer budget allows); also bounds the generic
  *              path's chunk and the FP64 products' chunk.
@@ -334,6 +338,12 @@ typedef struct {
 } aimx_schedule;
 int aimx_set_schedule(aimx_ctx* ctx, const aimx_schedule* s);
 int aimx_get_schedule(const aimx_ctx* ctx, aimx_schedule* s);
+
+/* Number of bounded device waits (copy-completion barriers of the variant-3
+ * z-pass) that ran out since the last call, and reset it.  A wait that runs
+ * out leaves that product's output incomplete; 0 is the normal answer.
+ * Synchronous. */
+int aimx_wait_timeouts(int* count);
 
 /* Time the FP32 product of nrhs right-hand sides at freq under every candidate
  * schedule (the variants the grid allows x passes {all, nrhs/2, nrhs/4 with at

@@ -5,4 +5,4 @@ The compute path is the CUDA library ``libaimx.so`` (sources in ``csrc/``, C ABI
 """
 
 from .aimx import (AimxError, Batch, Context, Gnn, Port, EFIE, PMCHWT, CFIE, F32, F64, PRECOND_DIAG, PRECOND_NONE,  # noqa: F401
-                   PRECOND_BLOCK, PRECOND_LEARNED, load)
+                   PRECOND_BLOCK, PRECOND_LEARNED, load, wait_timeouts)

@@ -95,6 +95,7 @@ _SIGS = [
     ("aimx_set_conventional_aim", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("aimx_set_schedule", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("aimx_get_schedule", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("aimx_wait_timeouts", ctypes.c_int, [ctypes.c_void_p]),
     ("aimx_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_char_p, ctypes.c_void_p,
                                      ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     ("aimx_export_aim_near", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p]),
@@ -209,6 +210,15 @@ def load(build_if_missing=False):
 
 def _ptr(a):
     return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def wait_timeouts():
+    """Bounded device waits that ran out since the last call (0 normally); resets the count."""
+    n = ctypes.c_int(0)
+    rc = load().aimx_wait_timeouts(ctypes.byref(n))
+    if rc != 0:
+        raise AimxError(rc)
+    return n.value
 
 
 def _stream_handle(stream):

@@ -248,7 +248,8 @@ struct aimx_ctx {
     int cufft_batch[2] = {0, 0};   // batch each plan was made for
 
     // product schedule (autotuner): variant 0 = plane-fused with register-resident lines
-    // where the grid allows, 1 = plane-fused with shared-memory lines, 2 = generic path;
+    // where the grid allows, 1 = plane-fused with shared-memory lines, 2 = generic path,
+    // 3 = as 0 with the TMA-pipelined persistent z-pass;
     // pass = right-hand sides per pass (0 = all that fit the work-buffer budget)
     int sched_variant = 0;
     int sched_pass = 0;

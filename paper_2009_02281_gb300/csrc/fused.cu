@@ -24,6 +24,9 @@
 
 #include <algorithm>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "aimx_internal.h"
 #include "cplx.cuh"
 #include "fftreg.cuh"
@@ -493,28 +496,20 @@ __global__ void __launch_bounds__(2 * N) k_xy_fwd_reg(const float2* __restrict__
 // K3 (register form): thread pair (pz = 0, 1) per (field, column) computes the
 // even / odd halves of the zero-padded 2 NZ transform, shared memory carries
 // the per-point mix across fields and the final even + odd sum.
+// One z-pass tile (TC columns of all F fields, both z parities) once each thread holds its
+// column in v: forward transform, spectral multiply across the fields, inverse transform,
+// and the even + odd sum written back to S.
 template <int NZ, int F>
-__global__ void __launch_bounds__(2 * F * 8) k_zpass_reg(float2* S, const float2* __restrict__ spec, int Nx,
-                                                             int Ny, int B) {
-    extern __shared__ float2 sm[];
+__device__ __forceinline__ void zpass_tile(float2 (&v)[NZ], float2* sm, float2* S, const float2* __restrict__ spec,
+                                           int Nx, int Ny, int kx0, int kyp, int q, int c, int f, int pz,
+                                           int64_t base, int64_t zs) {
     constexpr int TC = 8;
     constexpr int MZ = 2 * NZ;
     constexpr int LP = MZ + 2;       // line pitch: adjacent columns 2 banks apart
     constexpr int FS = TC * LP + 1;  // field stride: adjacent fields 1 bank apart
     const int Mx = 2 * Nx, My = 2 * Ny;
-    const int NP = Nx * Ny;
-    const int kx0 = blockIdx.x * TC, kyp = blockIdx.y;
-    const int q = blockIdx.z & 3, b = blockIdx.z >> 2;
     const int px = q & 1, py = q >> 1;
-    const int c = threadIdx.x % TC;
-    const int f = (threadIdx.x / TC) % F;
-    const int pz = threadIdx.x / (TC * F);
-    const int64_t zs = 4 * (int64_t)NP;
-    const int64_t base = (((int64_t)b * F + f) * NZ * 4 + q) * NP + (int64_t)kyp * Nx + kx0 + c;
     float2* line = sm + f * FS + c * LP;
-    float2 v[NZ];
-#pragma unroll
-    for (int z = 0; z < NZ; ++z) v[z] = S[base + z * zs];
     if (pz) {
 #pragma unroll
         for (int z = 1; z < NZ; ++z) v[z] = v[z] * twc<false>(z, MZ);
@@ -584,6 +579,144 @@ __global__ void __launch_bounds__(2 * F * 8) k_zpass_reg(float2* S, const float2
     if (!pz) {
 #pragma unroll
         for (int z = 0; z < NZ; ++z) S[base + z * zs] = v[z] + line[z];
+    }
+}
+
+template <int NZ, int F>
+__global__ void __launch_bounds__(2 * F * 8) k_zpass_reg(float2* S, const float2* __restrict__ spec, int Nx,
+                                                             int Ny, int B) {
+    extern __shared__ float2 sm[];
+    constexpr int TC = 8;
+    const int NP = Nx * Ny;
+    const int kx0 = blockIdx.x * TC, kyp = blockIdx.y;
+    const int q = blockIdx.z & 3, b = blockIdx.z >> 2;
+    const int c = threadIdx.x % TC;
+    const int f = (threadIdx.x / TC) % F;
+    const int pz = threadIdx.x / (TC * F);
+    const int64_t zs = 4 * (int64_t)NP;
+    const int64_t base = (((int64_t)b * F + f) * NZ * 4 + q) * NP + (int64_t)kyp * Nx + kx0 + c;
+    float2 v[NZ];
+#pragma unroll
+    for (int z = 0; z < NZ; ++z) v[z] = S[base + z * zs];
+    zpass_tile<NZ, F>(v, sm, S, spec, Nx, Ny, kx0, kyp, q, c, f, pz, base, zs);
+}
+
+// ------------------------------------------------------------------ K3, TMA-pipelined form
+// A persistent form of the register z-pass: each block walks the tiles with a
+// stride of the grid size, and while it transforms one tile the tensor-memory
+// accelerator copies the next tile's columns (one [NZ][TC] box per field,
+// cp.async.bulk.tensor) into shared memory, completing on an mbarrier.  Every
+// wait is bounded: a block whose copy does not complete within about a second
+// records the fault in `err`, waits (bounded) for its other copy and stops.
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait on phase `parity`: false after ~2e9 cycles (about a second)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > 2000000000LL) return false;
+    return true;
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];\n" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ int g_wait_timeouts = 0;   // bounded waits that ran out (read by aimx_wait_timeouts)
+
+// tmap: S as float32 [B*F*NZ][4][Ny][2 Nx] (innermost last), box {2 TC, 1, 1, NZ}.
+template <int NZ, int F>
+__global__ void __launch_bounds__(2 * F * 8) k_zpass_tma(const __grid_constant__ CUtensorMap tmap, float2* S,
+                                                             const float2* __restrict__ spec, int Nx, int Ny, int B) {
+    extern __shared__ __align__(128) unsigned char smraw[];
+    constexpr int TC = 8;
+    constexpr unsigned COLB = NZ * TC * sizeof(float2);   // one field's box
+    constexpr unsigned TILEB = F * COLB;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smraw);
+    unsigned char* buf = smraw + 128;
+    float2* sm = reinterpret_cast<float2*>(smraw + 128 + TILEB);
+    const int NP = Nx * Ny;
+    const int tx = Nx / TC;
+    const int64_t T = (int64_t)tx * Ny * 4 * B;
+    const int c = threadIdx.x % TC;
+    const int f = (threadIdx.x / TC) % F;
+    const int pz = threadIdx.x / (TC * F);
+    const int64_t zs = 4 * (int64_t)NP;
+    auto issue = [&](int64_t t) {   // thread 0: copy tile t's columns into buf
+        const int xb = (int)(t % tx);
+        int64_t r = t / tx;
+        const int kyp = (int)(r % Ny);
+        r /= Ny;
+        const int q = (int)(r & 3), b = (int)(r >> 2);
+        fence_proxy_async();
+        mbar_expect_tx(bar, TILEB);
+        for (int ff = 0; ff < F; ++ff)
+            tma_load_4d(buf + ff * COLB, &tmap, 2 * xb * TC, kyp, q, (b * F + ff) * NZ, bar);
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    int64_t t = blockIdx.x;
+    if (threadIdx.x == 0 && t < T) issue(t);
+    unsigned parity = 0;
+    bool failed = false;
+    for (; t < T; t += gridDim.x) {
+        const bool ok = mbar_wait_bounded(bar, parity);
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        parity ^= 1u;
+        const int xb = (int)(t % tx);
+        int64_t r = t / tx;
+        const int kyp = (int)(r % Ny);
+        r /= Ny;
+        const int q = (int)(r & 3), b = (int)(r >> 2);
+        const int kx0 = xb * TC;
+        const float2* col = reinterpret_cast<const float2*>(buf + f * COLB) + c;   // rows z of TC columns
+        float2 v[NZ];
+#pragma unroll
+        for (int z = 0; z < NZ; ++z) v[z] = col[z * TC];
+        __syncthreads();                                   // every column is in registers: buf is free
+        if (threadIdx.x == 0 && t + gridDim.x < T) issue(t + gridDim.x);
+        const int64_t base = (((int64_t)b * F + f) * NZ * 4 + q) * NP + (int64_t)kyp * Nx + kx0 + c;
+        zpass_tile<NZ, F>(v, sm, S, spec, Nx, Ny, kx0, kyp, q, c, f, pz, base, zs);
+        __syncthreads();                                   // the line area is reused by the next tile
+    }
+    if (failed && threadIdx.x == 0) {
+        atomicAdd(&g_wait_timeouts, 1);
+        mbar_wait_bounded(bar, parity);                    // the copy still in flight, bounded
     }
 }
 
@@ -778,6 +911,47 @@ static void launch_zpass_reg(const aimx_ctx* ctx, float2* S, int B, cudaStream_t
         S, reinterpret_cast<const float2*>(ctx->f32.spec), ctx->n[0], ctx->n[1], B);
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link-time driver dependency)
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !p) {
+            cudaGetLastError();
+            throw Error{AIMX_E_CUDA, "cuTensorMapEncodeTiled is not available"};
+        }
+        fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+template <int NZ, int F>
+static void launch_zpass_tma(const aimx_ctx* ctx, float2* S, int B, cudaStream_t s) {
+    constexpr int TC = 8, LP = 2 * NZ + 2, FS = TC * LP + 1;
+    const int Nx = ctx->n[0], Ny = ctx->n[1];
+    // S as float32 [B F NZ][4][Ny][2 Nx]; the box is TC complex columns (64 B, x a multiple of
+    // 16 floats) by NZ planes of one field
+    CUtensorMap map;
+    const cuuint64_t dims[4] = {(cuuint64_t)2 * Nx, (cuuint64_t)Ny, 4, (cuuint64_t)B * F * NZ};
+    const cuuint64_t strides[3] = {(cuuint64_t)Nx * sizeof(float2), (cuuint64_t)Nx * Ny * sizeof(float2),
+                                   (cuuint64_t)4 * Nx * Ny * sizeof(float2)};
+    const cuuint32_t box[4] = {2 * TC, 1, 1, NZ};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    if (reinterpret_cast<uintptr_t>(S) % 16 != 0) throw Error{AIMX_E_CUDA, "z-pass buffer not 16-byte aligned"};
+    const CUresult r = tensor_map_encoder()(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, S, dims, strides, box, estr,
+                                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) throw Error{AIMX_E_CUDA, "cuTensorMapEncodeTiled failed for the z-pass"};
+    const size_t sm = 128 + (size_t)F * NZ * TC * sizeof(float2) + (size_t)F * FS * sizeof(float2);
+    set_smem(k_zpass_tma<NZ, F>, sm);
+    const int64_t T = (int64_t)(Nx / TC) * Ny * 4 * B;
+    const int grid = (int)std::min<int64_t>(T, 2 * (int64_t)num_sms());
+    k_zpass_tma<NZ, F><<<grid, 2 * F * TC, sm, s>>>(map, S, reinterpret_cast<const float2*>(ctx->f32.spec), Nx, Ny, B);
+}
+
 struct FusedBufs {
     float2 *xT, *G, *S, *part;
 };
@@ -827,7 +1001,23 @@ static void run_fused(aimx_ctx* ctx, const NearC& nc, int B, const float2* xb, f
     AIMX_CUDA_TRY(cudaGetLastError());
     delete sc;
     sc = scope(ST_ZPASS);
-    if (reg) {
+    if (reg && ctx->sched_variant == 3) {
+        if (F == 4) {
+            switch (Nz) {
+                case 8: launch_zpass_tma<8, 4>(ctx, fb.S, B, s); break;
+                case 16: launch_zpass_tma<16, 4>(ctx, fb.S, B, s); break;
+                case 32: launch_zpass_tma<32, 4>(ctx, fb.S, B, s); break;
+                default: launch_zpass_tma<64, 4>(ctx, fb.S, B, s); break;
+            }
+        } else {
+            switch (Nz) {
+                case 8: launch_zpass_tma<8, 8>(ctx, fb.S, B, s); break;
+                case 16: launch_zpass_tma<16, 8>(ctx, fb.S, B, s); break;
+                case 32: launch_zpass_tma<32, 8>(ctx, fb.S, B, s); break;
+                default: launch_zpass_tma<64, 8>(ctx, fb.S, B, s); break;
+            }
+        }
+    } else if (reg) {
         if (F == 4) {
             switch (Nz) {
                 case 8: launch_zpass_reg<8, 4>(ctx, fb.S, B, s); break;
@@ -982,3 +1172,19 @@ void matvec_fused_into(aimx_ctx* ctx, double freq, int B, const float* x, float*
 }
 
 }  // namespace aimx
+
+extern "C" int aimx_wait_timeouts(int* count) {
+    if (!count) return AIMX_E_ARG;
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, aimx::g_wait_timeouts, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return AIMX_E_CUDA;
+    }
+    const int zero = 0;
+    if (cudaMemcpyToSymbol(aimx::g_wait_timeouts, &zero, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return AIMX_E_CUDA;
+    }
+    *count = v;
+    return AIMX_OK;
+}

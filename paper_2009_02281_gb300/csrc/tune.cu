@@ -70,6 +70,7 @@ bool schedule_valid(const aimx_ctx* ctx, const aimx_schedule& s) {
     if (s.pass < 0) return false;
     if (s.variant == 2) return true;
     if (s.variant == 1) return fused_supported(ctx);
+    if (s.variant == 3) return fused_reg_supported(ctx);
     if (s.variant == 0) return true;   // register kernels where they apply, else the fused or generic default
     return false;
 }
@@ -115,6 +116,7 @@ int aimx_autotune(aimx_ctx* ctx, double freq, int nrhs, const char* cache_path, 
     // candidates: kernel variants the grid allows x passes {all, 1/2, 1/4 of the RHS (>= 4)}
     std::vector<int> variants;
     if (fused_reg_supported(ctx)) variants.push_back(0);
+    if (fused_reg_supported(ctx)) variants.push_back(3);
     if (fused_supported(ctx)) variants.push_back(1);
     variants.push_back(2);
     std::vector<int> passes{0};
