@@ -480,8 +480,15 @@ def measure_batch(args, ws):
         e[3].record(stream)
         torch.cuda.synchronize()
         ms_tuned = _barrier_max(e[2].elapsed_time(e[3]) / reps, ws, device="cuda")
+        # members are tuned alone; inside the concurrent graph keep their choices only if the
+        # whole call got faster
+        kept = ms_tuned < ms_graph
+        if not kept:
+            for c in ctxs:
+                c.set_schedule(0, 0)
         tuned = {"ms_per_call": round(ms_tuned, 3), "speedup_vs_default": round(ms_graph / ms_tuned, 3),
-                 "tune_s": round(tune_s, 2), "cache_hits": hits, "schedules": picks}
+                 "tune_s": round(tune_s, 2), "cache_hits": hits, "schedules": picks,
+                 "kept": bool(kept)}
     rhs = sum(m["nrhs"] for m in members)
     step_bytes = 0.0
     bins = {}
