@@ -227,7 +227,8 @@ int aimx_precond_apply(aimx_ctx* ctx, double freq, int precond, int nrhs, const 
 /* Plane-wave right-hand sides (Eq. EFIEdis / CFIEdis excitation): for wave w
  * with unit propagation direction dirs[w] and polarisation pols[w] (host
  * [nwave][3] doubles, E0 = 1 V/m, background medium), b[w] = <f_m, E_inc>,
- * and for AIMX_PMCHWT additionally eta0 <f_m, H_inc> in the second half.
+ * and for AIMX_PMCHWT additionally eta0 <f_m, H_inc> in the second half; for
+ * AIMX_CFIE b[w] = alpha <f_m, E_inc> + (1 - alpha) eta <f_m, n x H_inc>.
  * b: device [nwave][nunk] complex128.  Synchronises stream. */
 int aimx_rhs_planewave(aimx_ctx* ctx, double freq, int nwave, const double* dirs, const double* pols, void* b,
                        void* stream);
