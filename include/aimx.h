@@ -195,6 +195,8 @@ typedef struct {
     int32_t inner_precision;  /* AIMX_F32 (default) or AIMX_F64 products inside a cycle              */
     int32_t precond;          /* AIMX_PRECOND_DIAG (default), _NONE, _BLOCK or _LEARNED              */
     int32_t use_x0;           /* 1: x holds an initial guess on entry                                 */
+    int32_t learned_trial;    /* AIMX_PRECOND_LEARNED only: Krylov steps of the trial that compares it
+                                 with the diagonal preconditioner (0 = 10, < 0 = no trial)            */
 } aimx_solve_opts;
 
 typedef struct {
@@ -202,6 +204,8 @@ typedef struct {
     int32_t refinements;      /* FP64 refinement cycles used                                          */
     double rel_residual;      /* final |b - A x| / |b| from the FP64 product                         */
     int32_t status;           /* AIMX_OK or AIMX_E_NOCONV                                             */
+    int32_t precond_used;     /* the preconditioner that finished the solve (differs from the one
+                                 requested when the learned one lost its trial)                       */
 } aimx_solve_stats;
 
 /* Solve A(k) x = b for nrhs right-hand sides in lockstep (the iterative GMRES
@@ -214,6 +218,15 @@ typedef struct {
  * stats.rel_residual always computed, with the FP64 product.  b, x: device
  * [nrhs][nunk] complex128 (double2), caller-owned; stats: host array [nrhs] or
  * NULL.  Returns AIMX_E_NOCONV (> 0) when any right-hand side misses tol.
+ * With AIMX_PRECOND_LEARNED the diagonal preconditioner is its fallback and
+ * the true residual judges it: the solve first runs one short cycle
+ * (learned_trial Krylov steps) with each of the two from the same start, and
+ * continues from the learned one's iterate unless its true residual is more
+ * than twice the diagonal one's for the median right-hand side, in which case
+ * it continues from the diagonal one's iterate with the diagonal
+ * preconditioner; both trials count in stats.iterations and
+ * stats.precond_used names the winner.  The trial catches networks that are
+ * bad from the start, not ones that only fall behind after many steps.
  * Synchronises stream. */
 int aimx_solve(aimx_ctx* ctx, double freq, int nrhs, const void* b, void* x, const aimx_solve_opts* opts,
                aimx_solve_stats* stats, void* stream);

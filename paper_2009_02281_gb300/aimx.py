@@ -166,22 +166,22 @@ class _AdamOpts(ctypes.Structure):
 class _SolveOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int32), ("max_iter", ctypes.c_int32),
                 ("max_refine", ctypes.c_int32), ("inner_precision", ctypes.c_int32), ("precond", ctypes.c_int32),
-                ("use_x0", ctypes.c_int32)]
+                ("use_x0", ctypes.c_int32), ("learned_trial", ctypes.c_int32)]
 
 
 class _SolveStats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("refinements", ctypes.c_int32), ("rel_residual", ctypes.c_double),
-                ("status", ctypes.c_int32)]
+                ("status", ctypes.c_int32), ("precond_used", ctypes.c_int32)]
 
 
-def _opts(tol, restart, max_iter, inner_precision, precond, use_x0=0, max_refine=0):
+def _opts(tol, restart, max_iter, inner_precision, precond, use_x0=0, max_refine=0, learned_trial=0):
     return _SolveOpts(float(tol), int(restart), int(max_iter), int(max_refine), int(inner_precision), int(precond),
-                      int(use_x0))
+                      int(use_x0), int(learned_trial))
 
 
 def _stats_list(arr):
-    return [dict(iterations=s.iterations, refinements=s.refinements, rel_residual=s.rel_residual, status=s.status)
-            for s in arr]
+    return [dict(iterations=s.iterations, refinements=s.refinements, rel_residual=s.rel_residual, status=s.status,
+                 precond_used=s.precond_used) for s in arr]
 
 
 def lib_path():
@@ -349,7 +349,7 @@ class Context:
         return b
 
     def solve(self, freq, b, x0=None, tol=1e-6, restart=50, max_iter=1000, inner_precision=F32,
-              precond=PRECOND_DIAG, max_refine=0, stream=None):
+              precond=PRECOND_DIAG, max_refine=0, learned_trial=0, stream=None):
         """Solve A x = b for CUDA complex128 b [nrhs, nunk]; returns (x, stats, status)."""
         import torch
         if b.dim() == 1:
@@ -357,7 +357,8 @@ class Context:
         b = b.contiguous()
         x = x0.clone().contiguous() if x0 is not None else torch.empty_like(b)
         st = (_SolveStats * b.shape[0])()
-        o = _opts(tol, restart, max_iter, inner_precision, precond, 1 if x0 is not None else 0, max_refine)
+        o = _opts(tol, restart, max_iter, inner_precision, precond, 1 if x0 is not None else 0, max_refine,
+                  learned_trial)
         rc = self._check(self._lib.aimx_solve(self._ctx, float(freq), b.shape[0], ctypes.c_void_p(b.data_ptr()),
                                               ctypes.c_void_p(x.data_ptr()), ctypes.byref(o), st,
                                               _stream_handle(stream)))

@@ -420,7 +420,8 @@ extern "C" int aimx_solve(aimx_ctx* ctx, double freq, int nrhs, const void* bdev
         double2* x = (double2*)xdev;
         Coefs cf = near_coefs(ctx, freq);
         const bool block = o.precond == AIMX_PRECOND_BLOCK;
-        const bool learned = o.precond == AIMX_PRECOND_LEARNED;
+        bool learned = o.precond == AIMX_PRECOND_LEARNED;   // cleared if it loses its trial
+        int used = o.precond;
         if (block) precond_block_prepare(ctx, freq, s);
         if (learned) learned_prepare(ctx, freq, s);
         if (o.precond == AIMX_PRECOND_NONE || block || learned) {
@@ -471,6 +472,20 @@ extern "C" int aimx_solve(aimx_ctx* ctx, double freq, int nrhs, const void* bdev
         std::vector<double2> hb1((size_t)nrhs * (m + 1)), hb2((size_t)nrhs * (m + 1));
         std::vector<double> scale(nrhs);
         std::vector<double2> coef((size_t)nrhs * (m + 1));
+        // learned-preconditioner trial: phase 1 runs a short cycle with the learned one, phase 2
+        // the same from the same start with the diagonal one; the better true residual continues
+        const int trial = o.learned_trial == 0 ? 10 : o.learned_trial;
+        int phase = (learned && trial > 0) ? 1 : 0;
+        int mcap = phase ? std::min(trial, m) : m;
+        double2* x0 = nullptr;
+        double2* xl = nullptr;
+        std::vector<double> relres0, relres_l;
+        if (phase) {
+            x0 = (double2*)alloc(sizeof(double2) * nv);
+            xl = (double2*)alloc(sizeof(double2) * nv);
+            AIMX_CUDA_TRY(cudaMemcpyAsync(x0, x, sizeof(double2) * nv, cudaMemcpyDeviceToDevice, s));
+            relres0 = relres;
+        }
         for (int ref = 0; ref < o.max_refine; ++ref) {
             auto count_active = [&]() {
                 int c = 0;
@@ -503,7 +518,7 @@ extern "C" int aimx_solve(aimx_ctx* ctx, double freq, int nrhs, const void* bdev
             AIMX_CUDA_TRY(cudaMemcpyAsync(dscale, scale.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
             k_scale<<<nblk(nv), 256, 0, s>>>(W.r, W.V, dscale, nunk, nunk, vstride, nrhs);
             int jlast = 0;
-            for (int j = 0; j < m; ++j) {
+            for (int j = 0; j < mcap; ++j) {
                 // w = A M v_j
                 const double2* vj = W.V + (int64_t)j * nunk;
                 if (o.inner_precision == AIMX_F32) {
@@ -599,7 +614,7 @@ extern "C" int aimx_solve(aimx_ctx* ctx, double freq, int nrhs, const void* bdev
                     scale[k] = (!done[k] && hn[k] > 0) ? 1.0 / hn[k] : 0.0;
                     ndone += done[k];
                 }
-                if (ndone == nrhs || j + 1 == m) break;
+                if (ndone == nrhs || j + 1 == mcap) break;
                 AIMX_CUDA_TRY(cudaMemcpyAsync(dscale, scale.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
                 k_scale<<<nblk(nv), 256, 0, s>>>(W.w, W.V + (int64_t)(j + 1) * nunk, dscale, nunk, nunk, vstride, nrhs);
             }
@@ -626,6 +641,47 @@ extern "C" int aimx_solve(aimx_ctx* ctx, double freq, int nrhs, const void* bdev
             }
             AIMX_CUDA_TRY(cudaGetLastError());
             true_residual(low);
+            if (phase == 1) {
+                // learned trial done: keep its iterate, restart from x0 with the diagonal one
+                // (unless the learned cycle already converged everything)
+                int left = 0;   // not converged (a non-finite residual counts as not converged)
+                for (int k = 0; k < nrhs; ++k) left += (relres[k] <= o.tol) ? 0 : 1;
+                if (left == 0) {
+                    phase = 0;
+                    mcap = m;
+                    continue;
+                }
+                relres_l = relres;
+                AIMX_CUDA_TRY(cudaMemcpyAsync(xl, x, sizeof(double2) * nv, cudaMemcpyDeviceToDevice, s));
+                AIMX_CUDA_TRY(cudaMemcpyAsync(x, x0, sizeof(double2) * nv, cudaMemcpyDeviceToDevice, s));
+                k_build_precond<<<nblk(N), 256, 0, s>>>(ctx->d_diag, ctx->d_gdiag, ctx->d_perm, W.minv, N, ctx->form,
+                                                         cf.near[0], cf.near[1], cf.near[2], cf.near[3], cf.near[4],
+                                                         cf.near[5]);
+                AIMX_CUDA_TRY(cudaGetLastError());
+                learned = false;
+                true_residual(low);
+                phase = 2;
+            } else if (phase == 2) {
+                // compare the two trials on the right-hand sides that were still open
+                std::vector<double> ratio;   // learned / diagonal; a non-finite learned residual loses
+                for (int k = 0; k < nrhs; ++k)
+                    if (relres0[k] > o.tol && relres[k] > 0 && std::isfinite(relres[k]))
+                        ratio.push_back(std::isfinite(relres_l[k]) ? relres_l[k] / relres[k] : HUGE_VAL);
+                std::sort(ratio.begin(), ratio.end());
+                // the learned one stays unless it is clearly behind: early Krylov steps of a good
+                // network and of the diagonal one reduce the residual about equally, a bad network's
+                // residual stays several times higher
+                const bool keep_learned = ratio.empty() || ratio[ratio.size() / 2] <= 2.0;
+                if (keep_learned) {
+                    AIMX_CUDA_TRY(cudaMemcpyAsync(x, xl, sizeof(double2) * nv, cudaMemcpyDeviceToDevice, s));
+                    learned = true;
+                    true_residual(low);
+                } else {
+                    used = AIMX_PRECOND_DIAG;
+                }
+                phase = 0;
+                mcap = m;
+            }
         }
         if (low) true_residual(false);   // reported residuals always from the FP64 product
         bool allok = true;
@@ -637,6 +693,7 @@ extern "C" int aimx_solve(aimx_ctx* ctx, double freq, int nrhs, const void* bdev
                 stats[k].refinements = refs[k];
                 stats[k].rel_residual = relres[k];
                 stats[k].status = ok ? AIMX_OK : AIMX_E_NOCONV;
+                stats[k].precond_used = used;
             }
         }
         if (!allok) rc = AIMX_E_NOCONV;

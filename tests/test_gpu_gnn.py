@@ -229,9 +229,13 @@ def test_training_lowers_loss_and_learned_solve_matches_lu(torch_cuda):
     dirs, pols = planewave_batch(2, seed=3)
     b = ctx.rhs_planewave(freq, dirs, pols)
     opts = dict(tol=1e-6, restart=300, max_iter=2000, inner_precision=F64)
-    xl, st_l, rc_l = ctx.solve(freq, b, precond=PRECOND_LEARNED, **opts)
+    # the preconditioner's own iteration count (no trial against the diagonal one)
+    xl, st_l, rc_l = ctx.solve(freq, b, precond=PRECOND_LEARNED, learned_trial=-1, **opts)
     xd, st_d, rc_d = ctx.solve(freq, b, precond=PRECOND_DIAG, **opts)
     assert rc_l == 0 and rc_d == 0
+    # with the trial (default) the trained network wins it and finishes the solve
+    _, st_t, rc_t = ctx.solve(freq, b, precond=PRECOND_LEARNED, **opts)
+    assert rc_t == 0 and all(q["precond_used"] == PRECOND_LEARNED for q in st_t)
     it_l = [s["iterations"] for s in st_l]
     it_d = [s["iterations"] for s in st_d]
     print("loss", losses[0], np.mean(losses[-50:]), "iterations learned", it_l, "diag", it_d)
@@ -244,4 +248,41 @@ def test_training_lowers_loss_and_learned_solve_matches_lu(torch_cuda):
         got = xl[k].cpu().numpy()
         assert np.linalg.norm(got - ref) <= 1e-4 * np.linalg.norm(ref)
     net.close()
+    ctx.close()
+
+
+def test_untrained_network_loses_its_trial(torch_cuda):
+    """A network with random parameters preconditions badly: the short trial against the
+    diagonal preconditioner (judged by the true residual) hands the solve to the diagonal
+    one, which reaches the dense-LU solution."""
+    torch = torch_cuda
+    from synth import icosphere, planewave_batch
+    from oracle import operator as op, excitation, solve as osolve
+    from paper_2009_02281_gb300 import Context, Gnn, EFIE, F64, PRECOND_LEARNED, PRECOND_DIAG
+    xyz, tri = icosphere(2)
+    ctx = Context(xyz, tri, (16, 16, 16), order=2, formulation=EFIE)
+    freq = 299792458.0 / 2
+    net = Gnn(EFIE)
+    rng = np.random.default_rng(5)
+    net.set_params((0.5 * rng.standard_normal(net.params().size)).astype(np.float32))
+    ctx.gnn_attach(net)
+    net.close()
+    dirs, pols = planewave_batch(2, seed=3)
+    b = ctx.rhs_planewave(freq, dirs, pols)
+    opts = dict(tol=1e-6, restart=300, max_iter=2000, inner_precision=F64)
+    _, st_n, _ = ctx.solve(freq, b, precond=PRECOND_LEARNED, learned_trial=-1, **opts)
+    x, st, rc = ctx.solve(freq, b, precond=PRECOND_LEARNED, **opts)
+    _, st_d, _ = ctx.solve(freq, b, precond=PRECOND_DIAG, **opts)
+    assert rc == 0
+    assert all(q["precond_used"] == PRECOND_DIAG for q in st)
+    it = sum(q["iterations"] for q in st)
+    # the trial costs two short cycles at most on top of the diagonal solve, and beats the bad network
+    assert it <= sum(q["iterations"] for q in st_d) + 2 * 2 * 10
+    assert it < sum(q["iterations"] for q in st_n)
+    prob = op.setup(xyz, tri, 2, (16, 16, 16), radius=3)
+    A = op.dense_efie(prob, freq)
+    for k in range(2):
+        bo, _ = excitation.planewave_rhs(prob["rwg"], 2 * np.pi * freq / 299792458.0, dirs[k], pols[k])
+        ref = osolve.lu_solve(A, bo)
+        assert np.linalg.norm(x[k].cpu().numpy() - ref) <= 1e-4 * np.linalg.norm(ref)
     ctx.close()
