@@ -707,6 +707,8 @@ def run_ours(args):
     }
     if not args.no_solves:
         out["solves"] = measure_solves(ctx, wl, args)
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(wl, args.cpu_rows, ctx)
     if args.batch_members > 0:
         ctx.close()
         out["uneven_batch"] = measure_batch(args, ws)
@@ -716,8 +718,6 @@ def run_ours(args):
         out["conductor_bars"] = measure_config3(args, ws)
     if not args.no_learned_eval:
         out["learned_generalisation"] = learned_eval(args)
-    if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(wl, args.cpu_rows)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if args.batch_members <= 0:
@@ -745,21 +745,37 @@ class OracleSample:
         wl, op = self.wl, self.op
         t0 = time.perf_counter()
         if wl["formulation"] == "pmchwt":
-            op.matvec_pmchwt(self.prob, wl["freq"], self.x, wl["eps_out"], wl["eps_in"], rows=rows)
+            y = op.matvec_pmchwt(self.prob, wl["freq"], self.x, wl["eps_out"], wl["eps_in"], rows=rows)
             nout = 2 * len(rows)
         else:
-            op.matvec_efie(self.prob, wl["freq"], self.x, wl["eps_out"], rows=rows)
+            y = op.matvec_efie(self.prob, wl["freq"], self.x, wl["eps_out"], rows=rows)
             nout = len(rows)
+        self.y = y
         return nout, time.perf_counter() - t0
 
+    def sampled(self, y_full):
+        """The sampled rows of a full product vector, in the oracle's output order."""
+        if self.wl["formulation"] == "pmchwt":
+            n = len(y_full) // 2
+            return np.concatenate([y_full[self.rows], y_full[n + self.rows]])
+        return y_full[self.rows]
 
-def cpu_baseline(wl, rows):
+
+def cpu_baseline(wl, rows, ctx=None):
+    """The oracle timed on sampled rows; with ctx, also the GPU product's error on those rows."""
     s = OracleSample(wl, rows)
     nout, dt = s.run(s.rows)
     nunk = len(s.x)
-    return {"value": nout / nunk / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "%d of %d output rows of one matvec (%s) by direct grid summation, %.1f s, numpy "
-                      "default threading; value = rows/s divided by rows per matvec" % (nout, nunk, wl["name"], dt)}
+    out = {"value": nout / nunk / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+           "sample": "%d of %d output rows of one matvec (%s) by direct grid summation, %.1f s, numpy "
+                     "default threading; value = rows/s divided by rows per matvec" % (nout, nunk, wl["name"], dt)}
+    if ctx is not None:
+        import torch
+        xg = torch.tensor(s.x[None].astype(np.complex64), device="cuda")
+        yg = ctx.matvec(wl["freq"], xg).cpu().numpy()[0].astype(np.complex128)
+        e32 = float(np.linalg.norm(s.sampled(yg) - s.y) / np.linalg.norm(s.y))
+        out["gpu_fp32_rel_err_on_sample"] = e32
+    return out
 
 
 def run_reference(args):
