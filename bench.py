@@ -135,8 +135,9 @@ def _traffic_record(kernel, workload):
     h = re.search(r"source_sha256:\s*([0-9a-f]+)", txt)
     if not m or not h:
         return None
-    src = open(os.path.join(ROOT, "paper_2009_02281_gb300", "csrc", "fused.cu"), "rb").read()
-    src += open(os.path.join(ROOT, "paper_2009_02281_gb300", "csrc", "fftreg.cuh"), "rb").read()
+    src = b""
+    for f in ("fused.cu", "fftreg.cuh", "regfft.cuh"):   # the plane-fused kernels' sources
+        src += open(os.path.join(ROOT, "paper_2009_02281_gb300", "csrc", f), "rb").read()
     if hashlib.sha256(src).hexdigest()[:16] != h.group(1)[:16]:
         return None
     return float(m.group(1))
