@@ -288,9 +288,11 @@ __global__ void k_edge_message(const float* __restrict__ P, const float* __restr
     const float cb0 = bf(w, oc + lane), cb1 = bf(w, oc + lane + 32);
     for (int m = warp; m < N; m += nwarp) {
         float s0 = 0.f, s1 = 0.f;
+        // branch-free (the self pair contributes an exact zero) so that the loads of several
+        // edges can be in flight together
         auto edge = [&](int t) {
             const int n = cols[t];
-            if (n == m) return;
+            const float keep = n != m ? 1.f : 0.f;
             float ef[kNed];
             load_row<kNed>(e, t, ef);
             float w0 = P[(int64_t)n * kW + lane] + cb0, w1 = P[(int64_t)n * kW + lane + 32] + cb1;
@@ -299,17 +301,19 @@ __global__ void k_edge_message(const float* __restrict__ P, const float* __restr
                 w0 = fmaf(C0[f], ef[f], w0);
                 w1 = fmaf(C1[f], ef[f], w1);
             }
-            s0 += fmaxf(w0, 0.f);
-            s1 += fmaxf(w1, 0.f);
+            s0 += keep * fmaxf(w0, 0.f);
+            s1 += keep * fmaxf(w1, 0.f);
         };
-        // two edges per iteration keep two independent gathers in flight
+        // four edges per iteration keep four independent gathers in flight
         int t = row_ptr[m];
         const int te = row_ptr[m + 1];
-        for (; t + 1 < te; t += 2) {
+        for (; t + 3 < te; t += 4) {
             edge(t);
             edge(t + 1);
+            edge(t + 2);
+            edge(t + 3);
         }
-        if (t < te) edge(t);
+        for (; t < te; ++t) edge(t);
         const float di = deginv[m];
         S[(int64_t)m * kW + lane] = s0 * di;
         S[(int64_t)m * kW + lane + 32] = s1 * di;
@@ -672,7 +676,7 @@ __global__ void k_edge_backward(const float* __restrict__ P, const float* __rest
         float d0 = 0.f, d1 = 0.f;
         auto edge = [&](int t) {
             const int m = cols[t];
-            if (m == n) return;
+            const bool keep = m != n;   // the self pair contributes exact zeros (branch-free)
             const int tr = trans[t];  // edge (m, n) in row m
             float ef[kNed];
             load_row<kNed>(e, tr, ef);
@@ -683,8 +687,8 @@ __global__ void k_edge_backward(const float* __restrict__ P, const float* __rest
                 w0 = fmaf(C0[f], ef[f], w0);
                 w1 = fmaf(C1[f], ef[f], w1);
             }
-            const float g0 = w0 > 0.f ? ds0 : 0.f;
-            const float g1 = w1 > 0.f ? ds1 : 0.f;
+            const float g0 = (keep && w0 > 0.f) ? ds0 : 0.f;
+            const float g1 = (keep && w1 > 0.f) ? ds1 : 0.f;
             d0 += g0;
             d1 += g1;
 #pragma unroll
@@ -695,11 +699,13 @@ __global__ void k_edge_backward(const float* __restrict__ P, const float* __rest
         };
         int t = row_ptr[n];
         const int te = row_ptr[n + 1];
-        for (; t + 1 < te; t += 2) {
+        for (; t + 3 < te; t += 4) {
             edge(t);
             edge(t + 1);
+            edge(t + 2);
+            edge(t + 3);
         }
-        if (t < te) edge(t);
+        for (; t < te; ++t) edge(t);
         ac0 += d0;
         ac1 += d1;
         dP[(int64_t)n * kW + lane] = d0;
@@ -735,8 +741,13 @@ __global__ void __launch_bounds__(256) k_rows_wgrad(const float* __restrict__ A,
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc[a][c] = 0.f;
-    for (int64_t r0 = lo; r0 < hi; r0 += 32) {
-        for (int k = t; k < 32 * kW; k += 256) {
+    // the next 32-row chunk is loaded into registers while the current one is multiplied
+    constexpr int PER = 32 * kW / 256;
+    float ra[PER], rb[PER];
+    auto load_chunk = [&](int64_t r0) {
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            const int k = t + 256 * i;
             const int r = k / kW, c = k % kW;
             float va = 0.f, vb = 0.f;
             if (r0 + r < hi) {
@@ -748,10 +759,20 @@ __global__ void __launch_bounds__(256) k_rows_wgrad(const float* __restrict__ A,
                 }
                 if (c < nb) vb = B[(r0 + r) * nb + c];
             }
-            As[r][c] = va;
-            Bs[r][c] = vb;
+            ra[i] = va;
+            rb[i] = vb;
+        }
+    };
+    if (lo < hi) load_chunk(lo);
+    for (int64_t r0 = lo; r0 < hi; r0 += 32) {
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            const int k = t + 256 * i;
+            As[k / kW][k % kW] = ra[i];
+            Bs[k / kW][k % kW] = rb[i];
         }
         __syncthreads();
+        if (r0 + 32 < hi) load_chunk(r0 + 32);
         if (active) {
 #pragma unroll 8
             for (int r = 0; r < 32; ++r) {
