@@ -1,10 +1,11 @@
 // Whole-line FFTs held in one thread's registers (lengths 8..64).
 //
-// Radix-2 decimation in time on a register array with compile-time indices:
-// the bit-reversal is a renaming, twiddles W_L^k come from a constant-memory
-// table read at warp-uniform addresses, and the trivial twiddles (1 and -i)
-// are applied without multiplications.  Natural order in and out; INV gives
-// the unnormalised inverse.
+// Decimation in time on a register array with compile-time indices: radix 4
+// for lengths that are powers of four (16, 64), radix 2 otherwise.  The digit
+// reversal is a renaming, twiddles W_L^k come from a constant-memory table read
+// at warp-uniform addresses, and the trivial twiddles (1, -1, -i) are applied
+// without multiplications.  Natural order in and out; INV gives the
+// unnormalised inverse.
 #pragma once
 
 #include "cplx.cuh"
@@ -50,9 +51,58 @@ __device__ __forceinline__ float2 tw_mul(float2 x, int k, int M) {
     return x * twc<INV>(k, M);
 }
 
+// Packed two-lane sums on FP32 pairs (one sm_100+ instruction for both lanes).  The
+// difference is an FMA with -1, which rounds exactly like the scalar subtraction.
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 psub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+
+// Two radix-4 butterflies of one stage (span q) at once, lanes j (even) and j + 1 of
+// group g: each lane's twiddles are applied in scalar form, then the sixteen sums run on
+// (lane j, lane j + 1) pairs of real parts and of imaginary parts.  Same operations and
+// rounding as two scalar butterflies, half the add instructions.
+template <bool INV>
+__device__ __forceinline__ void bfly4_pair(float2* v, int g, int j, int q) {
+    float2 R[4], I[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const float2 l0 = tw_mul<INV>(v[g + j + m * q], m * j, 4 * q);
+        const float2 l1 = tw_mul<INV>(v[g + j + 1 + m * q], m * (j + 1), 4 * q);
+        R[m] = make_float2(l0.x, l1.x);
+        I[m] = make_float2(l0.y, l1.y);
+    }
+    const float2 t0r = padd(R[0], R[2]), t0i = padd(I[0], I[2]);
+    const float2 t1r = psub(R[0], R[2]), t1i = psub(I[0], I[2]);
+    const float2 t2r = padd(R[1], R[3]), t2i = padd(I[1], I[3]);
+    const float2 dr = psub(R[1], R[3]), di = psub(I[1], I[3]);
+    // t3 = (-+i) d: forward (di, -dr), inverse (-di, dr)
+    float2 oR[4], oI[4];
+    oR[0] = padd(t0r, t2r);
+    oI[0] = padd(t0i, t2i);
+    oR[2] = psub(t0r, t2r);
+    oI[2] = psub(t0i, t2i);
+    if (INV) {
+        oR[1] = psub(t1r, di);
+        oI[1] = padd(t1i, dr);
+        oR[3] = padd(t1r, di);
+        oI[3] = psub(t1i, dr);
+    } else {
+        oR[1] = padd(t1r, di);
+        oI[1] = psub(t1i, dr);
+        oR[3] = psub(t1r, di);
+        oI[3] = padd(t1i, dr);
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        v[g + j + m * q] = make_float2(oR[m].x, oI[m].x);
+        v[g + j + 1 + m * q] = make_float2(oR[m].y, oI[m].y);
+    }
+}
+
 // Radix-4 decimation in time for L a power of four: base-4 digit reversal as a
 // renaming, then log4 L stages of radix-4 butterflies with three twiddles each
-// (fewer multiplications than the radix-2 form).  Natural order in and out.
+// (fewer multiplications than the radix-2 form).  Natural order in and out.  The
+// first stage (span 1, no twiddles) runs on complex values; later stages pair
+// neighbouring butterflies and run their sums as packed FP32x2 instructions.
 template <int L, bool INV>
 __device__ __forceinline__ void reg_fft4(float2 (&v)[L]) {
     constexpr int D = ilog2c(L) / 2;
@@ -66,23 +116,22 @@ __device__ __forceinline__ void reg_fft4(float2 (&v)[L]) {
         }
     }
 #pragma unroll
-    for (int q = 1; q < L; q *= 4) {
+    for (int g = 0; g < L; g += 4) {
+        const float2 a0 = v[g], a1 = v[g + 1], a2 = v[g + 2], a3 = v[g + 3];
+        const float2 t0 = a0 + a2, t1 = a0 - a2, t2 = a1 + a3;
+        const float2 d = a1 - a3;
+        const float2 t3 = INV ? make_float2(-d.y, d.x) : make_float2(d.y, -d.x);
+        v[g] = t0 + t2;
+        v[g + 1] = t1 + t3;
+        v[g + 2] = t0 - t2;
+        v[g + 3] = t1 - t3;
+    }
+#pragma unroll
+    for (int q = 4; q < L; q *= 4) {
 #pragma unroll
         for (int g = 0; g < L; g += 4 * q) {
 #pragma unroll
-            for (int j = 0; j < q; ++j) {
-                const float2 a0 = v[g + j];
-                const float2 a1 = tw_mul<INV>(v[g + j + q], j, 4 * q);
-                const float2 a2 = tw_mul<INV>(v[g + j + 2 * q], 2 * j, 4 * q);
-                const float2 a3 = tw_mul<INV>(v[g + j + 3 * q], 3 * j, 4 * q);
-                const float2 t0 = a0 + a2, t1 = a0 - a2, t2 = a1 + a3;
-                const float2 d = a1 - a3;
-                const float2 t3 = INV ? make_float2(-d.y, d.x) : make_float2(d.y, -d.x);   // (-+i)(a1 - a3)
-                v[g + j] = t0 + t2;
-                v[g + j + q] = t1 + t3;
-                v[g + j + 2 * q] = t0 - t2;
-                v[g + j + 3 * q] = t1 - t3;
-            }
+            for (int j = 0; j < q; j += 2) bfly4_pair<INV>(v, g, j, q);
         }
     }
 }
