@@ -788,7 +788,200 @@ def cpu_baseline(wl, rows, ctx=None):
         yg = ctx.matvec(wl["freq"], xg).cpu().numpy()[0].astype(np.complex128)
         e32 = float(np.linalg.norm(s.sampled(yg) - s.y) / np.linalg.norm(s.y))
         out["gpu_fp32_rel_err_on_sample"] = e32
+    out["host"] = host_cpu()
+    out["single_thread"] = oracle_single_thread(wl, max(2, rows // 8))
+    out["fast_cpu_reference"] = fast_cpu_reference(s)
     return out
+
+
+def host_cpu():
+    """Host CPU model and logical core count (lscpu, else /proc/cpuinfo)."""
+    import platform
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None and os.path.exists("/proc/cpuinfo"):
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                model = line.split(":", 1)[1].strip()
+                break
+    return {"nproc": os.cpu_count(), "model": model, "machine": platform.machine()}
+
+
+_SINGLE_THREAD_CHILD = """
+import json, sys
+import bench
+from synth import workloads
+wl = workloads.WORKLOADS[sys.argv[1]]()
+s = bench.OracleSample(wl, int(sys.argv[2]))
+nout, dt = s.run(s.rows)
+print(json.dumps({"nout": nout, "nunk": len(s.x), "s": dt}))
+"""
+
+
+def oracle_single_thread(wl, rows):
+    """The oracle sample with one BLAS / OpenMP thread, in a fresh interpreter (thread pools are
+    sized when numpy loads); returns {value, sample} or {error}."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               OMP_THREAD_LIMIT="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", _SINGLE_THREAD_CHILD, wl["name"], str(rows)], env=env, cwd=ROOT,
+                           capture_output=True, text=True, timeout=900)
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+    except (OSError, subprocess.SubprocessError, ValueError, IndexError) as e:
+        return {"error": "single-thread oracle run failed: %s" % str(e)[:200]}
+    return {"value": d["nout"] / d["nunk"] / d["s"], "unit": UNIT, "cores": 1,
+            "sample": "%d of %d output rows, %.1f s, one thread" % (d["nout"], d["nunk"], d["s"])}
+
+
+class FastCpuAIMx:
+    """An FP64 AIMx product on the host cores with NumPy and scipy.fft: a timing baseline for
+    the GPU product (a reasonably fast CPU program), not the oracle and not a fallback.
+
+    Projection by bincount onto the zero-padded (2N)^3 grid, forward FFTs of the projected
+    fields, the kernel spectra of every region combined per output field in the spectral domain
+    (scalar kernel for the vector and scalar potentials, the gradient kernel's cross product for
+    K), inverse FFTs of the output fields, interpolation by gather (W = P^T).  Kernel tables are
+    the oracle's (sampled G and grad G over all offsets, Eqs. Hmn and Hmm), embedded in the
+    circulant grid at offset mod 2N; their spectra are computed once per frequency.
+
+    The near correction is a CSR SpMV over the full near pattern with three value arrays (N^A,
+    N^Phi, N^K).  Only the sampled rows' near values exist on the host (integrating all of them in
+    Python would take far longer than the product), so the timed SpMV runs on placeholder values
+    of the true pattern and the accuracy check uses the exact near rows of the sample."""
+
+    def __init__(self, sample, workers):
+        import scipy.fft as sfft
+        import scipy.sparse as sp
+        from oracle import greens, grid as gridmod
+        self.sfft, self.workers = sfft, workers
+        self.s = sample
+        wl, prob = sample.wl, sample.prob
+        self.pmchwt = wl["formulation"] == "pmchwt"
+        g = prob["grid"]
+        Nx, Ny, Nz = g["n"]
+        self.M = (2 * Nz, 2 * Ny, 2 * Nx)
+        off = gridmod.stencil_offsets(g["order"])
+        node = prob["anc"][:, None, :] + off[None, :, :]
+        self.flat = ((node[..., 2] * self.M[1] + node[..., 1]) * self.M[2] + node[..., 0]).ravel()
+        self.lam = prob["lam"]
+        self.N = prob["N"]
+        w = 2.0 * np.pi * wl["freq"]
+        self.w = w
+        self.regions = sample.op.materials(wl["freq"], wl["eps_out"], wl["eps_in"] if self.pmchwt else None)[1]
+        t0 = time.perf_counter()
+        idx = [np.arange(-(n - 1), n) % m for n, m in zip((Nz, Ny, Nx), self.M)]
+        self.spec = []
+        for mu, eps, k in self.regions:
+            H = np.zeros(self.M, dtype=np.complex128)
+            H[np.ix_(*idx)] = greens.kernel_table(k, g["n"], g["h"])
+            Hs = sfft.fftn(H, workers=workers)
+            Gs = None
+            if self.pmchwt:
+                Gt = greens.grad_kernel_table(k, g["n"], g["h"])
+                Gs = np.zeros((3,) + self.M, dtype=np.complex128)
+                for a in range(3):
+                    Gs[a][np.ix_(*idx)] = Gt[a]
+                Gs = sfft.fftn(Gs, axes=(1, 2, 3), workers=workers)
+            self.spec.append((mu, eps, k, Hs, Gs))
+        self.spectra_s = time.perf_counter() - t0
+        rng = np.random.default_rng(11)
+        pat = (np.ones(len(prob["cols"])), prob["cols"], prob["row_ptr"])
+        self.near_pattern = sp.csr_matrix(pat, shape=(self.N, self.N))
+        self.near_vals = [rng.standard_normal(self.near_pattern.nnz) for _ in range(3)]
+
+    def _project(self, x):
+        size = self.M[0] * self.M[1] * self.M[2]
+        g = np.empty((4,) + self.M, dtype=np.complex128)
+        for f in range(4):
+            wts = (self.lam[:, :, f] * x[:, None]).ravel()
+            g[f] = (np.bincount(self.flat, weights=wts.real, minlength=size)
+                    + 1j * np.bincount(self.flat, weights=wts.imag, minlength=size)).reshape(self.M)
+        return self.sfft.fftn(g, axes=(1, 2, 3), workers=self.workers)
+
+    def _interp(self, O):
+        o = self.sfft.ifftn(O, axes=(1, 2, 3), workers=self.workers).reshape(4, -1)
+        nu = self.lam.shape[1]
+        return sum(np.einsum("nu,nu->n", self.lam[:, :, f], o[f][self.flat].reshape(-1, nu)) for f in range(4))
+
+    @staticmethod
+    def _cross(G, F):
+        return np.stack([G[1] * F[2] - G[2] * F[1], G[2] * F[0] - G[0] * F[2], G[0] * F[1] - G[1] * F[0]])
+
+    def far(self, x):
+        """The grid part W H P x of every output row (E rows, then H rows for the two-region form)."""
+        from oracle.constants import ETA0
+        w, N = self.w, self.N
+        if not self.pmchwt:
+            mu, eps, k, Hs, _ = self.spec[0]
+            FJ = self._project(x)
+            O = np.empty_like(FJ)
+            O[:3] = (1j * w * mu) * Hs * FJ[:3]
+            O[3] = (-1j * w * mu / k ** 2) * Hs * FJ[3]
+            return self._interp(O)
+        FJ, FM = self._project(x[:N]), self._project(x[N:])
+        OE = np.zeros_like(FJ)
+        OH = np.zeros_like(FJ)
+        for mu, eps, k, Hs, Gs in self.spec:
+            OE[:3] += (1j * w * mu) * Hs * FJ[:3] + ETA0 * self._cross(Gs, FM[:3])
+            OE[3] += (-1j * w * mu / k ** 2) * Hs * FJ[3]
+            OH[:3] += (ETA0 ** 2 * 1j * w * eps) * Hs * FM[:3] - ETA0 * self._cross(Gs, FJ[:3])
+            OH[3] += (-ETA0 ** 2 * 1j * w * eps / k ** 2) * Hs * FM[3]
+        return np.concatenate([self._interp(OE), self._interp(OH)])
+
+    def near_placeholder(self, x):
+        """Cost stand-in for the near correction: three CSR products per input vector block."""
+        A = self.near_pattern
+        ys = []
+        for xs in ((x,) if not self.pmchwt else (x[:self.N], x[self.N:])):
+            for v in self.near_vals:
+                A.data = v
+                ys.append(A @ xs)
+        return ys
+
+    def near_exact_rows(self, x):
+        """The exact near correction on the sampled rows (the oracle's integrals of those rows)."""
+        from oracle.constants import ETA0
+        op, prob, rows, w, N = self.s.op, self.s.prob, self.s.rows, self.w, self.N
+        if not self.pmchwt:
+            mu, eps, k, _, _ = self.spec[0]
+            return 1j * w * mu * (op.near_apply(prob, "NA", x, rows) - op.near_apply(prob, "NP", x, rows) / k ** 2)
+        nJ = {c: op.near_apply(prob, c, x[:N], rows) for c in ("NA", "NP", "NK")}
+        nM = {c: op.near_apply(prob, c, x[N:], rows) for c in ("NA", "NP", "NK")}
+        yE, yH = 0.0, 0.0
+        for mu, eps, k, _, _ in self.spec:
+            yE = yE + 1j * w * mu * (nJ["NA"] - nJ["NP"] / k ** 2) + ETA0 * nM["NK"]
+            yH = yH - ETA0 * nJ["NK"] + ETA0 ** 2 * 1j * w * eps * (nM["NA"] - nM["NP"] / k ** 2)
+        return np.concatenate([yE, yH])
+
+
+def fast_cpu_reference(sample, reps=3):
+    """Time FastCpuAIMx on the sample's workload and check it on the oracle's sampled rows."""
+    workers = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    fc = FastCpuAIMx(sample, workers)
+    setup_s = time.perf_counter() - t0
+    times = []
+    for _ in range(reps):
+        t = time.perf_counter()
+        yf = fc.far(sample.x)
+        fc.near_placeholder(sample.x)
+        times.append(time.perf_counter() - t)
+    y_rows = sample.sampled(yf) + fc.near_exact_rows(sample.x)
+    err = float(np.linalg.norm(y_rows - sample.y) / np.linalg.norm(sample.y))
+    ms = float(np.median(times))
+    return {"value": 1.0 / ms, "unit": UNIT, "cores": workers, "kind": "numpy + scipy.fft FP64 timing baseline",
+            "sample": "one full single-RHS product, median of %d; kernel spectra once per frequency "
+                      "(%.2f s, not timed per product); near SpMV on placeholder values of the true "
+                      "pattern (%d entries x 3)" % (reps, fc.spectra_s, len(fc.near_vals[0])),
+            "ms_per_matvec": round(1e3 * ms, 1), "setup_s": round(setup_s, 2),
+            "rel_err_vs_oracle_on_sample": err}
 
 
 def run_reference(args):
@@ -813,7 +1006,7 @@ def run_reference(args):
            "vs_baseline": None, "dtype": "c128 (f64)", "data": "synthetic", "impl": "reference",
            "config": {"workload": args.workload},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                            "sample": sample},
+                            "sample": sample, "host": host_cpu()},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
