@@ -721,7 +721,7 @@ def run_ours(args):
     if not args.no_solves:
         out["solves"] = measure_solves(ctx, wl, args)
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(wl, args.cpu_rows, ctx)
+        out["cpu_baseline"] = cpu_baseline(wl, args.cpu_rows, ctx, args.path)
     if args.batch_members > 0:
         ctx.close()
         out["uneven_batch"] = measure_batch(args, ws)
@@ -774,8 +774,10 @@ class OracleSample:
         return y_full[self.rows]
 
 
-def cpu_baseline(wl, rows, ctx=None):
-    """The oracle timed on sampled rows; with ctx, also the GPU product's error on those rows."""
+def cpu_baseline(wl, rows, ctx=None, path=0):
+    """The oracle timed on sampled rows; with ctx, also the GPU products' errors on those rows
+    (the timed FP32 product, and FP32 / FP64 on the generic and cuFFT comparison paths; the
+    context is returned to product path ``path``)."""
     s = OracleSample(wl, rows)
     nout, dt = s.run(s.rows)
     nunk = len(s.x)
@@ -784,10 +786,24 @@ def cpu_baseline(wl, rows, ctx=None):
                      "default threading; value = rows/s divided by rows per matvec" % (nout, nunk, wl["name"], dt)}
     if ctx is not None:
         import torch
-        xg = torch.tensor(s.x[None].astype(np.complex64), device="cuda")
-        yg = ctx.matvec(wl["freq"], xg).cpu().numpy()[0].astype(np.complex128)
-        e32 = float(np.linalg.norm(s.sampled(yg) - s.y) / np.linalg.norm(s.y))
-        out["gpu_fp32_rel_err_on_sample"] = e32
+        from paper_2009_02281_gb300 import F32
+        x32 = torch.tensor(s.x[None].astype(np.complex64), device="cuda")
+        x64 = torch.tensor(s.x[None].astype(np.complex128), device="cuda")
+
+        def err(x):
+            y = ctx.matvec(wl["freq"], x).cpu().numpy()[0].astype(np.complex128)
+            return float(np.linalg.norm(s.sampled(y) - s.y) / np.linalg.norm(s.y))
+
+        out["gpu_fp32_rel_err_on_sample"] = err(x32)
+        errs = {("fp32_plane_fused" if ctx.matvec_path(F32) == 0 else "fp32_generic"): out["gpu_fp32_rel_err_on_sample"]}
+        ctx.set_path(1)
+        errs["fp32_generic"] = err(x32)
+        errs["fp64_generic"] = err(x64)
+        ctx.set_path(2)
+        errs["fp32_cufft"] = err(x32)
+        errs["fp64_cufft"] = err(x64)
+        ctx.set_path(path)
+        out["gpu_rel_err_on_sample_by_path"] = errs
     out["host"] = host_cpu()
     out["single_thread"] = oracle_single_thread(wl, max(2, rows // 8))
     out["fast_cpu_reference"] = fast_cpu_reference(s)
