@@ -227,6 +227,10 @@ typedef struct {
  * preconditioner; both trials count in stats.iterations and
  * stats.precond_used names the winner.  The trial catches networks that are
  * bad from the start, not ones that only fall behind after many steps.
+ * Electrically small conductors (EFIE with k h below about 1e-3, h the mesh
+ * edge) can stall with AIMX_F32 inner products: the vector-potential term is
+ * O((k h)^2) of the scalar-potential term and falls below FP32 rounding, so the
+ * refinement stops short of tol (AIMX_E_NOCONV); use AIMX_F64 there.
  * Synchronises stream. */
 int aimx_solve(aimx_ctx* ctx, double freq, int nrhs, const void* b, void* x, const aimx_solve_opts* opts,
                aimx_solve_stats* stats, void* stream);
