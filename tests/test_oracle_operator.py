@@ -233,3 +233,52 @@ def test_gmres_matches_lu(small_sphere):
     x, it, rr = solve.gmres(lambda v: Z @ v, b, tol=1e-10, restart=50)
     assert rr <= 1e-10
     assert np.linalg.norm(x - solve.lu_solve(Z, b)) / np.linalg.norm(x) < 1e-8
+
+
+def test_loop_currents_scalar_potential(small_sphere):
+    """Divergence-free (loop) currents: the MoM scalar potential vanishes on them exactly; the
+    AIMx one does not.
+
+    A combination x of RWG functions with D x = 0 (D the RWG-to-triangle incidence, the discrete
+    divergence) carries no charge, so L^Phi x = int int div f_m div'(sum x_n f_n) G = 0 for any
+    kernel.  On a closed genus-0 surface the loop space has dimension N - T + 1 (Euler).  AIMx
+    projects each basis onto its own stencil (moment matching, Sec. II-B), so the projected charges
+    of neighbouring bases no longer cancel node by node: the grid charge P_rho x of a loop is not
+    zero, only its moments up to the stencil order vanish.  The remainder acts as a high-order
+    multipole source that the near correction removes only inside the near region, and the
+    residue left in L^Phi x, amplified by 1/k^2 at small k h, swamps the vector-potential term of
+    electrically small conductors (the case the AEFIE's charge form L^Phi = D^T P D avoids)."""
+    import scipy.linalg as sl
+    prob = small_sphere
+    r = prob["rwg"]
+    N, nt = r["n"], len(r["tri"])
+    T, P, C, S = rw.rwg_arrays(r)
+    D = np.zeros((nt, N))
+    for n in range(N):
+        D[T[n, 0], n] += r["length"][n]
+        D[T[n, 1], n] -= r["length"][n]
+    Q = sl.null_space(D)
+    assert Q.shape[1] == N - nt + 1
+    x = Q @ np.random.default_rng(1).standard_normal(Q.shape[1])
+    k = 0.5
+    _, LA, LP = mom.dense_efie_mom(r, k * C0 / (2 * np.pi))
+    nP, nx = np.linalg.norm(LP, 2), np.linalg.norm(x)
+    assert np.linalg.norm(LP @ x) <= 1e-12 * nP * nx
+    # the loop's grid charge is not zero, but its moments up to the stencil order vanish ...
+    grid = prob["grid"]
+    g = gm.project(prob["lam"], prob["anc"], grid, x, fields=(3,))[0]
+    Nx, Ny, Nz = grid["n"]
+    zz, yy, xx = np.meshgrid(*(np.arange(n) * grid["h"][a] + grid["origin"][a] for a, n in ((2, Nz), (1, Ny), (0, Nx))),
+                             indexing="ij")
+    assert np.abs(g).max() > 1e-3 * np.abs(x).max() * np.abs(D).max()
+    scale = np.sum(np.abs(g))
+    for ax in range(grid["order"] + 1):
+        for ay in range(grid["order"] + 1):
+            for az in range(grid["order"] + 1):
+                mom_ = np.sum(g * xx ** ax * yy ** ay * zz ** az)
+                assert abs(mom_) <= 1e-12 * scale * max(1.0, np.abs(xx).max()) ** (ax + ay + az)
+    # ... and the AIMx scalar potential of the loop leaves a residue far above rounding
+    GA, GP, _ = op._grid_matrices(prob, k, False)
+    LPa = op.near_dense(prob, "NP") + GP
+    leak = np.linalg.norm(LPa @ x) / (nP * nx)
+    assert 1e-6 < leak < 1e-2
