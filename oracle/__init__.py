@@ -31,6 +31,10 @@ Modules and the passages they follow:
 * ``mie``         -- Mie series for PEC and dielectric spheres (textbook).
 * ``mom``         -- dense MoM by direct integration (error reference).
 * ``solve``       -- dense LU and plain GMRES.
+* ``chargepot``   -- the EFIE scalar potential in charge form, L^Phi = D^T Pt D
+                     with the pulse matrix Pt in AIMx form (the discretisation of
+                     the augmented EFIE the paper cites for small conductors);
+                     oracle of a row with no GPU path yet.
 
 Where the paper is silent each module states the reading it takes.
 """

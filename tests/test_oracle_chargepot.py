@@ -1,0 +1,118 @@
+"""Pins for the charge-form scalar potential (oracle only; no GPU path yet).
+
+References other than the module itself: the Euler count of the loop space, the exact identity
+L^Phi_s = D^T Pt_s D against the RWG static integrals, moments of the pulse weights against a
+higher-order quadrature, the precorrection against explicit loops, the dense MoM scalar
+potential, and the vanishing potential of divergence-free currents.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import chargepot as cp, grid as gm, greens, mom, operator as op, static
+from oracle.quadrature import triangle_rule, map_points
+from oracle.constants import C0
+
+
+@pytest.fixture(scope="module")
+def ch1(small_sphere):
+    return cp.setup_charge(small_sphere)
+
+
+def test_incidence(small_sphere, ch1):
+    r = small_sphere["rwg"]
+    D = ch1["D"]
+    nt, N = D.shape
+    assert np.allclose(D.sum(axis=0), 0.0)                          # +l on T+, -l on T-
+    assert np.allclose(np.abs(D).sum(axis=0), 2 * r["length"])
+    assert np.linalg.matrix_rank(D) == nt - 1                        # closed surface: total charge 0
+    assert N - np.linalg.matrix_rank(D) == N - nt + 1                # Euler: loop space dimension
+
+
+def test_static_identity_against_rwg_integrals(small_sphere):
+    """L^Phi_s(m, n) = sum_ij D_im Pt_s(i, j) D_jn on every pair, including the singular ones."""
+    r = small_sphere["rwg"]
+    N, nt = r["n"], len(r["tri"])
+    ii, jj = np.meshgrid(np.arange(nt), np.arange(nt), indexing="ij")
+    Ps = cp.static_pulse(r, ii.ravel(), jj.ravel()).reshape(nt, nt)
+    mm, nn = np.meshgrid(np.arange(N), np.arange(N), indexing="ij")
+    LPs = static.static_direct(r, mm.ravel(), nn.ravel())[1].reshape(N, N)
+    D = cp.incidence(r)
+    assert np.abs(D.T @ Ps @ D - LPs).max() <= 1e-12 * np.abs(LPs).max()
+    assert np.allclose(Ps, Ps.T, rtol=1e-2, atol=0)                  # symmetric up to the outer rule
+
+
+def test_pulse_weight_moments(small_sphere, ch1):
+    """sum_u Lp[u, t] (r_u - c)^alpha = A_t^-1 int_T (r - c)^alpha dS for alpha_i <= n."""
+    r, g = small_sphere["rwg"], small_sphere["grid"]
+    o = g["order"]
+    off = gm.stencil_offsets(o)
+    bary, w = triangle_rule(10)
+    xyz, tri = r["xyz"], r["tri"]
+    for t in (0, 17, 55):
+        c = xyz[tri[t]].mean(axis=0)
+        nodes = g["origin"] + (ch1["anc_t"][t] + off) * g["h"]
+        q = map_points(bary, xyz[tri[t, 0]][None], xyz[tri[t, 1]][None], xyz[tri[t, 2]][None])[0]
+        for a in range(o + 1):
+            for b in range(o + 1):
+                for e in range(o + 1):
+                    lhs = np.sum(ch1["Lp"][t] * (nodes[:, 0] - c[0]) ** a * (nodes[:, 1] - c[1]) ** b
+                                 * (nodes[:, 2] - c[2]) ** e)
+                    rhs = np.sum(w * (q[:, 0] - c[0]) ** a * (q[:, 1] - c[1]) ** b * (q[:, 2] - c[2]) ** e)
+                    assert abs(lhs - rhs) <= 1e-12 * max(1.0, abs(rhs))
+
+
+def test_precorrection_vs_loops(small_sphere, ch1):
+    g = small_sphere["grid"]
+    off = gm.stencil_offsets(g["order"])
+    Lp, anc = ch1["Lp"], ch1["anc_t"]
+    span = ch1["radius"] + g["order"]
+    Hs, _ = greens.static_offset_kernels(g["h"], span)
+    picks = [0, 5, len(ch1["rows"]) // 2, len(ch1["rows"]) - 1]
+    rows, cols = ch1["rows"][picks], ch1["cols"][picks]
+    got = cp.pulse_precorrection(Lp, anc, g, rows, cols, ch1["radius"])
+    for p, (i, j) in enumerate(zip(rows, cols)):
+        want = 0.0
+        for u in range(len(off)):
+            for v in range(len(off)):
+                d = anc[i] + off[u] - anc[j] - off[v] + span
+                want += Lp[i, u] * Hs[d[2], d[1], d[0]] * Lp[j, v]
+        assert abs(got[p] - want) <= 1e-13 * max(1e-30, abs(want))
+
+
+def test_charge_form_against_mom_and_on_loops(small_sphere, ch1):
+    """The AIMx charge form approximates the MoM scalar potential as well as the RWG form does, and
+    gives divergence-free currents exactly zero potential where the RWG form leaves a residue."""
+    import scipy.linalg as sl
+    prob = small_sphere
+    r = prob["rwg"]
+    k = 0.5
+    LPc = cp.lphi_charge_dense(prob, ch1, k)
+    _, LA, LPm = mom.dense_efie_mom(r, k * C0 / (2 * np.pi))
+    GA, GP, _ = op._grid_matrices(prob, k, False)
+    LPr = op.near_dense(prob, "NP") + GP
+    ec = np.linalg.norm(LPc - LPm) / np.linalg.norm(LPm)
+    er = np.linalg.norm(LPr - LPm) / np.linalg.norm(LPm)
+    assert ec < 5e-3 and ec < 3 * er
+    x = sl.null_space(ch1["D"]) @ np.random.default_rng(1).standard_normal(r["n"] - len(r["tri"]) + 1)
+    nP, nx = np.linalg.norm(LPm, 2), np.linalg.norm(x)
+    assert np.linalg.norm(LPc @ x) <= 1e-12 * nP * nx
+    assert np.linalg.norm(LPr @ x) > 1e-6 * nP * nx
+
+
+def test_dense_efie_charge_solves_like_the_rwg_form_on_a_sphere(small_sphere, ch1):
+    """Plane-wave currents on a sphere at k a = 0.5 against MoM: the charge form is the more
+    accurate AIMx form (1.1e-3 against 2.5e-2 for the RWG form on this 8^3 grid), consistent with
+    the 1/k^2 amplifying the RWG form's scalar-potential residue on the current's loop part."""
+    from oracle.excitation import planewave_rhs
+    prob = small_sphere
+    r = prob["rwg"]
+    f = 0.5 * C0 / (2 * np.pi)
+    b = planewave_rhs(r, 0.5, [0, 0, 1.0], [1.0, 0, 0])
+    b = b[0] if isinstance(b, tuple) else b
+    Jm = np.linalg.solve(mom.dense_efie_mom(r, f)[0], b)
+    Jc = np.linalg.solve(cp.dense_efie_charge(prob, ch1, f), b)
+    Jr = np.linalg.solve(op.dense_efie(prob, f), b)
+    ec = np.linalg.norm(Jc - Jm) / np.linalg.norm(Jm)
+    er = np.linalg.norm(Jr - Jm) / np.linalg.norm(Jm)
+    assert ec < 5e-3 and ec < 0.2 * er
