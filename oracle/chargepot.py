@@ -27,7 +27,7 @@ import numpy as np
 
 from . import greens
 from . import grid as gridmod
-from .operator import materials, near_dense, _grid_matrices
+from .operator import materials, near_dense, near_apply, conv_full, _grid_matrices
 from .potentials import tri_potentials
 from .quadrature import triangle_rule, map_points, projection_order
 from .rwg import rwg_arrays
@@ -144,3 +144,28 @@ def dense_efie_charge(prob, ch, freq, eps_bg=1.0):
     GA, _, _ = _grid_matrices(prob, k, False)
     LA = near_dense(prob, "NA") + GA
     return 1j * w * mu * (LA - lphi_charge_dense(prob, ch, k) / k ** 2)
+
+
+def matvec_efie_charge(prob, ch, freq, x, eps_bg=1.0):
+    """y = j w mu [ (N^A + P_v^T H P_v) x - k^-2 D^T ((Pt_s,NR - Pt_s,P) + Lp^T H Lp) D x ]
+    by direct grid summation: the charge-form AIMx EFIE product (the RWG form is
+    ``operator.matvec_efie``)."""
+    w, regs = materials(freq, eps_bg)
+    mu, eps, k = regs[0]
+    g = prob["grid"]
+    Nx, Ny, Nz = g["n"]
+    # vector potential exactly as in the RWG form
+    f = gridmod.project(prob["lam"], prob["anc"], g, x, fields=(0, 1, 2))
+    H = greens.kernel_table(k, g["n"], g["h"])
+    GA = gridmod.interpolate(prob["lam"], prob["anc"], g, conv_full(H, f), fields=(0, 1, 2))
+    NA = near_apply(prob, "NA", x)
+    # scalar potential from the triangle charges q = D x
+    q = ch["D"] @ x
+    off = gridmod.stencil_offsets(g["order"])
+    node = ch["anc_t"][:, None, :] + off[None]
+    gq = np.zeros((1, Nz, Ny, Nx), dtype=np.complex128)
+    np.add.at(gq[0], (node[..., 2], node[..., 1], node[..., 0]), ch["Lp"] * q[:, None])
+    oq = conv_full(H, gq)[0]
+    phi = np.einsum("tu,tu->t", ch["Lp"], oq[node[..., 2], node[..., 1], node[..., 0]])
+    np.add.at(phi, ch["rows"], ch["NPt"] * q[ch["cols"]])
+    return 1j * w * mu * ((NA + GA) - (ch["D"].T @ phi) / k ** 2)

@@ -116,3 +116,15 @@ def test_dense_efie_charge_solves_like_the_rwg_form_on_a_sphere(small_sphere, ch
     ec = np.linalg.norm(Jc - Jm) / np.linalg.norm(Jm)
     er = np.linalg.norm(Jr - Jm) / np.linalg.norm(Jm)
     assert ec < 5e-3 and ec < 0.2 * er
+
+
+def test_matvec_equals_dense(small_sphere, ch1):
+    prob = small_sphere
+    f = 0.5 * C0 / (2 * np.pi)
+    x = np.random.default_rng(3).standard_normal(prob["N"]) + 1j * np.random.default_rng(4).standard_normal(prob["N"])
+    y = cp.matvec_efie_charge(prob, ch1, f, x)
+    Z = cp.dense_efie_charge(prob, ch1, f)
+    assert np.linalg.norm(y - Z @ x) <= 1e-12 * np.linalg.norm(Z @ x)
+    # and it differs from the RWG form only by the scalar-potential approximation
+    yr = op.matvec_efie(prob, f, x)
+    assert np.linalg.norm(y - yr) < 0.05 * np.linalg.norm(yr)
