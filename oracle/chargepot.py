@@ -27,7 +27,7 @@ import numpy as np
 
 from . import greens
 from . import grid as gridmod
-from .operator import materials, near_dense, near_apply, conv_full, _grid_matrices
+from .operator import materials, near_dense, near_apply, conv_full, conv_nodes, _grid_matrices, _grid_parts
 from .potentials import tri_potentials
 from .quadrature import triangle_rule, map_points, projection_order
 from .rwg import rwg_arrays
@@ -146,26 +146,44 @@ def dense_efie_charge(prob, ch, freq, eps_bg=1.0):
     return 1j * w * mu * (LA - lphi_charge_dense(prob, ch, k) / k ** 2)
 
 
-def matvec_efie_charge(prob, ch, freq, x, eps_bg=1.0):
+def matvec_efie_charge(prob, ch, freq, x, eps_bg=1.0, rows=None):
     """y = j w mu [ (N^A + P_v^T H P_v) x - k^-2 D^T ((Pt_s,NR - Pt_s,P) + Lp^T H Lp) D x ]
     by direct grid summation: the charge-form AIMx EFIE product (the RWG form is
-    ``operator.matvec_efie``)."""
+    ``operator.matvec_efie``).  With ``rows``, only those output rows: the scalar potential is
+    then evaluated on the two triangles of each row only (their stencil nodes, their near rows)."""
     w, regs = materials(freq, eps_bg)
     mu, eps, k = regs[0]
     g = prob["grid"]
     Nx, Ny, Nz = g["n"]
-    # vector potential exactly as in the RWG form
-    f = gridmod.project(prob["lam"], prob["anc"], g, x, fields=(0, 1, 2))
     H = greens.kernel_table(k, g["n"], g["h"])
-    GA = gridmod.interpolate(prob["lam"], prob["anc"], g, conv_full(H, f), fields=(0, 1, 2))
-    NA = near_apply(prob, "NA", x)
+    # vector potential exactly as in the RWG form
+    if rows is None:
+        f = gridmod.project(prob["lam"], prob["anc"], g, x, fields=(0, 1, 2))
+        GA = gridmod.interpolate(prob["lam"], prob["anc"], g, conv_full(H, f), fields=(0, 1, 2))
+    else:
+        GA = _grid_parts(prob, k, [x], rows, False)[0][0]
+    NA = near_apply(prob, "NA", x, rows)
     # scalar potential from the triangle charges q = D x
-    q = ch["D"] @ x
+    D = ch["D"]
+    q = D @ x
     off = gridmod.stencil_offsets(g["order"])
     node = ch["anc_t"][:, None, :] + off[None]
     gq = np.zeros((1, Nz, Ny, Nx), dtype=np.complex128)
     np.add.at(gq[0], (node[..., 2], node[..., 1], node[..., 0]), ch["Lp"] * q[:, None])
-    oq = conv_full(H, gq)[0]
-    phi = np.einsum("tu,tu->t", ch["Lp"], oq[node[..., 2], node[..., 1], node[..., 0]])
-    np.add.at(phi, ch["rows"], ch["NPt"] * q[ch["cols"]])
-    return 1j * w * mu * ((NA + GA) - (ch["D"].T @ phi) / k ** 2)
+    if rows is None:
+        tris = np.arange(len(q))
+        oq = conv_full(H, gq)[0][node[..., 2], node[..., 1], node[..., 0]]
+    else:
+        T = rwg_arrays(prob["rwg"])[0]
+        tris = np.unique(T[np.asarray(rows)].ravel())
+        nodes = node[tris].reshape(-1, 3)
+        uniq, inv = np.unique(nodes, axis=0, return_inverse=True)
+        oq = conv_nodes(H, gq, uniq)[0][inv.reshape(len(tris), -1)]
+    phi = np.zeros(len(q), dtype=np.complex128)
+    phi[tris] = np.einsum("tu,tu->t", ch["Lp"][tris], oq)
+    sel = np.isin(ch["rows"], tris)
+    np.add.at(phi, ch["rows"][sel], ch["NPt"][sel] * q[ch["cols"][sel]])
+    LPx = D.T @ phi
+    if rows is not None:
+        LPx = LPx[np.asarray(rows)]
+    return 1j * w * mu * ((NA + GA) - LPx / k ** 2)

@@ -128,3 +128,14 @@ def test_matvec_equals_dense(small_sphere, ch1):
     # and it differs from the RWG form only by the scalar-potential approximation
     yr = op.matvec_efie(prob, f, x)
     assert np.linalg.norm(y - yr) < 0.05 * np.linalg.norm(yr)
+
+
+def test_sampled_rows_equal_full_product(small_sphere, ch1):
+    prob = small_sphere
+    f = 0.7 * C0 / (2 * np.pi)
+    rng = np.random.default_rng(6)
+    x = rng.standard_normal(prob["N"]) + 1j * rng.standard_normal(prob["N"])
+    rows = np.array([0, 7, 33, 64, prob["N"] - 1])
+    y = cp.matvec_efie_charge(prob, ch1, f, x)
+    ys = cp.matvec_efie_charge(prob, ch1, f, x, rows=rows)
+    assert np.linalg.norm(ys - y[rows]) <= 1e-12 * np.linalg.norm(y[rows])
