@@ -388,6 +388,17 @@ int aimx_profile(aimx_ctx* ctx, int enable);
 int aimx_profile_read(aimx_ctx* ctx, double* ms, int64_t* launches, int max_stages);
 const char* aimx_profile_stage_name(int stage);
 
+/* ------------------------------------------------------------------ device peak
+ * FP32 arithmetic rate of the current device for the ALU roofline of the FFT
+ * passes (the paper has no counterpart; a measurement utility).  variant 0:
+ * chains of scalar FMAs, 1: packed two-lane FMAs (the form of the register
+ * FFTs' butterfly sums).  Runs 8 blocks of 256 threads per SM, 16 independent
+ * chains per thread, best of 5 timed launches with CUDA events on the legacy
+ * default stream; *tflops = FLOP/s / 1e12 with an FMA counted as 2 FLOPs (a
+ * packed FMA as 4).  Synchronous; allocates and frees 16 bytes.  Errors:
+ * AIMX_E_ARG (null pointer, unknown variant), AIMX_E_NOMEM, AIMX_E_CUDA. */
+int aimx_measure_fp32_peak(int variant, double* tflops);
+
 /* ------------------------------------------------------------------ allocation-free product
  * aimx_matvec_noalloc: the FP32 product y = A(k) x of aimx_matvec (plane-fused
  * path), for callers that must not allocate device memory when they need it,
@@ -397,10 +408,14 @@ const char* aimx_profile_stage_name(int stage);
  *   - Allocates nothing: no cudaMalloc / cudaFree / allocating library call.
  *     Its work buffers live in one file-scope static device array of 64 MiB
  *     that every device loading the library holds until the process exits.
- *   - Preconditions: the grid takes the plane-fused path (aimx_matvec_path(ctx,
- *     AIMX_F32) == 0) and aimx_matvec has run once in FP32 on this context (it
- *     creates the kernel-spectra buffers and plane tables that are reused here;
- *     a new frequency then regenerates spectra in place).  Otherwise
+ *   - Preconditions: FP32 products of this context take the plane-fused path
+ *     (aimx_matvec_path(ctx, AIMX_F32) == 0, i.e. the grid allows it and
+ *     neither aimx_set_path nor the schedule selects the generic path) and
+ *     aimx_matvec has run once in FP32 on this context (it creates the
+ *     kernel-spectra buffers and plane tables that are reused here; a new
+ *     frequency then regenerates spectra in place, on the stream).  In
+ *     conventional-AIM mode the frequency must be the one whose near entries
+ *     were last filled (a new fill would block the host).  Otherwise
  *     AIMX_E_STATE.
  *   - x, y: device [nrhs][nunk] float2, caller-owned, not overlapping.
  *     nrhs is limited by the 64 MiB array; larger requests return AIMX_E_ARG

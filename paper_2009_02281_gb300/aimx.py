@@ -103,6 +103,7 @@ _SIGS = [
     ("aimx_profile", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("aimx_profile_read", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     ("aimx_profile_stage_name", ctypes.c_char_p, [ctypes.c_int]),
+    ("aimx_measure_fp32_peak", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     ("aimx_matvec_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
                                            ctypes.c_void_p, ctypes.c_void_p]),
     ("aimx_solve", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
@@ -219,6 +220,15 @@ def wait_timeouts():
     if rc != 0:
         raise AimxError(rc)
     return n.value
+
+
+def measure_fp32_peak(packed=False):
+    """FP32 TFLOP/s of the current device (aimx_measure_fp32_peak): scalar or packed two-lane FMAs."""
+    t = ctypes.c_double(0.0)
+    rc = load().aimx_measure_fp32_peak(1 if packed else 0, ctypes.byref(t))
+    if rc != 0:
+        raise AimxError(rc)
+    return t.value
 
 
 def _stream_handle(stream):

@@ -10,11 +10,16 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libaimx.so")
 SOURCES = ["setup.cu", "fft.cu", "matvec.cu", "fused.cu", "solve.cu", "precond.cu", "gnn.cu", "batch.cu", "ports.cu",
-           "aim.cu", "tune.cu", "noalloc.cu", "api.cu"]
+           "aim.cu", "tune.cu", "noalloc.cu", "peak.cu", "api.cu"]
 HEADERS = ["aimx_internal.h", "cplx.cuh", "fftreg.cuh", "regfft.cuh", "geom.cuh"]
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
          "-diag-suppress", "177"]
+# extra nvcc flags and an output directory for side-by-side builds (e.g. AIMX_NVCC_FLAGS="-DNAME")
+EXTRA = os.environ.get("AIMX_NVCC_FLAGS", "").split()
+if os.environ.get("AIMX_LIB_DIR"):
+    OUT_DIR = os.environ["AIMX_LIB_DIR"]
+    LIB = os.path.join(OUT_DIR, "libaimx.so")
 
 
 def _nvcc():
@@ -45,7 +50,7 @@ def build(force=False, verbose=False):
 
     def compile_one(src):
         obj = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
-        cmd = [nvcc] + GENCODE + FLAGS + inc + ["-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [nvcc] + GENCODE + FLAGS + EXTRA + inc + ["-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s%s" % (src, r.stdout, r.stderr))

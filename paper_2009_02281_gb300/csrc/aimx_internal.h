@@ -241,6 +241,14 @@ struct aimx_ctx {
     float* d_S = nullptr;          // [B][F][Nz][4][Ny][Nx] complex (xy spectra, parity blocks)
     float* d_part = nullptr;       // [B][F/4][P][N] complex (per-plane interpolation partials)
     int fused_cap = 0;             // RHS capacity of the buffers above
+    // near rows grouped into blocks for the final kernel of the plane-fused path: each block
+    // is <= 32 consecutive internal rows whose near columns, taken together, are staged once
+    int nb_count = 0;              // row blocks (0 = not built, or a row too wide: CSR kernel)
+    int nb_umax = 0;               // largest column union of a block
+    int* d_nb_rows = nullptr;      // [nb_count+1] first internal row of each block
+    int* d_nb_ustart = nullptr;    // [nb_count+1] offset of each block's union in d_nb_ucols
+    int* d_nb_ucols = nullptr;     // [sum of unions] internal column ids, ascending per block
+    float4* d_nb_ent = nullptr;    // [nnz] CSR order: (union-local column as int bits, N^A, N^Phi, N^K or Gram)
     int max_plane_bases = 0;
     int* d_plane = nullptr;        // [2][Nz] plane_lo then plane_hi
     int path = 0;                  // 0 = automatic, 1 = generic FFT path, 2 = generic with cuFFT (comparison)

@@ -41,7 +41,8 @@ static void free_all(aimx_ctx* c) {
                     c->d_xT,      c->d_G,       c->d_S,        c->d_part,   c->d_plane,  c->d_q5,
                     c->pc.d_ptr,  c->pc.d_idx,  c->pc.d_work,  c->pc.d_inv, c->d_wsoa,   c->f32.ng,
                     c->f64.ng,    c->d_gdiag,   c->d_lin_ptr,  c->d_lin_cols, c->f64.la, c->f64.lp,
-                    c->f32.la,    c->f32.lp,    c->f64.zn,     c->f32.zn,     c->d_aim_row_of, c->d_aim_htab};
+                    c->f32.la,    c->f32.lp,    c->f64.zn,     c->f32.zn,     c->d_aim_row_of, c->d_aim_htab,
+                    c->d_nb_rows, c->d_nb_ustart, c->d_nb_ucols, c->d_nb_ent};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& r : c->prof.recs) {

@@ -19,13 +19,23 @@ namespace aimx {
 
 // ------------------------------------------------------------------ twiddles
 
-static double2* g_tw64 = nullptr;
-static float2* g_tw32 = nullptr;
+// one table pair per device: a context on another device must not be handed
+// this device's pointers
+constexpr int kTwMaxDevices = 64;
+static double2* g_tw64[kTwMaxDevices] = {};
+static float2* g_tw32[kTwMaxDevices] = {};
 static std::mutex g_tw_mutex;
 
-static void init_twiddles() {
+static int tw_device() {
+    int dev = 0;
+    AIMX_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kTwMaxDevices) throw Error{AIMX_E_STATE, "device index out of range"};
+    return dev;
+}
+
+static void init_twiddles(int dev) {
     std::lock_guard<std::mutex> lock(g_tw_mutex);
-    if (g_tw64) return;
+    if (g_tw64[dev]) return;
     const int H = kTwiddleLen;   // full circle: e^{-2 pi i k / 4096}, k < 4096
     std::vector<double2> t64(H);
     std::vector<float2> t32(H);
@@ -40,17 +50,19 @@ static void init_twiddles() {
     AIMX_CUDA_TRY(cudaMalloc(&d32, H * sizeof(float2)));
     AIMX_CUDA_TRY(cudaMemcpy(d64, t64.data(), H * sizeof(double2), cudaMemcpyHostToDevice));
     AIMX_CUDA_TRY(cudaMemcpy(d32, t32.data(), H * sizeof(float2), cudaMemcpyHostToDevice));
-    g_tw32 = d32;
-    g_tw64 = d64;
+    g_tw32[dev] = d32;
+    g_tw64[dev] = d64;
 }
 
 const double2* twiddles64() {
-    if (!g_tw64) init_twiddles();
-    return g_tw64;
+    const int dev = tw_device();
+    if (!g_tw64[dev]) init_twiddles(dev);
+    return g_tw64[dev];
 }
 const float2* twiddles32() {
-    if (!g_tw64) init_twiddles();
-    return g_tw32;
+    const int dev = tw_device();
+    if (!g_tw64[dev]) init_twiddles(dev);
+    return g_tw32[dev];
 }
 
 template <class T>

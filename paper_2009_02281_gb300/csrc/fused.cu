@@ -448,6 +448,126 @@ __global__ void __launch_bounds__(kThreads) k_final(const float2* __restrict__ p
     }
 }
 
+// K5, blocked form: the near correction of Eq. LAIMx (L_s,NR - L_s,P applied to x, Sec. III-A) for
+// a block of <= 32 anchor-sorted rows whose near columns, taken together, form a union of at most
+// a few hundred bases.  For each chunk of 32 right-hand sides (lane = RHS) and each unknown block
+// (J, then M), the block stages x of every union column once in shared memory; each warp then
+// walks its rows' CSR entries (one broadcast 16-byte load of local column and the three static
+// values per entry) and reads x from shared memory instead of gathering it from L2 per entry.
+// Sums run in CSR order per row, so results are bitwise reproducible.
+constexpr int kNbRows = 32;        // rows per block at most
+constexpr int kNbWarps = 16;
+constexpr int kNbUmax = 448;       // target column union per block
+
+template <int F>
+__global__ void __launch_bounds__(kNbWarps * 32) k_near_blk(
+    const float2* __restrict__ part, const float2* __restrict__ xT, const int* __restrict__ nb_rows,
+    const int* __restrict__ nb_ustart, const int* __restrict__ nb_ucols, const float4* __restrict__ ent,
+    const int* __restrict__ row_ptr, const int* __restrict__ perm, const int* __restrict__ lin_ptr,
+    const int* __restrict__ lin_cols, const float* __restrict__ la, const float* __restrict__ lp, float2* y,
+    NearC nc, int has_k, int N, int nunk, int P, int B) {
+    extern __shared__ float2 xs[];                         // [union][32]
+    __shared__ float2 accE[kNbRows][32];
+    __shared__ float2 accH[F == 8 ? kNbRows : 1][32];
+    __shared__ float4 ebuf[kNbWarps][32];                  // per-warp entry staging
+    constexpr int G = F / 4;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int r0 = nb_rows[blockIdx.x], nr = nb_rows[blockIdx.x + 1] - r0;
+    const int u0 = nb_ustart[blockIdx.x], nu = nb_ustart[blockIdx.x + 1] - u0;
+    for (int bc = 0; bc < B; bc += 32) {
+        const int nbc = min(32, B - bc);
+        // interpolation partials summed over the stencil slots, rows fastest (coalesced)
+        for (int idx = threadIdx.x; idx < G * 32 * kNbRows; idx += blockDim.x) {
+            const int r = idx % kNbRows, rest = idx / kNbRows;
+            const int bl = rest % 32, g = rest / 32;
+            float2 s = make_float2(0.f, 0.f);
+            if (r < nr && bl < nbc)
+                for (int sl = 0; sl < P; ++sl) s = s + part[(((int64_t)(bc + bl) * G + g) * P + sl) * N + r0 + r];
+            if (g == 0)
+                accE[r][bl] = s;
+            else if (F == 8)
+                accH[r][bl] = s;
+        }
+        // accumulators per row slot: J block (A, Phi, K) then M block (A, Phi, K)
+        float2 acc[2][6];
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+            for (int m = 0; m < 6; ++m) acc[k][m] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int ph = 0; ph < G; ++ph) {
+            __syncthreads();                              // xs free (and accE / accH written)
+            for (int u = warp; u < nu; u += kNbWarps)
+                xs[u * 32 + lane] =
+                    lane < nbc ? __ldg(xT + ((int64_t)ph * N + nb_ucols[u0 + u]) * B + bc + lane) : make_float2(0.f, 0.f);
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int r = warp + k * kNbWarps;
+                if (r >= nr) continue;   // warp-uniform
+                const int eb = row_ptr[r0 + r], e1 = row_ptr[r0 + r + 1];
+                float2 a = make_float2(0.f, 0.f), p = a, q = a;
+                // entries 32 at a time: one coalesced load per lane into this warp's buffer, the
+                // next 32 loaded while the current ones are applied
+                float4 nxt = eb + lane < e1 ? __ldg(ent + eb + lane) : make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int e0 = eb; e0 < e1; e0 += 32) {
+                    __syncwarp();
+                    ebuf[warp][lane] = nxt;
+                    __syncwarp();
+                    if (e0 + 32 + lane < e1) nxt = __ldg(ent + e0 + 32 + lane);
+                    const int cnt = min(32, e1 - e0);
+#pragma unroll 4
+                    for (int m = 0; m < cnt; ++m) {
+                        const float4 t = ebuf[warp][m];
+                        const float2 xv = xs[__float_as_int(t.x) * 32 + lane];
+                        rfma(a, t.y, xv);
+                        rfma(p, t.z, xv);
+                        rfma(q, t.w, xv);
+                    }
+                }
+                acc[k][3 * ph] = a;
+                acc[k][3 * ph + 1] = p;
+                acc[k][3 * ph + 2] = q;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int r = warp + k * kNbWarps;
+            if (r >= nr || lane >= nbc) continue;
+            const int i = r0 + r;
+            float2 e = accE[r][lane] + nc.c[0] * acc[k][0] + nc.c[1] * acc[k][1];
+            float2 h = make_float2(0.f, 0.f);
+            if (F == 4 && has_k) e = e + nc.c[2] * acc[k][2];
+            if (F == 8) {
+                e = e + nc.c[2] * acc[k][5];
+                h = accH[r][lane] + nc.c[3] * acc[k][2] + nc.c[4] * acc[k][3] + nc.c[5] * acc[k][4];
+            }
+            if (lin_ptr) {
+                // linear-term modification: a few overlapping pairs per row
+                const int l1 = lin_ptr[i + 1];
+                for (int le = lin_ptr[i]; le < l1; ++le) {
+                    const int j = lin_cols[le];
+                    const float va = __ldg(la + le), vp = __ldg(lp + le);
+                    e = e + (va * nc.lin[0] + vp * nc.lin[1]) * __ldg(xT + (int64_t)j * B + bc + lane);
+                    if (F == 8) h = h + (va * nc.lin[2] + vp * nc.lin[3]) * __ldg(xT + (int64_t)(N + j) * B + bc + lane);
+                }
+            }
+            y[(int64_t)(bc + lane) * nunk + perm[i]] = e;
+            if (F == 8) y[(int64_t)(bc + lane) * nunk + N + perm[i]] = h;
+        }
+        __syncthreads();                                  // accE / accH reused by the next chunk
+    }
+}
+
+// entries of the blocked near kernel: union-local column and the three static values
+__global__ void k_pack_near_ent(const int* __restrict__ li, const float* __restrict__ na,
+                                const float* __restrict__ np, const float* __restrict__ nk, int64_t nnz,
+                                float4* ent) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= nnz) return;
+    ent[e] = make_float4(__int_as_float(li[e]), na[e], np[e], nk ? nk[e] : 0.f);
+}
+
 // ------------------------------------------------------------------ register-FFT kernels
 // Square planes Nx = Ny = N <= 64 and Nz <= 64: every line transform runs in
 // one thread's registers; shared memory only carries the transposes.
@@ -857,19 +977,6 @@ bool fused_reg_supported(const aimx_ctx* ctx) { return fused_supported(ctx) && r
 // register kernels unless the schedule asks for the shared-memory ones
 static bool reg_path(const aimx_ctx* ctx) { return ctx->sched_variant != 1 && reg_shape(ctx); }
 
-static void ensure_const_twiddles() {
-    static bool done[64] = {};
-    int dev = 0;
-    AIMX_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev >= 0 && dev < 64 && done[dev]) return;
-    std::vector<float2> t(4096);
-    for (int k = 0; k < 4096; ++k) {
-        double a = -2.0 * kPi * (double)k / 4096.0;
-        t[k] = make_float2((float)std::cos(a), (float)std::sin(a));
-    }
-    AIMX_CUDA_TRY(cudaMemcpyToSymbol(c_tw4096, t.data(), sizeof(float2) * 4096));
-    if (dev >= 0 && dev < 64) done[dev] = true;
-}
 
 template <class K>
 static void set_smem(K kernel, size_t bytes) {
@@ -1058,6 +1165,22 @@ static void run_fused(aimx_ctx* ctx, const NearC& nc, int B, const float2* xb, f
     AIMX_CUDA_TRY(cudaGetLastError());
     delete sc;
     sc = scope(ST_FINAL);
+    if (!ctx->aim && ctx->nb_count > 0) {
+        const size_t smem = (size_t)ctx->nb_umax * 32 * sizeof(float2);
+        const int* lp_ = ctx->linterm ? ctx->d_lin_ptr : nullptr;
+        const int has_k = F == 8 ? 1 : (ctx->f32.ng != nullptr);
+        if (F == 8) {
+            set_smem(k_near_blk<8>, smem);
+            k_near_blk<8><<<ctx->nb_count, kNbWarps * 32, smem, s>>>(
+                fb.part, fb.xT, ctx->d_nb_rows, ctx->d_nb_ustart, ctx->d_nb_ucols, ctx->d_nb_ent, ctx->d_row_ptr,
+                ctx->d_perm, lp_, ctx->d_lin_cols, ctx->f32.la, ctx->f32.lp, yb, nc, has_k, N, nunk, P, B);
+        } else {
+            set_smem(k_near_blk<4>, smem);
+            k_near_blk<4><<<ctx->nb_count, kNbWarps * 32, smem, s>>>(
+                fb.part, fb.xT, ctx->d_nb_rows, ctx->d_nb_ustart, ctx->d_nb_ucols, ctx->d_nb_ent, ctx->d_row_ptr,
+                ctx->d_perm, lp_, ctx->d_lin_cols, ctx->f32.la, ctx->f32.lp, yb, nc, has_k, N, nunk, P, B);
+        }
+    } else
     k_final<<<(N + kFinalRows - 1) / kFinalRows, kThreads, 0, s>>>(fb.part, fb.xT, ctx->d_row_ptr, ctx->d_cols,
                                                                    ctx->f32.na, ctx->f32.np,
                                                                    F == 8 ? ctx->f32.nk : ctx->f32.ng, ctx->d_perm,
@@ -1114,6 +1237,77 @@ static void ensure_plane_table(aimx_ctx* ctx) {
     ctx->max_plane_bases = mpb;
 }
 
+// Row blocks of the near CSR for k_near_blk (built once per context, on the host from the
+// internal-order pattern): consecutive rows are added to a block while it has fewer than
+// kNbRows rows and the union of their columns stays within kNbUmax (a single row may exceed
+// it).  If some block's union would not fit in shared memory the blocked kernel is not used.
+static void ensure_near_blocks(aimx_ctx* ctx) {
+    if (ctx->nb_count > 0 || ctx->nb_umax < 0) return;
+    const int N = ctx->N;
+    const std::vector<int>& rp = ctx->row_ptr;
+    const std::vector<int>& cols = ctx->cols;
+    std::vector<int> stamp(N, -1), pos(N, 0), rows{0}, ust{0}, ucols, li(ctx->nnz), tmp;
+    int blk = 0, umax = 0;
+    for (int i = 0; i < N;) {
+        int j = i, u = 0;
+        while (j < N && j - i < kNbRows) {
+            int add = 0;
+            for (int e = rp[j]; e < rp[j + 1]; ++e) add += stamp[cols[e]] != blk;
+            if (j > i && u + add > kNbUmax) break;
+            for (int e = rp[j]; e < rp[j + 1]; ++e) stamp[cols[e]] = blk;
+            u += add;
+            ++j;
+        }
+        tmp.clear();
+        for (int e = rp[i]; e < rp[j]; ++e) {
+            const int c = cols[e];
+            if (stamp[c] == blk) {
+                stamp[c] = -2 - blk;   // collected (never equal to a later block id)
+                tmp.push_back(c);
+            }
+        }
+        std::sort(tmp.begin(), tmp.end());
+        for (size_t k = 0; k < tmp.size(); ++k) pos[tmp[k]] = (int)k;
+        for (int e = rp[i]; e < rp[j]; ++e) li[e] = pos[cols[e]];
+        ucols.insert(ucols.end(), tmp.begin(), tmp.end());
+        rows.push_back(j);
+        ust.push_back((int)ucols.size());
+        umax = std::max(umax, (int)tmp.size());
+        ++blk;
+        i = j;
+    }
+    // shared memory: the staged union plus 24 KB of partial-sum tiles and entry buffers
+    if ((size_t)umax * 32 * sizeof(float2) + 24 * 1024 > 200 * 1024) {
+        ctx->nb_umax = -1;
+        return;
+    }
+    ctx->d_nb_rows = (int*)dev_alloc(ctx, sizeof(int) * rows.size());
+    ctx->d_nb_ustart = (int*)dev_alloc(ctx, sizeof(int) * ust.size());
+    ctx->d_nb_ucols = (int*)dev_alloc(ctx, sizeof(int) * std::max<size_t>(1, ucols.size()));
+    ctx->d_nb_ent = (float4*)dev_alloc(ctx, sizeof(float4) * std::max<int64_t>(1, ctx->nnz));
+    AIMX_CUDA_TRY(cudaMemcpy(ctx->d_nb_rows, rows.data(), sizeof(int) * rows.size(), cudaMemcpyHostToDevice));
+    AIMX_CUDA_TRY(cudaMemcpy(ctx->d_nb_ustart, ust.data(), sizeof(int) * ust.size(), cudaMemcpyHostToDevice));
+    AIMX_CUDA_TRY(cudaMemcpy(ctx->d_nb_ucols, ucols.data(), sizeof(int) * ucols.size(), cudaMemcpyHostToDevice));
+    if (ctx->nnz > 0) {
+        int* d_li = (int*)dev_alloc(ctx, sizeof(int) * ctx->nnz);
+        try {
+            AIMX_CUDA_TRY(cudaMemcpy(d_li, li.data(), sizeof(int) * ctx->nnz, cudaMemcpyHostToDevice));
+            const float* vk = ctx->F == 8 ? ctx->f32.nk : ctx->f32.ng;
+            k_pack_near_ent<<<(unsigned)((ctx->nnz + 255) / 256), 256>>>(d_li, ctx->f32.na, ctx->f32.np, vk,
+                                                                        ctx->nnz, ctx->d_nb_ent);
+            AIMX_CUDA_TRY(cudaGetLastError());
+            AIMX_CUDA_TRY(cudaDeviceSynchronize());
+        } catch (...) {
+            dev_free(ctx, d_li);
+            throw;
+        }
+        dev_free(ctx, d_li);
+        ctx->device_bytes -= (int64_t)sizeof(int) * ctx->nnz;
+    }
+    ctx->nb_umax = umax;
+    ctx->nb_count = blk;
+}
+
 void matvec_fused(aimx_ctx* ctx, double freq, int nrhs, const float* x, float* y, cudaStream_t s) {
     {
         StageScope sc(ctx, ST_KERNELGEN, s);
@@ -1121,7 +1315,7 @@ void matvec_fused(aimx_ctx* ctx, double freq, int nrhs, const float* x, float* y
     }
     ensure_aim_near(ctx, freq, s);
     ensure_plane_table(ctx);
-    ensure_const_twiddles();
+    ensure_near_blocks(ctx);
     const NearC nc = near_c(ctx, freq);
     const int64_t NG = (int64_t)ctx->n[0] * ctx->n[1] * ctx->n[2];
     const int F = ctx->F;
@@ -1153,8 +1347,9 @@ size_t fused_scratch_bytes(const aimx_ctx* ctx, int B) {
 // The plane-fused FP32 product for all B right-hand sides at once, with the
 // work buffers carved from caller-provided device memory `scratch` of at
 // least fused_scratch_bytes(ctx, B) bytes.  Performs no allocation: the
-// kernel spectra buffers, the plane table and the constant twiddles must
-// already exist (any earlier FP32 aimx_matvec on this context creates them).
+// kernel spectra buffers, the plane table, the near row blocks and the device
+// twiddle table must already exist (any earlier FP32 aimx_matvec on this
+// context creates them).
 void matvec_fused_into(aimx_ctx* ctx, double freq, int B, const float* x, float* y, cudaStream_t s,
                        unsigned char* scratch) {
     ensure_spectra<float>(ctx, freq, s);

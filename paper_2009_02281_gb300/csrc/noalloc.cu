@@ -61,8 +61,18 @@ extern "C" int aimx_matvec_noalloc(aimx_ctx* ctx, double freq, int nrhs, const v
         ctx->last_error = "aimx_matvec_noalloc: null buffer, nrhs <= 0 or freq <= 0";
         return AIMX_E_ARG;
     }
-    if (!fused_supported(ctx)) {
-        ctx->last_error = "aimx_matvec_noalloc: the grid does not take the plane-fused FP32 path";
+    if (!use_fused(ctx)) {
+        ctx->last_error =
+            "aimx_matvec_noalloc: FP32 products of this context do not take the plane-fused path "
+            "(grid shape, aimx_set_path or the schedule)";
+        return AIMX_E_STATE;
+    }
+    // The conventional-AIM near fill of a new frequency copies a host table and waits for it,
+    // which would block the caller; that mode is accepted only at the frequency already filled.
+    if (ctx->aim && ctx->aim_freq != freq) {
+        ctx->last_error =
+            "aimx_matvec_noalloc: conventional-AIM mode needs the near entries of this frequency; "
+            "call aimx_matvec at it first";
         return AIMX_E_STATE;
     }
     // Everything that would otherwise be allocated lazily must already exist.

@@ -2,19 +2,15 @@
 //
 // Decimation in time on a register array with compile-time indices: radix 4
 // for lengths that are powers of four (16, 64), radix 2 otherwise.  The digit
-// reversal is a renaming, twiddles W_L^k come from a constant-memory table read
-// at warp-uniform addresses, and the trivial twiddles (1, -1, -i) are applied
-// without multiplications.  Natural order in and out; INV gives the
+// reversal is a renaming, twiddles W_L^k are compile-time constants (instruction
+// immediates), and the trivial twiddles (1, -1, -i) are applied without
+// multiplications.  Natural order in and out; INV gives the
 // unnormalised inverse.
 #pragma once
 
 #include "cplx.cuh"
 
 namespace aimx {
-
-// e^{-2 pi i k / 4096}, k < 4096; include this header in one translation unit
-// only, which fills the table once per device before the first launch
-static __constant__ float2 c_tw4096[4096];
 
 __host__ __device__ constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v / 2); }
 __host__ __device__ constexpr int brevc(int v, int bits) {
@@ -23,12 +19,63 @@ __host__ __device__ constexpr int brevc(int v, int bits) {
     return r;
 }
 
-// W_M^k (forward) or its conjugate (inverse) for a compile-time or uniform k
+// Twiddles as compile-time constants.  Every line length here is a power of two <= 128, so
+// all twiddles are W_128^k = e^{-2 pi i k / 128}.  The angle is reduced exactly with integers
+// to [0, pi/4] (quadrant, then the complementary angle), where Taylor series of sin and cos
+// summed in double precision are accurate to rounding; the table is then rounded to FP32.
+// Indices are compile-time constants after unrolling, so the values become instruction
+// immediates instead of constant-memory loads.
+constexpr int kTwTab = 128;
+__host__ __device__ constexpr double taylor_sin(double x) {
+    double x2 = x * x, term = x, sum = x;
+    for (int n = 1; n < 12; ++n) {
+        term *= -x2 / ((2.0 * n) * (2.0 * n + 1.0));
+        sum += term;
+    }
+    return sum;
+}
+__host__ __device__ constexpr double taylor_cos(double x) {
+    double x2 = x * x, term = 1.0, sum = 1.0;
+    for (int n = 1; n < 12; ++n) {
+        term *= -x2 / ((2.0 * n - 1.0) * (2.0 * n));
+        sum += term;
+    }
+    return sum;
+}
+struct TwTable {
+    float re[kTwTab];
+    float im[kTwTab];
+};
+__host__ __device__ constexpr TwTable make_tw_table() {
+    TwTable t{};
+    constexpr double two_pi = 6.283185307179586476925286766559;
+    for (int k = 0; k < kTwTab; ++k) {
+        const int q = k / (kTwTab / 4), r = k % (kTwTab / 4);   // angle = q pi/2 + 2 pi r / 128
+        double c0 = 0.0, s0 = 0.0;
+        if (r <= kTwTab / 8) {
+            const double a = two_pi * r / kTwTab;
+            c0 = taylor_cos(a);
+            s0 = taylor_sin(a);
+        } else {                                                // pi/2 - angle, also in [0, pi/4]
+            const double a = two_pi * (kTwTab / 4 - r) / kTwTab;
+            c0 = taylor_sin(a);
+            s0 = taylor_cos(a);
+        }
+        const double c = q == 0 ? c0 : q == 1 ? -s0 : q == 2 ? -c0 : s0;
+        const double sn = q == 0 ? s0 : q == 1 ? c0 : q == 2 ? -s0 : -c0;
+        t.re[k] = (float)c;
+        t.im[k] = (float)(-sn);
+    }
+    return t;
+}
+
+// W_M^k (forward) or its conjugate (inverse) for k and M compile-time constants after
+// unrolling, M a power of two dividing 128
 template <bool INV>
 __device__ __forceinline__ float2 twc(int k, int M) {
-    float2 w = c_tw4096[(k % M) * (4096 / M)];
-    if (INV) w.y = -w.y;
-    return w;
+    constexpr TwTable tab = make_tw_table();
+    const int i = (k % M) * (kTwTab / M);
+    return make_float2(tab.re[i], INV ? -tab.im[i] : tab.im[i]);
 }
 
 __host__ __device__ constexpr bool pow4c(int v) { return v == 1 || (v % 4 == 0 && pow4c(v / 4)); }

@@ -31,7 +31,7 @@ def _relerr(a, b):
 
 
 @pytest.mark.parametrize("form", ["efie", "pmchwt"])
-@pytest.mark.parametrize("nrhs", [1, 5, 9])
+@pytest.mark.parametrize("nrhs", [1, 5, 9, 37])
 def test_fused_matches_oracle_and_generic(torch_cuda, form, nrhs):
     torch = torch_cuda
     from synth import icosphere, random_complex

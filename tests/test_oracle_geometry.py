@@ -148,7 +148,7 @@ def _exact_poly_moment(v0, v1, v2, A, field, alpha, r0, p_free, sgn, c, div):
 
 
 def test_projection_moment_matching(small_sphere):
-    """sum_u Lambda_f[u,n] (r_u - r0)^alpha = int f (r - r0)^alpha dS for alpha_a <= n."""
+    """sum_u Lambda_f[u,n] (r_u - r0)^alpha = int f (r - r0)^alpha dS for alpha_a <= n (moment matching: Sec. I and the opening of Sec. IV)."""
     r = small_sphere["rwg"]
     g = small_sphere["grid"]
     lam = small_sphere["lam"]
