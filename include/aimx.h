@@ -319,6 +319,42 @@ int aimx_set_linear_term(aimx_ctx* ctx, int enable);
  * Off by default. */
 int aimx_set_conventional_aim(aimx_ctx* ctx, int enable);
 
+/* ------------------------------------------------------------------ charge-form scalar potential
+ * The discretisation of the augmented EFIE that the paper uses for its on-chip
+ * examples (Sec. V-C to V-E), kept on the EFIE's RWG unknowns.  With enable = 1
+ * the scalar-potential operator of this EFIE context is written through the
+ * triangle charges q = D x (D_tn = +l_n on T+, -l_n on T-):
+ *     L^Phi = D^T Pt D,   Pt = (Pt_s,NR - Pt_s,P) + Lp^T H(k) Lp,
+ * Pt_ij = (A_i A_j)^-1 int_{T_i} int_{T_j} G the pulse-pulse potential, Lp the
+ * pulse projection weights (moment matching of a unit charge on each
+ * triangle's own stencil), triangle anchors and near pairs as for the bases
+ * (same anchor formula on the centroids, same Chebyshev radius), the static
+ * near values Pt_s,NR from the closed-form inner potential of 1/(4 pi R) and
+ * the 5 x 5 outer rule, and Pt_s,P their precorrection with the static grid
+ * kernel.  The product replaces the RWG terms N^Phi x + P_rho^T H P_rho x;
+ * the vector potential is unchanged.  A divergence-free current then gets
+ * exactly zero scalar potential (no residue of the grid approximation).
+ *   - The first enable builds the triangle data (host integer steps, FP64
+ *     device kernels) and synchronises the device.  Later toggles are cheap.
+ *   - Applies to aimx_matvec (both precisions, generic and plane-fused paths),
+ *     aimx_solve, aimx_sweep, ports and batches.  Preconditioners keep the RWG
+ *     static self terms.  aimx_matvec_noalloc returns AIMX_E_STATE while on.
+ *   - AIMX_E_STATE for non-EFIE contexts, or with the linear term or the
+ *     conventional-AIM mode on; AIMX_E_GRID if a triangle stencil leaves the
+ *     grid.  enable = 0 returns to the RWG form.
+ * Off by default. */
+int aimx_set_charge_form(aimx_ctx* ctx, int enable);
+
+/* Copy the charge-form setup to host arrays in caller triangle numbering (any
+ * output may be NULL): nt = triangles; tnnz = triangle near pairs; tanc int32 [nt][3]
+ * anchors; rows, cols int32 [tnnz] the pairs (internal order of rows, so
+ * compare as sets); npt double [tnnz] = Pt_s,NR - Pt_s,P on them (same
+ * order); lp double [nt][(order+1)^3] pulse weights (stencil node u = ux +
+ * (order+1) (uy + (order+1) uz)).  AIMX_E_STATE before the first enable.
+ * Synchronous. */
+int aimx_export_charge(aimx_ctx* ctx, int32_t* nt, int64_t* tnnz, int32_t* tanc, int32_t* rows, int32_t* cols,
+                       double* npt, double* lp);
+
 /* The conventional-AIM near entries at freq as complex float64 pairs z [nnz][2],
  * in the near pattern of aimx_export_setup (caller numbering, columns
  * ascending).  AIMX_E_STATE unless the mode is on.  Synchronous. */

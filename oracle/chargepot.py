@@ -76,28 +76,38 @@ def static_pulse(rwg, rows, cols, q=Q_NEAR):
     return np.einsum("q,bq->b", w, I1) / (FOUR_PI * area[cols])
 
 
-def pulse_precorrection(Lp, anc_t, grid, rows, cols, radius):
-    """Pt_s,P(i, j) = sum_{u,v} Lp[u, i] H_s[s_i + u - s_j - v] Lp[v, j] on the given pairs."""
+def pulse_precorrection(Lp, anc_t, grid, rows, cols, radius, chunk=4096):
+    """Pt_s,P(i, j) = sum_{u,v} Lp[u, i] H_s[s_i + u - s_j - v] Lp[v, j] on the given pairs
+    (evaluated ``chunk`` pairs at a time to bound memory)."""
     o = grid["order"]
     off = gridmod.stencil_offsets(o)
     span = radius + o
     Hs, _ = greens.static_offset_kernels(grid["h"], span)
-    d = (anc_t[rows] - anc_t[cols])[:, None, None, :] + (off[:, None, :] - off[None, :, :])[None] + span
-    hs = Hs[(d[..., 2], d[..., 1], d[..., 0])]                                         # [B,U,V]
-    return np.einsum("bu,buv,bv->b", Lp[rows], hs, Lp[cols])
+    out = np.empty(len(rows))
+    for a in range(0, len(rows), chunk):
+        r, c = rows[a:a + chunk], cols[a:a + chunk]
+        d = (anc_t[r] - anc_t[c])[:, None, None, :] + (off[:, None, :] - off[None, :, :])[None] + span
+        hs = Hs[(d[..., 2], d[..., 1], d[..., 0])]                                     # [B,U,V]
+        out[a:a + chunk] = np.einsum("bu,buv,bv->b", Lp[r], hs, Lp[c])
+    return out
 
 
-def setup_charge(prob, radius=None):
+def setup_charge(prob, radius=None, tri_rows=None):
     """Triangle anchors, pulse weights, triangle near pairs and the static near values
-    N_Pt = Pt_s,NR - Pt_s,P on them, on the grid of an operator problem."""
+    N_Pt = Pt_s,NR - Pt_s,P on them, on the grid of an operator problem.  With ``tri_rows``, the
+    near values are computed only on the rows of those triangles (NaN elsewhere): enough for
+    products restricted to the output rows whose triangles they are."""
     rwg, g = prob["rwg"], prob["grid"]
     radius = prob["radius"] if radius is None else radius
     anc_t = gridmod.anchors(g, centroids(rwg))
     Lp = pulse_weights(rwg, g, anc_t)
     row_ptr, cols = gridmod.near_pairs(anc_t, radius)
     rows = np.repeat(np.arange(len(anc_t)), np.diff(row_ptr))
-    Ps = static_pulse(rwg, rows, cols)
-    PP = pulse_precorrection(Lp, anc_t, g, rows, cols, radius)
+    sel = np.arange(len(rows)) if tri_rows is None else np.flatnonzero(np.isin(rows, tri_rows))
+    Ps = np.full(len(rows), np.nan)
+    PP = np.full(len(rows), np.nan)
+    Ps[sel] = static_pulse(rwg, rows[sel], cols[sel])
+    PP[sel] = pulse_precorrection(Lp, anc_t, g, rows[sel], cols[sel], radius)
     return dict(anc_t=anc_t, Lp=Lp, rows=rows, cols=cols, Ps=Ps, PP=PP, NPt=Ps - PP, D=incidence(rwg),
                 radius=radius)
 

@@ -99,6 +99,8 @@ _SIGS = [
     ("aimx_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_char_p, ctypes.c_void_p,
                                      ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     ("aimx_export_aim_near", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p]),
+    ("aimx_set_charge_form", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("aimx_export_charge", ctypes.c_int, [ctypes.c_void_p] + [ctypes.c_void_p] * 7),
     ("aimx_matvec_path", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("aimx_profile", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("aimx_profile_read", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
@@ -448,6 +450,27 @@ class Context:
     def set_conventional_aim(self, enable=True):
         """Conventional-AIM comparison mode (Sec. II-B): near entries refilled at every new frequency."""
         self._check(self._lib.aimx_set_conventional_aim(self._ctx, 1 if enable else 0))
+
+    def set_charge_form(self, enable=True):
+        """Charge-form scalar potential L^Phi = D^T Pt D (EFIE); builds the triangle data on the first enable."""
+        self._check(self._lib.aimx_set_charge_form(self._ctx, 1 if enable else 0))
+
+    def export_charge(self):
+        """Charge-form setup in caller triangle numbering: anchors, near pairs, N_Pt values, pulse weights."""
+        n = ctypes.c_int64(0)
+        ntc = ctypes.c_int32(0)
+        self._check(self._lib.aimx_export_charge(self._ctx, ctypes.byref(ntc), ctypes.byref(n), None, None, None,
+                                                 None, None))
+        nt = int(ntc.value)
+        U = (self.info["order"] + 1) ** 3
+        tanc = np.zeros((nt, 3), dtype=np.int32)
+        rows = np.zeros(n.value, dtype=np.int32)
+        cols = np.zeros(n.value, dtype=np.int32)
+        npt = np.zeros(n.value)
+        lp = np.zeros((nt, U))
+        self._check(self._lib.aimx_export_charge(self._ctx, None, None, _ptr(tanc), _ptr(rows), _ptr(cols),
+                                                 _ptr(npt), _ptr(lp)))
+        return dict(tanc=tanc, rows=rows, cols=cols, npt=npt, lp=lp)
 
     def export_aim_near(self, freq):
         """Conventional-AIM near entries at freq, complex [nnz], in export_setup's near order."""

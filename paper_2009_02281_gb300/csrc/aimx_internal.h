@@ -65,6 +65,11 @@ struct PrecData {
     T* la = nullptr;       // linear-term N^A_lin on the overlap pattern [nlin] (when enabled)
     T* lp = nullptr;       // linear-term N^Phi_lin on the overlap pattern [nlin]
     T* zn = nullptr;       // conventional-AIM near entries j w mu (N^A(k) - k^-2 N^Phi(k)) [nnz] complex
+    T* plw = nullptr;      // charge form: pulse weights [nt][U] (internal triangle order)
+    T* npt = nullptr;      // charge form: static pulse near values Pt_s,NR - Pt_s,P [tnnz]
+    T* tl = nullptr;       // charge form: incidence [nt][3] signed edge lengths (0 = no edge)
+    T* cwork = nullptr;    // charge form, generic path: q and phi [2][chunk][nt] complex
+    size_t cwork_elems = 0;
     T* spec = nullptr;     // octant spectra [nspec][Oz][Oy][Ox] complex (2 T each)
     double spec_freq = -1.0;
     // work buffers of the generic FFT path
@@ -241,6 +246,28 @@ struct aimx_ctx {
     float* d_S = nullptr;          // [B][F][Nz][4][Ny][Nx] complex (xy spectra, parity blocks)
     float* d_part = nullptr;       // [B][F/4][P][N] complex (per-plane interpolation partials)
     int fused_cap = 0;             // RHS capacity of the buffers above
+    // charge-form scalar potential (EFIE): L^Phi = D^T Pt D with the pulse matrix Pt in AIMx form
+    int charge = 0;                // 1 = products use the charge form (aimx_set_charge_form)
+    int charge_built = 0;
+    int64_t tnnz = 0;              // triangle near pairs
+    std::vector<int> tperm;        // internal triangle -> caller triangle (sorted by anchor z, y, x)
+    std::vector<int> tanc;         // [nt][3] triangle anchors, internal order
+    std::vector<int> trow_ptr, tcols;       // triangle near CSR, internal order, columns ascending
+    std::vector<int> tplane_lo, tplane_hi;  // per z plane: internal triangles touching it
+    int max_plane_tris = 0;
+    int* d_tanc = nullptr;         // [nt][3]
+    int* d_trow_ptr = nullptr;     // [nt+1]
+    int* d_tcols = nullptr;        // [tnnz]
+    int* d_tnode_ptr = nullptr;    // [Nz*Ny*Nx + 1] node-major triangle lists
+    int* d_tnode_w = nullptr;      // [nt*U] entry t*U+u
+    int* d_tinc = nullptr;         // [nt][3] internal basis id of each edge (-1 = boundary edge)
+    int* d_btri_t = nullptr;       // [N][2] internal triangle ids of T+ / T- (internal basis order)
+    int* d_tplane = nullptr;       // [2][Nz] tplane_lo then tplane_hi
+    float* d_lp_soa = nullptr;     // FP32 pulse weights field-major [U][nt]
+    float* d_qT = nullptr;         // fused path: triangle charges [nt][B] complex
+    float* d_phiT = nullptr;       // fused path: triangle potentials [nt][B] complex
+    float* d_tpart = nullptr;      // fused path: per-plane triangle partials [B][P][nt] complex
+    int charge_cap = 0;            // RHS capacity of the three buffers above
     // near rows grouped into blocks for the final kernel of the plane-fused path: each block
     // is <= 32 consecutive internal rows whose near columns, taken together, are staged once
     int nb_count = 0;              // row blocks (0 = not built, or a row too wide: CSR kernel)
@@ -283,6 +310,9 @@ struct StaticData {
     std::vector<double> na, np, nk;  // [nnz] near matrices N^A, N^Phi, N^K
     std::vector<double> diag;  // [N][3] static self terms
 };
+// collapsed Gauss-Legendre product rule on a triangle, q x q points: [Q][4] = (l1, l2, l3, w),
+// weights normalised to sum to one; exact to total degree 2q - 2
+void triangle_rule(int q, std::vector<double>& out);
 // formulations with one unknown block (EFIE, CFIE) vs two (PMCHWT)
 inline bool two_blocks(int form) { return form == AIMX_PMCHWT; }
 
@@ -342,10 +372,28 @@ struct StageScope {
 bool fused_supported(const aimx_ctx* ctx);
 // the plane-fused kernels with register-resident lines apply to this grid
 bool fused_reg_supported(const aimx_ctx* ctx);
-// FP32 products of this context take the plane-fused path (path setting and schedule)
+// FP32 products of this context take the plane-fused path (path setting and schedule); the
+// charge form is carried by the register-line kernels only
 inline bool use_fused(const aimx_ctx* ctx) {
+    if (ctx->charge && (ctx->sched_variant == 1 || !fused_reg_supported(ctx))) return false;
     return ctx->path == 0 && ctx->sched_variant != 2 && fused_supported(ctx);
 }
+
+// charge.cu: the charge-form scalar potential (setup on the first enable; product steps)
+void build_charge(aimx_ctx* ctx);
+// generic path: q = D x for nb right-hand sides ([nb][nt], caller-order x), and the rho field
+// of the padded grid (field rho_field of Fg per RHS) projected from q with the pulse weights
+template <class T>
+void charge_project(aimx_ctx* ctx, const typename Cplx<T>::type* x, int nb, typename Cplx<T>::type* q,
+                    typename Cplx<T>::type* grid, int Fg, int rho_field, cudaStream_t s);
+// generic path: phi = Lp^T (convolved rho field) + cP N_Pt q per triangle ([nb][nt])
+template <class T>
+void charge_potential(aimx_ctx* ctx, const typename Cplx<T>::type* grid, int Fg, int rho_field, int nb,
+                      const typename Cplx<T>::type* q, typename Cplx<T>::type* phi, double2 cP, cudaStream_t s);
+// plane-fused path: qT = D x from xT ([nt][B]); phiT = sum of plane partials + cP N_Pt qT
+void charge_fused_q(aimx_ctx* ctx, const float2* xT, int B, cudaStream_t s);
+void charge_fused_phi(aimx_ctx* ctx, int B, float2 cP, cudaStream_t s);
+void ensure_charge_buffers(aimx_ctx* ctx, int B);
 void matvec_fused(aimx_ctx* ctx, double freq, int nrhs, const float* x, float* y, cudaStream_t s);
 
 // precond.cu

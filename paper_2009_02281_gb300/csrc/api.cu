@@ -42,7 +42,11 @@ static void free_all(aimx_ctx* c) {
                     c->pc.d_ptr,  c->pc.d_idx,  c->pc.d_work,  c->pc.d_inv, c->d_wsoa,   c->f32.ng,
                     c->f64.ng,    c->d_gdiag,   c->d_lin_ptr,  c->d_lin_cols, c->f64.la, c->f64.lp,
                     c->f32.la,    c->f32.lp,    c->f64.zn,     c->f32.zn,     c->d_aim_row_of, c->d_aim_htab,
-                    c->d_nb_rows, c->d_nb_ustart, c->d_nb_ucols, c->d_nb_ent};
+                    c->d_nb_rows, c->d_nb_ustart, c->d_nb_ucols, c->d_nb_ent,
+                    c->d_tanc, c->d_trow_ptr, c->d_tcols, c->d_tnode_ptr, c->d_tnode_w, c->d_tinc,
+                    c->d_btri_t, c->d_tplane, c->d_lp_soa, c->d_qT, c->d_phiT, c->d_tpart,
+                    c->f64.plw, c->f32.plw, c->f64.npt, c->f32.npt, c->f64.tl, c->f32.tl,
+                    c->f64.cwork, c->f32.cwork};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& r : c->prof.recs) {
@@ -211,6 +215,8 @@ int aimx_set_path(aimx_ctx* ctx, int path) {
 
 int aimx_set_linear_term(aimx_ctx* ctx, int enable) {
     if (!ctx || enable < 0 || enable > 1) return AIMX_E_ARG;
+    if (enable && ctx->charge)
+        return fail(ctx, Error{AIMX_E_STATE, "the linear term is not combined with the charge form"});
     try {
         if (enable) build_linterm(ctx);
         if (ctx->linterm != enable) ctx->config_gen++;
@@ -223,12 +229,66 @@ int aimx_set_linear_term(aimx_ctx* ctx, int enable) {
 
 int aimx_set_conventional_aim(aimx_ctx* ctx, int enable) {
     if (!ctx || enable < 0 || enable > 1) return AIMX_E_ARG;
+    if (enable && ctx->charge)
+        return fail(ctx, Error{AIMX_E_STATE, "the conventional-AIM mode is not combined with the charge form"});
     try {
         if (enable) aim_enable(ctx);
         if (ctx->aim != enable) ctx->config_gen++;
         ctx->aim = enable;
     } catch (const Error& e) {
         return fail(ctx, e);
+    }
+    return AIMX_OK;
+}
+
+int aimx_set_charge_form(aimx_ctx* ctx, int enable) {
+    if (!ctx || enable < 0 || enable > 1) return AIMX_E_ARG;
+    if (enable && ctx->form != AIMX_EFIE)
+        return fail(ctx, Error{AIMX_E_STATE, "the charge form is available for the EFIE"});
+    if (enable && (ctx->linterm || ctx->aim))
+        return fail(ctx, Error{AIMX_E_STATE,
+                               "the charge form is not combined with the linear term or the conventional-AIM mode"});
+    try {
+        if (enable) build_charge(ctx);
+        if (ctx->charge != enable) ctx->config_gen++;
+        ctx->charge = enable;
+    } catch (const Error& e) {
+        return fail(ctx, e);
+    }
+    return AIMX_OK;
+}
+
+int aimx_export_charge(aimx_ctx* ctx, int32_t* nt_out, int64_t* tnnz, int32_t* tanc, int32_t* rows, int32_t* cols,
+                       double* npt, double* lp) {
+    if (!ctx) return AIMX_E_ARG;
+    if (!ctx->charge_built) {
+        ctx->last_error = "the charge form has not been enabled on this context";
+        return AIMX_E_STATE;
+    }
+    try {
+        const int nt = ctx->nt, U = ctx->U;
+        const int64_t nn = ctx->tnnz;
+        if (nt_out) *nt_out = nt;
+        if (tnnz) *tnnz = nn;
+        if (tanc)
+            for (int i = 0; i < nt; ++i)
+                for (int a = 0; a < 3; ++a) tanc[3 * (size_t)ctx->tperm[i] + a] = ctx->tanc[3 * (size_t)i + a];
+        if (rows || cols)
+            for (int i = 0; i < nt; ++i)
+                for (int e = ctx->trow_ptr[i]; e < ctx->trow_ptr[i + 1]; ++e) {
+                    if (rows) rows[e] = ctx->tperm[i];
+                    if (cols) cols[e] = ctx->tperm[ctx->tcols[e]];
+                }
+        if (npt && nn) AIMX_CUDA_TRY(cudaMemcpy(npt, ctx->f64.npt, nn * sizeof(double), cudaMemcpyDeviceToHost));
+        if (lp) {
+            std::vector<double> v((size_t)nt * U);
+            AIMX_CUDA_TRY(cudaMemcpy(v.data(), ctx->f64.plw, v.size() * sizeof(double), cudaMemcpyDeviceToHost));
+            for (int i = 0; i < nt; ++i)
+                std::memcpy(lp + (size_t)ctx->tperm[i] * U, v.data() + (size_t)i * U, sizeof(double) * U);
+        }
+    } catch (const Error& e) {
+        ctx->last_error = e.msg;
+        return e.code;
     }
     return AIMX_OK;
 }

@@ -80,10 +80,14 @@ __global__ void k_transpose_x(const float2* __restrict__ x, const int* __restric
 // right-hand sides; lane = right-hand side, so the x reads ([nunk][B] layout)
 // are contiguous and each node's (basis, weight) list is read once per warp as
 // broadcasts; a shared-memory transpose writes the projected grid node-fastest.
+// Charge form (tnode_ptr given, EFIE): the rho field is gathered from the triangle charges qT
+// with the pulse weights instead of from the RWG divergence weights.
 template <int F>
 __global__ void __launch_bounds__(256) k_gather_tile(const float4* __restrict__ w, const int* __restrict__ node_ptr,
                                                      const int* __restrict__ node_w, const float2* __restrict__ xT,
-                                                     float2* G, int B, int N, int U, int64_t NG) {
+                                                     float2* G, int B, int N, int U, int64_t NG,
+                                                     const int* __restrict__ tnode_ptr, const int* __restrict__ tnode_w,
+                                                     const float* __restrict__ lp, const float2* __restrict__ qT) {
     constexpr int TG = 16;
     __shared__ float2 tile[F][32][TG + 1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -106,13 +110,20 @@ __global__ void __launch_bounds__(256) k_gather_tile(const float4* __restrict__ 
                 rfma(acc[0], wv.x, xj);
                 rfma(acc[1], wv.y, xj);
                 rfma(acc[2], wv.z, xj);
-                rfma(acc[3], wv.w, xj);
+                if (F == 8 || !tnode_ptr) rfma(acc[3], wv.w, xj);
                 if (F == 8) {
                     const float2 xm = __ldg(xT + (int64_t)(N + i) * B + b);
                     rfma(acc[4], wv.x, xm);
                     rfma(acc[5], wv.y, xm);
                     rfma(acc[6], wv.z, xm);
                     rfma(acc[7], wv.w, xm);
+                }
+            }
+            if (F == 4 && tnode_ptr) {
+                const int t1 = tnode_ptr[g + 1];
+                for (int e = tnode_ptr[g]; e < t1; ++e) {
+                    const int wt = tnode_w[e];
+                    rfma(acc[3], __ldg(lp + wt), __ldg(qT + (int64_t)(wt / U) * B + b));
                 }
             }
         }
@@ -331,6 +342,7 @@ __global__ void __launch_bounds__(kThreads) k_xy_inv(const float2* __restrict__ 
 struct NearC {
     float2 c[6];
     float2 lin[4];   // linear-term coefficients (J rows: A, Phi; M rows: A, Phi)
+    float2 cphi;     // charge form: coefficient of the triangle near part (c[1] is then 0)
 };
 
 __global__ void __launch_bounds__(kThreads) k_final(const float2* __restrict__ part, const float2* __restrict__ xT,
@@ -340,7 +352,8 @@ __global__ void __launch_bounds__(kThreads) k_final(const float2* __restrict__ p
                                                     const int* __restrict__ lin_ptr, const int* __restrict__ lin_cols,
                                                     const float* __restrict__ la, const float* __restrict__ lp,
                                                     const float2* __restrict__ zn, float2* y, NearC nc, int F, int N,
-                                                    int nunk, int P, int B) {
+                                                    int nunk, int P, int B, const float2* __restrict__ phiT,
+                                                    const int* __restrict__ btri_t, const double* __restrict__ blen) {
     __shared__ float2 accE[kFinalRows][kFinalB];
     __shared__ float2 accH[kFinalRows][kFinalB];
     const int G = F / 4;
@@ -435,6 +448,9 @@ __global__ void __launch_bounds__(kThreads) k_final(const float2* __restrict__ p
                 if (bl < nbc) {
                     float2 e = accE[r][bl] + nc.c[0] * aJ[h] + nc.c[1] * pJ[h];
                     if (F == 4 && nk) e = e + nc.c[2] * kJ[h];
+                    if (F == 4 && phiT)
+                        e = e + (float)blen[i] * (__ldg(phiT + (int64_t)btri_t[2 * i] * B + bc + bl) -
+                                                  __ldg(phiT + (int64_t)btri_t[2 * i + 1] * B + bc + bl));
                     if (F == 8) {
                         e = e + nc.c[2] * kM[h];
                         float2 hh = accH[r][bl] + nc.c[3] * kJ[h] + nc.c[4] * aM[h] + nc.c[5] * pM[h];
@@ -465,7 +481,8 @@ __global__ void __launch_bounds__(kNbWarps * 32) k_near_blk(
     const int* __restrict__ nb_ustart, const int* __restrict__ nb_ucols, const float4* __restrict__ ent,
     const int* __restrict__ row_ptr, const int* __restrict__ perm, const int* __restrict__ lin_ptr,
     const int* __restrict__ lin_cols, const float* __restrict__ la, const float* __restrict__ lp, float2* y,
-    NearC nc, int has_k, int N, int nunk, int P, int B) {
+    NearC nc, int has_k, int N, int nunk, int P, int B, const float2* __restrict__ phiT,
+    const int* __restrict__ btri_t, const double* __restrict__ blen) {
     extern __shared__ float2 xs[];                         // [union][32]
     __shared__ float2 accE[kNbRows][32];
     __shared__ float2 accH[F == 8 ? kNbRows : 1][32];
@@ -541,6 +558,12 @@ __global__ void __launch_bounds__(kNbWarps * 32) k_near_blk(
             if (F == 8) {
                 e = e + nc.c[2] * acc[k][5];
                 h = accH[r][lane] + nc.c[3] * acc[k][2] + nc.c[4] * acc[k][3] + nc.c[5] * acc[k][4];
+            }
+            if (F == 4 && phiT) {
+                // charge form: D^T phi, phi the triangle potentials (nc.c[1] = 0 drops N^Phi)
+                const float2 pp = __ldg(phiT + (int64_t)btri_t[2 * i] * B + bc + lane);
+                const float2 pm = __ldg(phiT + (int64_t)btri_t[2 * i + 1] * B + bc + lane);
+                e = e + (float)blen[i] * (pp - pm);
             }
             if (lin_ptr) {
                 // linear-term modification: a few overlapping pairs per row
@@ -841,11 +864,15 @@ __global__ void __launch_bounds__(2 * F * 8) k_zpass_tma(const __grid_constant__
 }
 
 // K4 (register form): inverse of K2 plus the interpolation partials.
+// Charge form (tpart given, EFIE): the rho field's output plane is interpolated with the pulse
+// weights per triangle touching the plane (partials tpart[b][slot][t]) instead of per basis.
 template <int N>
 __global__ void __launch_bounds__(2 * N) k_xy_inv_reg(const float2* __restrict__ S, const float* __restrict__ w,
                                                       const int* __restrict__ anc, const int* __restrict__ plane_lo,
                                                       const int* __restrict__ plane_hi, float2* part, int F, int Nz,
-                                                      int Ntot, int P) {
+                                                      int Ntot, int P, const int* __restrict__ tanc,
+                                                      const int* __restrict__ tplane, const float* __restrict__ lps,
+                                                      float2* tpart, int nt) {
     extern __shared__ float2 sm[];
     constexpr int PITCH = N + 1;
     float2* acc = sm + 2 * N * PITCH;
@@ -904,7 +931,19 @@ __global__ void __launch_bounds__(2 * N) k_xy_inv_reg(const float2* __restrict__
             for (int x = 0; x < N; ++x) O[r * PITCH + x] = O[r * PITCH + x] + v[x];
         }
         __syncthreads();
-        if (P == 3) {
+        if (tpart && f == 3) {
+            // charge form: triangle partials of the rho field, one per (triangle, stencil slot)
+            const int tlo = tplane[z], thi = tplane[Nz + z];
+            for (int k = tlo + threadIdx.x; k < thi; k += blockDim.x) {
+                const int sx = tanc[3 * k], sy = tanc[3 * k + 1], slot = z - tanc[3 * k + 2];
+                const float* lw = lps + (int64_t)slot * P * P * nt + k;
+                float2 sk = make_float2(0.f, 0.f);
+                for (int uy = 0; uy < P; ++uy)
+                    for (int ux = 0; ux < P; ++ux)
+                        rfma(sk, __ldg(lw + (int64_t)(uy * P + ux) * nt), O[(sy + uy) * PITCH + sx + ux]);
+                tpart[((int64_t)b * P + slot) * nt + k] = sk;
+            }
+        } else if (P == 3) {
             // four bases per iteration so that their 36 weight gathers are in flight together
             // (the transform's registers are free in this phase)
             const int bd = blockDim.x;
@@ -1005,8 +1044,10 @@ static void launch_xy_inv_reg(const aimx_ctx* ctx, const float2* S, const int* p
                               int B, cudaStream_t s) {
     size_t sm = (2 * (size_t)N * (N + 1) + 2 * (size_t)ctx->max_plane_bases) * sizeof(float2);
     set_smem(k_xy_inv_reg<N>, sm);
-    k_xy_inv_reg<N><<<dim3(ctx->n[2], ctx->F / 4, B), 2 * N, sm, s>>>(S, ctx->d_wsoa, ctx->d_anc, plo, phi, part,
-                                                                      ctx->F, ctx->n[2], ctx->N, ctx->P);
+    const bool chg = ctx->charge != 0;
+    k_xy_inv_reg<N><<<dim3(ctx->n[2], ctx->F / 4, B), 2 * N, sm, s>>>(
+        S, ctx->d_wsoa, ctx->d_anc, plo, phi, part, ctx->F, ctx->n[2], ctx->N, ctx->P, ctx->d_tanc, ctx->d_tplane,
+        ctx->d_lp_soa, chg ? reinterpret_cast<float2*>(ctx->d_tpart) : nullptr, ctx->nt);
 }
 
 template <int NZ, int F>
@@ -1080,15 +1121,20 @@ static void run_fused(aimx_ctx* ctx, const NearC& nc, int B, const float2* xb, f
     int64_t tot = (int64_t)nunk * B;
     k_transpose_x<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(xb, ctx->d_perm, fb.xT, N, nunk, B);
     AIMX_CUDA_TRY(cudaGetLastError());
+    const bool chg = ctx->charge != 0;
+    if (chg) charge_fused_q(ctx, fb.xT, B, s);
     delete sc;
     sc = scope(ST_GATHER);
     {
         const dim3 grid((unsigned)((NG + 15) / 16), (unsigned)((B + 31) / 32));
         const float4* w4 = reinterpret_cast<const float4*>(ctx->f32.w);
         if (F == 8)
-            k_gather_tile<8><<<grid, 256, 0, s>>>(w4, ctx->d_node_ptr, ctx->d_node_w, fb.xT, fb.G, B, N, U, NG);
+            k_gather_tile<8><<<grid, 256, 0, s>>>(w4, ctx->d_node_ptr, ctx->d_node_w, fb.xT, fb.G, B, N, U, NG,
+                                                  nullptr, nullptr, nullptr, nullptr);
         else
-            k_gather_tile<4><<<grid, 256, 0, s>>>(w4, ctx->d_node_ptr, ctx->d_node_w, fb.xT, fb.G, B, N, U, NG);
+            k_gather_tile<4><<<grid, 256, 0, s>>>(w4, ctx->d_node_ptr, ctx->d_node_w, fb.xT, fb.G, B, N, U, NG,
+                                                  chg ? ctx->d_tnode_ptr : nullptr, ctx->d_tnode_w, ctx->f32.plw,
+                                                  reinterpret_cast<const float2*>(ctx->d_qT));
     }
     AIMX_CUDA_TRY(cudaGetLastError());
     delete sc;
@@ -1165,6 +1211,8 @@ static void run_fused(aimx_ctx* ctx, const NearC& nc, int B, const float2* xb, f
     AIMX_CUDA_TRY(cudaGetLastError());
     delete sc;
     sc = scope(ST_FINAL);
+    if (chg) charge_fused_phi(ctx, B, nc.cphi, s);
+    const float2* phiT = chg ? reinterpret_cast<const float2*>(ctx->d_phiT) : nullptr;
     if (!ctx->aim && ctx->nb_count > 0) {
         const size_t smem = (size_t)ctx->nb_umax * 32 * sizeof(float2);
         const int* lp_ = ctx->linterm ? ctx->d_lin_ptr : nullptr;
@@ -1173,12 +1221,14 @@ static void run_fused(aimx_ctx* ctx, const NearC& nc, int B, const float2* xb, f
             set_smem(k_near_blk<8>, smem);
             k_near_blk<8><<<ctx->nb_count, kNbWarps * 32, smem, s>>>(
                 fb.part, fb.xT, ctx->d_nb_rows, ctx->d_nb_ustart, ctx->d_nb_ucols, ctx->d_nb_ent, ctx->d_row_ptr,
-                ctx->d_perm, lp_, ctx->d_lin_cols, ctx->f32.la, ctx->f32.lp, yb, nc, has_k, N, nunk, P, B);
+                ctx->d_perm, lp_, ctx->d_lin_cols, ctx->f32.la, ctx->f32.lp, yb, nc, has_k, N, nunk, P, B, phiT,
+                ctx->d_btri_t, ctx->d_blen);
         } else {
             set_smem(k_near_blk<4>, smem);
             k_near_blk<4><<<ctx->nb_count, kNbWarps * 32, smem, s>>>(
                 fb.part, fb.xT, ctx->d_nb_rows, ctx->d_nb_ustart, ctx->d_nb_ucols, ctx->d_nb_ent, ctx->d_row_ptr,
-                ctx->d_perm, lp_, ctx->d_lin_cols, ctx->f32.la, ctx->f32.lp, yb, nc, has_k, N, nunk, P, B);
+                ctx->d_perm, lp_, ctx->d_lin_cols, ctx->f32.la, ctx->f32.lp, yb, nc, has_k, N, nunk, P, B, phiT,
+                ctx->d_btri_t, ctx->d_blen);
         }
     } else
     k_final<<<(N + kFinalRows - 1) / kFinalRows, kThreads, 0, s>>>(fb.part, fb.xT, ctx->d_row_ptr, ctx->d_cols,
@@ -1188,7 +1238,8 @@ static void run_fused(aimx_ctx* ctx, const NearC& nc, int B, const float2* xb, f
                                                                    ctx->d_lin_cols, ctx->f32.la, ctx->f32.lp,
                                                                    ctx->aim ? reinterpret_cast<const float2*>(ctx->f32.zn)
                                                                             : nullptr,
-                                                                   yb, nc, F, N, nunk, P, B);
+                                                                   yb, nc, F, N, nunk, P, B, phiT, ctx->d_btri_t,
+                                                                   ctx->d_blen);
     AIMX_CUDA_TRY(cudaGetLastError());
     delete sc;
 }
@@ -1198,6 +1249,12 @@ static NearC near_c(const aimx_ctx* ctx, double freq) {
     NearC nc;
     for (int k = 0; k < 6; ++k) nc.c[k] = make_float2((float)cf.near[k].x, (float)cf.near[k].y);
     for (int k = 0; k < 4; ++k) nc.lin[k] = make_float2((float)cf.lin[k].x, (float)cf.lin[k].y);
+    nc.cphi = make_float2(0.f, 0.f);
+    if (ctx->charge) {
+        // charge form: the RWG N^Phi drops out; its coefficient scales the triangle near part
+        nc.cphi = nc.c[1];
+        nc.c[1] = make_float2(0.f, 0.f);
+    }
     if (ctx->aim) {
         // the per-frequency entries carry j w mu and -j w mu / k^2 already; they are exact on the
         // near pairs, so the linear-term modification does not apply
@@ -1325,6 +1382,7 @@ void matvec_fused(aimx_ctx* ctx, double freq, int nrhs, const float* x, float* y
     int cap = (int)std::max<size_t>(1, std::min<size_t>(nrhs, ((size_t)8 << 30) / per_rhs));
     if (ctx->sched_pass > 0) cap = std::min(cap, ctx->sched_pass);
     ensure_fused_buffers(ctx, cap);
+    if (ctx->charge) ensure_charge_buffers(ctx, cap);
     FusedBufs fb{reinterpret_cast<float2*>(ctx->d_xT), reinterpret_cast<float2*>(ctx->d_G),
                  reinterpret_cast<float2*>(ctx->d_S), reinterpret_cast<float2*>(ctx->d_part)};
     for (int b0 = 0; b0 < nrhs; b0 += cap) {

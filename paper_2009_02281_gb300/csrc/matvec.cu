@@ -143,6 +143,8 @@ __global__ void k_interp_near(const T* __restrict__ w, const T* __restrict__ wg,
                               const T* __restrict__ la, const T* __restrict__ lp,
                               const cplx_t<T>* __restrict__ zn,
                               const cplx_t<T>* __restrict__ grid, const cplx_t<T>* __restrict__ x,
+                              const cplx_t<T>* __restrict__ phi, const int* __restrict__ btri_t,
+                              const double* __restrict__ blen, int nt,
                               cplx_t<T>* y, NearCoefs nc, int nrhs, int F, int two, int N, int nunk, int P,
                               int Mx, int My, int Mz) {
     using C = cplx_t<T>;
@@ -157,9 +159,11 @@ __global__ void k_interp_near(const T* __restrict__ w, const T* __restrict__ wg,
     const T* wgi = wg ? wg + (int64_t)i * U * 3 : nullptr;
     C aE = czero<T>(), aH = czero<T>();
     int sx = anc[3 * i], sy = anc[3 * i + 1], sz = anc[3 * i + 2];
+    // charge form (phi given): the rho field belongs to the triangles, not to the RWG weights
+    const int nfe = phi ? 3 : 4;
     for (int u = 0; u < U; ++u) {
         int64_t node = ((int64_t)(sz + u / (P * P)) * My + (sy + (u / P) % P)) * Mx + (sx + u % P);
-        for (int f = 0; f < 4; ++f) rfma(aE, wi[4 * u + f], gb[f * MT + node]);
+        for (int f = 0; f < nfe; ++f) rfma(aE, wi[4 * u + f], gb[f * MT + node]);
         if (wgi)
             for (int c = 0; c < 3; ++c) rfma(aE, wgi[3 * u + c], gb[(4 + c) * MT + node]);
         else if (two)
@@ -202,7 +206,13 @@ __global__ void k_interp_near(const T* __restrict__ w, const T* __restrict__ wg,
                 if (ng) rfma(sG, ng[e], xj);
             }
         }
-        aE = aE + cA * sA + cP * sP;
+        if (phi) {
+            // charge form: D^T phi in place of the RWG scalar potential's near part
+            const C* pb = phi + (int64_t)b * nt;
+            aE = aE + cA * sA + (T)blen[i] * (pb[btri_t[2 * i]] - pb[btri_t[2 * i + 1]]);
+        } else {
+            aE = aE + cA * sA + cP * sP;
+        }
         if (nk) aE = aE + mk((T)nc.c[2].x, (T)nc.c[2].y) * sK;            // CFIE: K_g
         if (ng) {
             const int g = nk ? 3 : 2;                                      // Gram: c[3] (CFIE), c[2] (EFIE)
@@ -298,6 +308,18 @@ void matvec_generic(aimx_ctx* ctx, double freq, int nrhs, const T* x, T* y, cuda
         pd.grid_elems = per_rhs * chunk;
     }
     C* grid = reinterpret_cast<C*>(pd.grid);
+    const bool chg = ctx->charge != 0;
+    C *cq = nullptr, *cphi = nullptr;
+    if (chg) {
+        const size_t need = 2 * (size_t)ctx->nt * chunk;
+        if (pd.cwork_elems < need) {
+            if (pd.cwork) dev_free(ctx, pd.cwork);
+            pd.cwork = (T*)dev_alloc(ctx, sizeof(C) * need);
+            pd.cwork_elems = need;
+        }
+        cq = reinterpret_cast<C*>(pd.cwork);
+        cphi = cq + (size_t)ctx->nt * chunk;
+    }
     const C* xc = reinterpret_cast<const C*>(x);
     C* yc = reinterpret_cast<C*>(y);
     const int act[3] = {ctx->n[0], ctx->n[1], ctx->n[2]};
@@ -311,6 +333,7 @@ void matvec_generic(aimx_ctx* ctx, double freq, int nrhs, const T* x, T* y, cuda
             pd.w, ctx->d_node_ptr, ctx->d_node_w, ctx->d_node_x, xc + (int64_t)b0 * ctx->nunk, grid, nb,
             two ? 8 : 4, F, ctx->N, ctx->nunk, ctx->n[0], ctx->n[1], ctx->n[2], ctx->M[0], ctx->M[1], ctx->M[2]);
         AIMX_CUDA_TRY(cudaGetLastError());
+        if (chg) charge_project<T>(ctx, xc + (int64_t)b0 * ctx->nunk, nb, cq, grid, F, 3, s);
         if (ctx->path == 2)
             cufft_padded<T>(ctx, grid, nb * F, CUFFT_FORWARD, s);
         else
@@ -323,13 +346,15 @@ void matvec_generic(aimx_ctx* ctx, double freq, int nrhs, const T* x, T* y, cuda
             cufft_padded<T>(ctx, grid, nb * F, CUFFT_INVERSE, s);
         else
             fft3d_padded<T>(reinterpret_cast<T*>(grid), nb * F, ctx->M, act, true, s);
+        if (chg) charge_potential<T>(ctx, grid, F, 3, nb, cq, cphi, nc.c[1], s);
         int64_t tn = (int64_t)ctx->N * nb;
         k_interp_near<T><<<(unsigned)((tn + 127) / 128), 128, 0, s>>>(
             pd.w, ctx->form == AIMX_CFIE ? pd.wg : nullptr, ctx->d_anc, ctx->d_perm, ctx->d_row_ptr, ctx->d_cols,
             pd.na, pd.np, ctx->form == AIMX_EFIE ? nullptr : pd.nk, two ? nullptr : pd.ng,
             ctx->linterm && !ctx->aim ? ctx->d_lin_ptr : nullptr, ctx->d_lin_cols, pd.la, pd.lp,
             ctx->aim ? reinterpret_cast<const C*>(pd.zn) : nullptr, grid,
-            xc + (int64_t)b0 * ctx->nunk, yc + (int64_t)b0 * ctx->nunk, nc, nb, F, two ? 1 : 0, ctx->N, ctx->nunk,
+            xc + (int64_t)b0 * ctx->nunk, chg ? cphi : nullptr, ctx->d_btri_t, ctx->d_blen, ctx->nt,
+            yc + (int64_t)b0 * ctx->nunk, nc, nb, F, two ? 1 : 0, ctx->N, ctx->nunk,
             ctx->P, ctx->M[0], ctx->M[1], ctx->M[2]);
         AIMX_CUDA_TRY(cudaGetLastError());
     }

@@ -67,6 +67,10 @@ extern "C" int aimx_matvec_noalloc(aimx_ctx* ctx, double freq, int nrhs, const v
             "(grid shape, aimx_set_path or the schedule)";
         return AIMX_E_STATE;
     }
+    if (ctx->charge) {
+        ctx->last_error = "aimx_matvec_noalloc: the charge form needs work buffers of its own; use aimx_matvec";
+        return AIMX_E_STATE;
+    }
     // The conventional-AIM near fill of a new frequency copies a host table and waits for it,
     // which would block the caller; that mode is accepted only at the frequency already filled.
     if (ctx->aim && ctx->aim_freq != freq) {

@@ -60,7 +60,7 @@ static void gauss_legendre01(int q, std::vector<double>& x, std::vector<double>&
 
 // Collapsed (Duffy) product rule: barycentric (u, (1-u)v, (1-u)(1-v)) with
 // normalised weight 2 w_u w_v (1-u); exact to total degree 2q-2.
-static void triangle_rule(int q, std::vector<double>& out /* [Q][4] l1 l2 l3 w */) {
+void triangle_rule(int q, std::vector<double>& out /* [Q][4] l1 l2 l3 w */) {
     std::vector<double> x, w;
     gauss_legendre01(q, x, w);
     out.clear();
