@@ -267,6 +267,40 @@ int aimx_farfield(aimx_ctx* ctx, double freq, int nrhs, const void* x, int ndir,
 int aimx_sweep(aimx_ctx* ctx, int nf, const double* freqs, int nwave, const double* dirs, const double* pols, void* X,
                const aimx_solve_opts* opts, int warm_start, aimx_solve_stats* stats, void* stream);
 
+/* Batched frequency sweep (the cost model of the Discussion, T = T_s + N T_d):
+ * the nf x nrhs systems A(k_f) x_{f,w} = b_{f,w} are solved together instead of
+ * one frequency after another.
+ *   - B: device [nf][nrhs][nunk] complex128 right-hand sides (plane waves,
+ *     ports or any other); X: device [nf][nrhs][nunk] complex128 solutions
+ *     (an initial guess when opts->use_x0).  Caller-owned, not overlapping.
+ *   - Right-preconditioned GMRES(restart) in lockstep over up to max_batch
+ *     systems at a time (0 = as many as fit about 8 GiB of Krylov vectors).
+ *     Each product of the batch carries one frequency per system: that
+ *     frequency's kernel spectra (Eq. Hmm), near coefficients and diagonal
+ *     preconditioner, built once per call for all frequencies, while the
+ *     static near matrices and weights are shared (Sec. III-A).
+ *   - The Arnoldi steps (classical Gram-Schmidt twice, FP64), the Givens
+ *     rotations, the convergence test and the back substitution run on the
+ *     device; one cycle of restart steps is captured into a CUDA graph and
+ *     replayed while the batch size stays the same.  The host synchronises
+ *     once per cycle to retire converged systems and admit pending ones; the
+ *     batch shrinks (a new graph) when fewer than 3/4 of it is busy.
+ *   - Every cycle starts from the true residual; with AIMX_F32 inner products
+ *     and tol >= 1e-5 cycle residuals use the FP32 product, and every reported
+ *     residual (stats[f][w].rel_residual, host array or NULL) is recomputed with
+ *     the FP64 product; systems that fail that check run more cycles with FP64
+ *     residuals.
+ *   - Products use the generic path (the plane-fused kernels take one
+ *     frequency per pass).  opts->precond: AIMX_PRECOND_DIAG or _NONE, others
+ *     AIMX_E_STATE; AIMX_E_STATE in the conventional-AIM mode.  The linear term
+ *     and the charge form apply.
+ *   - counters (host int64 [3] or NULL): cycles, graphs captured, batched
+ *     products.  Returns AIMX_E_NOCONV if any system missed tol.  Runs on a
+ *     private stream ordered after `stream`; synchronous on return. */
+int aimx_sweep_batched(aimx_ctx* ctx, int nf, const double* freqs, int nrhs, const void* B, void* X,
+                       const aimx_solve_opts* opts, int max_batch, aimx_solve_stats* stats, int64_t* counters,
+                       void* stream);
+
 /* Select the matvec implementation: 0 = automatic (FP32: the plane-fused
  * path whenever the grid is padded to exactly twice a power-of-two size per
  * axis, else the generic path), 1 = always the generic path, 2 = the generic

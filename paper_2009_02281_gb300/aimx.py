@@ -117,6 +117,9 @@ _SIGS = [
     ("aimx_sweep", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                   ctypes.c_void_p]),
+    ("aimx_sweep_batched", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("aimx_precond_apply", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("aimx_batch_create", ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
@@ -413,6 +416,26 @@ class Context:
                                               ctypes.c_void_p(X.data_ptr()), ctypes.byref(o), 1 if warm_start else 0,
                                               st, _stream_handle(stream)))
         return X, _stats_list(st), rc
+
+    def sweep_batched(self, freqs, B, tol=1e-6, restart=50, max_iter=1000, inner_precision=F32,
+                      precond=PRECOND_DIAG, max_batch=0, x0=None, stream=None):
+        """Solve A(k_f) x = b for every frequency f and RHS at once (aimx_sweep_batched).
+
+        B: CUDA complex128 [nf, nrhs, nunk].  Returns (X, stats [nf][nrhs], rc, counters) with
+        counters = (cycles, graphs captured, batched products)."""
+        import torch
+        freqs = np.ascontiguousarray(freqs, dtype=np.float64)
+        B = B.contiguous()
+        nf, nrhs = int(B.shape[0]), int(B.shape[1])
+        X = x0.clone().contiguous() if x0 is not None else torch.empty_like(B)
+        st = (_SolveStats * (nf * nrhs))()
+        cnt = np.zeros(3, dtype=np.int64)
+        o = _opts(tol, restart, max_iter, inner_precision, precond, 1 if x0 is not None else 0, 0, 0)
+        rc = self._check(self._lib.aimx_sweep_batched(self._ctx, nf, _ptr(freqs), nrhs, ctypes.c_void_p(B.data_ptr()),
+                                                      ctypes.c_void_p(X.data_ptr()), ctypes.byref(o), int(max_batch),
+                                                      st, _ptr(cnt), _stream_handle(stream)))
+        stats = _stats_list(st)
+        return X, [stats[f * nrhs:(f + 1) * nrhs] for f in range(nf)], rc, tuple(int(v) for v in cnt)
 
     def set_path(self, path):
         """0 = automatic (plane-fused FP32 path when supported), 1 = generic path, 2 = generic with cuFFT."""

@@ -10,8 +10,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libaimx.so")
 SOURCES = ["setup.cu", "fft.cu", "matvec.cu", "fused.cu", "solve.cu", "precond.cu", "gnn.cu", "batch.cu", "ports.cu",
-           "aim.cu", "tune.cu", "noalloc.cu", "peak.cu", "charge.cu", "api.cu"]
-HEADERS = ["aimx_internal.h", "cplx.cuh", "fftreg.cuh", "regfft.cuh", "geom.cuh"]
+           "aim.cu", "tune.cu", "noalloc.cu", "peak.cu", "charge.cu", "sweep.cu", "api.cu"]
+HEADERS = ["aimx_internal.h", "cplx.cuh", "fftreg.cuh", "regfft.cuh", "geom.cuh", "krylov.cuh"]
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
          "-diag-suppress", "177"]

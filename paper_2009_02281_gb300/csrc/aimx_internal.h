@@ -389,7 +389,8 @@ void charge_project(aimx_ctx* ctx, const typename Cplx<T>::type* x, int nb, type
 // generic path: phi = Lp^T (convolved rho field) + cP N_Pt q per triangle ([nb][nt])
 template <class T>
 void charge_potential(aimx_ctx* ctx, const typename Cplx<T>::type* grid, int Fg, int rho_field, int nb,
-                      const typename Cplx<T>::type* q, typename Cplx<T>::type* phi, double2 cP, cudaStream_t s);
+                      const typename Cplx<T>::type* q, typename Cplx<T>::type* phi, double2 cP, cudaStream_t s,
+                      const double2* cps = nullptr, const int* fidx = nullptr);
 // plane-fused path: qT = D x from xT ([nt][B]); phiT = sum of plane partials + cP N_Pt qT
 void charge_fused_q(aimx_ctx* ctx, const float2* xT, int B, cudaStream_t s);
 void charge_fused_phi(aimx_ctx* ctx, int B, float2 cP, cudaStream_t s);
@@ -414,8 +415,24 @@ void gnn_free(aimx_ctx* ctx);
 // solve.cu: inverse of the frequency-combined static self blocks (caller order)
 void build_diag_inverse(aimx_ctx* ctx, double freq, double2* minv, cudaStream_t s);
 
+// near coefficients of a product (the generic path's form of Coefs)
+struct NearCoefs {
+    double2 c[6];
+    double2 lin[4];   // linear-term coefficients (J rows: A, Phi; M rows: A, Phi)
+};
+// Frequencies of a batched product: RHS b of the pass takes frequency d_fidx[b]
+struct MultiFreq {
+    const int* d_fidx = nullptr;       // [nrhs] frequency index per RHS (device)
+    const void* spec = nullptr;        // [nf][nspec][Oz][Oy][Ox] complex of the product's precision
+    int64_t fstride = 0;               // complex elements per frequency in spec
+    const NearCoefs* d_ncs = nullptr;  // [nf] near coefficients (device)
+    const double2* d_cphi = nullptr;   // [nf] charge-form near coefficient (device)
+};
+
 // matvec.cu
 void cufft_release(aimx_ctx* ctx);
+template <class T>
+void matvec_generic_multi(aimx_ctx* ctx, const MultiFreq& mf, int nrhs, const T* x, T* y, cudaStream_t s);
 template <class T>
 void matvec_generic(aimx_ctx* ctx, double freq, int nrhs, const T* x, T* y, cudaStream_t s);
 

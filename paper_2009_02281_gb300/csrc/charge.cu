@@ -338,11 +338,13 @@ template <class T>
 __global__ void k_potential(const T* __restrict__ lp, const int* __restrict__ tanc, const int* __restrict__ row_ptr,
                             const int* __restrict__ cols, const T* __restrict__ npt,
                             const cplx_t<T>* __restrict__ grid, int Fg, int rho_field, const cplx_t<T>* __restrict__ q,
-                            cplx_t<T>* phi, double2 cP, int nb, int nt, int P, int Mx, int My, int Mz) {
+                            cplx_t<T>* phi, double2 cP0, const double2* __restrict__ cps, const int* __restrict__ fidx,
+                            int nb, int nt, int P, int Mx, int My, int Mz) {
     using C = cplx_t<T>;
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= (int64_t)nt * nb) return;
     const int ti = (int)(t % nt), b = (int)(t / nt);
+    const double2 cP = cps ? cps[fidx[b]] : cP0;   // per-RHS frequency in batched products
     const int U = P * P * P;
     const int64_t SB = (int64_t)Mx * My * Mz;
     const C* gr = grid + ((int64_t)b * Fg + rho_field) * SB;
@@ -375,12 +377,12 @@ void charge_project(aimx_ctx* ctx, const cplx_t<T>* x, int nb, cplx_t<T>* q, cpl
 
 template <class T>
 void charge_potential(aimx_ctx* ctx, const cplx_t<T>* grid, int Fg, int rho_field, int nb, const cplx_t<T>* q,
-                      cplx_t<T>* phi, double2 cP, cudaStream_t s) {
+                      cplx_t<T>* phi, double2 cP, cudaStream_t s, const double2* cps, const int* fidx) {
     PrecData<T>& pd = prec<T>(ctx);
     const int nt = ctx->nt;
     const int64_t tq = (int64_t)nt * nb;
     k_potential<T><<<(unsigned)((tq + 127) / 128), 128, 0, s>>>(pd.plw, ctx->d_tanc, ctx->d_trow_ptr, ctx->d_tcols,
-                                                                 pd.npt, grid, Fg, rho_field, q, phi, cP, nb, nt,
+                                                                 pd.npt, grid, Fg, rho_field, q, phi, cP, cps, fidx, nb, nt,
                                                                  ctx->P, ctx->M[0], ctx->M[1], ctx->M[2]);
     AIMX_CUDA_TRY(cudaGetLastError());
 }
@@ -388,9 +390,9 @@ void charge_potential(aimx_ctx* ctx, const cplx_t<T>* grid, int Fg, int rho_fiel
 template void charge_project<float>(aimx_ctx*, const float2*, int, float2*, float2*, int, int, cudaStream_t);
 template void charge_project<double>(aimx_ctx*, const double2*, int, double2*, double2*, int, int, cudaStream_t);
 template void charge_potential<float>(aimx_ctx*, const float2*, int, int, int, const float2*, float2*, double2,
-                                      cudaStream_t);
+                                      cudaStream_t, const double2*, const int*);
 template void charge_potential<double>(aimx_ctx*, const double2*, int, int, int, const double2*, double2*, double2,
-                                       cudaStream_t);
+                                       cudaStream_t, const double2*, const int*);
 
 // ------------------------------------------------------------------ plane-fused path
 

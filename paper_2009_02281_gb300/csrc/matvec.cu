@@ -16,10 +16,6 @@
 
 namespace aimx {
 
-struct NearCoefs {
-    double2 c[6];
-    double2 lin[4];   // linear-term coefficients (J rows: A, Phi; M rows: A, Phi)
-};
 
 // Fields per RHS: EFIE (Jx, Jy, Jz, rho); PMCHWT adds (Mx, My, Mz, rho_M).
 // Field f uses weight component f % 4 and unknown block f / 4.  F fields are
@@ -54,79 +50,95 @@ __global__ void k_project(const T* __restrict__ w, const int* __restrict__ node_
     for (int f = 0; f < F; ++f) gb[f * SB] = acc[f];
 }
 
+
+// The kernel multiply at one spectral point for one RHS (g: that RHS's first field at the point,
+// fields MT apart).  sp: the point's spectra, odd signs of the gradient components applied.
+// EFIE (A, Phi): S1 J, S2 rho; PMCHWT: E rows S1 J + V x M, S2 rho_J; H rows S3 M - V x J,
+// S4 rho_M; CFIE: (A, Phi) of J and the K part V x J (V = (1 - alpha) eta grad G).
 template <class T>
-__device__ inline cplx_t<T> load_spec(const cplx_t<T>* spec, int s, int64_t OT, int64_t oi) {
-    return spec[s * OT + oi];
+__device__ inline void mix_rhs(cplx_t<T>* g, int64_t MT, const cplx_t<T>* sp, int F, int cfie) {
+    using C = cplx_t<T>;
+    if (cfie) {
+        const C s1 = sp[0], s2 = sp[1], vx = sp[2], vy = sp[3], vz = sp[4];
+        C jx = g[0], jy = g[MT], jz = g[2 * MT];
+        g[0] = s1 * jx;
+        g[MT] = s1 * jy;
+        g[2 * MT] = s1 * jz;
+        g[3 * MT] = s2 * g[3 * MT];
+        g[4 * MT] = vy * jz - vz * jy;
+        g[5 * MT] = vz * jx - vx * jz;
+        g[6 * MT] = vx * jy - vy * jx;
+        g[7 * MT] = czero<T>();
+    } else if (F == 4) {
+        g[0] = sp[0] * g[0];
+        g[MT] = sp[0] * g[MT];
+        g[2 * MT] = sp[0] * g[2 * MT];
+        g[3 * MT] = sp[1] * g[3 * MT];
+    } else {
+        const C s1 = sp[0], s2 = sp[1], s3 = sp[2], s4 = sp[3], vx = sp[4], vy = sp[5], vz = sp[6];
+        C jx = g[0], jy = g[MT], jz = g[2 * MT], rj = g[3 * MT];
+        C mx = g[4 * MT], my = g[5 * MT], mz = g[6 * MT], rm = g[7 * MT];
+        g[0] = s1 * jx + (vy * mz - vz * my);
+        g[MT] = s1 * jy + (vz * mx - vx * mz);
+        g[2 * MT] = s1 * jz + (vx * my - vy * mx);
+        g[3 * MT] = s2 * rj;
+        g[4 * MT] = s3 * mx - (vy * jz - vz * jy);
+        g[5 * MT] = s3 * my - (vz * jx - vx * jz);
+        g[6 * MT] = s3 * mz - (vx * jy - vy * jx);
+        g[7 * MT] = s4 * rm;
+    }
 }
 
-// Per spectral point: out = mix(in) with the octant spectra (EFIE: 2 scalar,
-// PMCHWT: 4 scalar + gradient vector V with odd symmetry per component).
+// the octant spectra of point t (index oi), with the odd components' signs applied
+template <class T>
+__device__ inline int load_point_spectra(const cplx_t<T>* spec, int64_t t, int F, int cfie, int Mx, int My, int Mz,
+                                         cplx_t<T>* sp) {
+    const int kx = (int)(t % Mx), ky = (int)((t / Mx) % My), kz = (int)(t / ((int64_t)Mx * My));
+    const int ox = kx <= Mx / 2 ? kx : Mx - kx;
+    const int oy = ky <= My / 2 ? ky : My - ky;
+    const int oz = kz <= Mz / 2 ? kz : Mz - kz;
+    const int64_t OT = (int64_t)(Mx / 2 + 1) * (My / 2 + 1) * (Mz / 2 + 1);
+    const int64_t oi = ((int64_t)oz * (My / 2 + 1) + oy) * (Mx / 2 + 1) + ox;
+    const int ns = cfie ? 5 : (F == 4 ? 2 : 7);
+    const int g0 = cfie ? 2 : 4;                 // first gradient component
+    for (int k = 0; k < ns; ++k) sp[k] = spec[k * OT + oi];
+    if (cfie || F == 8) {
+        if (kx > Mx / 2) sp[g0] = -sp[g0];
+        if (ky > My / 2) sp[g0 + 1] = -sp[g0 + 1];
+        if (kz > Mz / 2) sp[g0 + 2] = -sp[g0 + 2];
+    }
+    return ns;
+}
+
+// Per spectral point: out = mix(in) with the octant spectra, all RHS of the pass (one frequency)
 template <class T>
 __global__ void k_mix(cplx_t<T>* grid, const cplx_t<T>* __restrict__ spec, int nrhs, int F, int cfie, int Mx,
                       int My, int Mz) {
     using C = cplx_t<T>;
-    int64_t MT = (int64_t)Mx * My * Mz;
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t MT = (int64_t)Mx * My * Mz;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= MT) return;
-    int kx = (int)(t % Mx), ky = (int)((t / Mx) % My), kz = (int)(t / ((int64_t)Mx * My));
-    int ox = kx <= Mx / 2 ? kx : Mx - kx;
-    int oy = ky <= My / 2 ? ky : My - ky;
-    int oz = kz <= Mz / 2 ? kz : Mz - kz;
-    int Ox = Mx / 2 + 1, Oy = My / 2 + 1, Oz = Mz / 2 + 1;
-    int64_t OT = (int64_t)Ox * Oy * Oz;
-    int64_t oi = ((int64_t)oz * Oy + oy) * Ox + ox;
-    if (cfie) {
-        // (A, Phi) of J and the K part V x J (V = (1 - alpha) eta grad G spectra, odd per component)
-        C s1 = load_spec<T>(spec, 0, OT, oi), s2 = load_spec<T>(spec, 1, OT, oi);
-        C vx = load_spec<T>(spec, 2, OT, oi), vy = load_spec<T>(spec, 3, OT, oi),
-          vz = load_spec<T>(spec, 4, OT, oi);
-        if (kx > Mx / 2) vx = -vx;
-        if (ky > My / 2) vy = -vy;
-        if (kz > Mz / 2) vz = -vz;
-        for (int b = 0; b < nrhs; ++b) {
-            C* g = grid + (int64_t)b * 8 * MT + t;
-            C jx = g[0], jy = g[MT], jz = g[2 * MT];
-            g[0] = s1 * jx;
-            g[MT] = s1 * jy;
-            g[2 * MT] = s1 * jz;
-            g[3 * MT] = s2 * g[3 * MT];
-            g[4 * MT] = vy * jz - vz * jy;
-            g[5 * MT] = vz * jx - vx * jz;
-            g[6 * MT] = vx * jy - vy * jx;
-            g[7 * MT] = czero<T>();
-        }
-    } else if (F == 4) {
-        C s1 = load_spec<T>(spec, 0, OT, oi), s2 = load_spec<T>(spec, 1, OT, oi);
-        for (int b = 0; b < nrhs; ++b) {
-            C* g = grid + (int64_t)b * 4 * MT + t;
-            g[0] = s1 * g[0];
-            g[MT] = s1 * g[MT];
-            g[2 * MT] = s1 * g[2 * MT];
-            g[3 * MT] = s2 * g[3 * MT];
-        }
-    } else {
-        C s1 = load_spec<T>(spec, 0, OT, oi), s2 = load_spec<T>(spec, 1, OT, oi);
-        C s3 = load_spec<T>(spec, 2, OT, oi), s4 = load_spec<T>(spec, 3, OT, oi);
-        C vx = load_spec<T>(spec, 4, OT, oi), vy = load_spec<T>(spec, 5, OT, oi),
-          vz = load_spec<T>(spec, 6, OT, oi);
-        if (kx > Mx / 2) vx = -vx;
-        if (ky > My / 2) vy = -vy;
-        if (kz > Mz / 2) vz = -vz;
-        for (int b = 0; b < nrhs; ++b) {
-            C* g = grid + (int64_t)b * 8 * MT + t;
-            C jx = g[0], jy = g[MT], jz = g[2 * MT], rj = g[3 * MT];
-            C mx = g[4 * MT], my = g[5 * MT], mz = g[6 * MT], rm = g[7 * MT];
-            // E rows: S1 J + V x M ; H rows: -V x J + S3 M
-            g[0] = s1 * jx + (vy * mz - vz * my);
-            g[MT] = s1 * jy + (vz * mx - vx * mz);
-            g[2 * MT] = s1 * jz + (vx * my - vy * mx);
-            g[3 * MT] = s2 * rj;
-            g[4 * MT] = s3 * mx - (vy * jz - vz * jy);
-            g[5 * MT] = s3 * my - (vz * jx - vx * jz);
-            g[6 * MT] = s3 * mz - (vx * jy - vy * jx);
-            g[7 * MT] = s4 * rm;
-        }
-    }
+    C sp[7];
+    load_point_spectra<T>(spec, t, F, cfie, Mx, My, Mz, sp);
+    const int Fg = cfie ? 8 : F;
+    for (int b = 0; b < nrhs; ++b) mix_rhs<T>(grid + (int64_t)b * Fg * MT + t, MT, sp, F, cfie);
+}
+
+// The same with a frequency per RHS: RHS b takes the spectra of frequency fidx[b] (fstride
+// complex apart); one thread per (point, RHS)
+template <class T>
+__global__ void k_mix_multi(cplx_t<T>* grid, const cplx_t<T>* __restrict__ spec, const int* __restrict__ fidx,
+                            int64_t fstride, int nrhs, int F, int cfie, int Mx, int My, int Mz) {
+    using C = cplx_t<T>;
+    const int64_t MT = (int64_t)Mx * My * Mz;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= MT * nrhs) return;
+    const int b = (int)(t / MT);
+    const int64_t p = t % MT;
+    C sp[7];
+    load_point_spectra<T>(spec + fidx[b] * fstride, p, F, cfie, Mx, My, Mz, sp);
+    const int Fg = cfie ? 8 : F;
+    mix_rhs<T>(grid + (int64_t)b * Fg * MT + p, MT, sp, F, cfie);
 }
 
 // y[b][perm i] (and y[b][N + perm i]) = W-gather of the output fields + near correction.
@@ -145,13 +157,16 @@ __global__ void k_interp_near(const T* __restrict__ w, const T* __restrict__ wg,
                               const cplx_t<T>* __restrict__ grid, const cplx_t<T>* __restrict__ x,
                               const cplx_t<T>* __restrict__ phi, const int* __restrict__ btri_t,
                               const double* __restrict__ blen, int nt,
-                              cplx_t<T>* y, NearCoefs nc, int nrhs, int F, int two, int N, int nunk, int P,
+                              cplx_t<T>* y, NearCoefs nc0, const NearCoefs* __restrict__ ncs,
+                              const int* __restrict__ fidx, int nrhs, int F, int two, int N, int nunk, int P,
                               int Mx, int My, int Mz) {
     using C = cplx_t<T>;
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= (int64_t)N * nrhs) return;
     int i = (int)(t % N);
     int b = (int)(t / N);
+    // near coefficients of this RHS's frequency (one frequency per pass unless ncs is given)
+    const NearCoefs& nc = ncs ? ncs[fidx[b]] : nc0;
     int U = P * P * P;
     int64_t MT = (int64_t)Mx * My * Mz;
     const C* gb = grid + (int64_t)b * F * MT;
@@ -280,19 +295,29 @@ void cufft_release(aimx_ctx* ctx) {
         }
 }
 
+// The generic product for one frequency (mf == nullptr) or for a batch whose RHS b takes
+// frequency mf->d_fidx[b] (spectra, near coefficients and charge-form coefficient of that
+// frequency from the tables in mf).
 template <class T>
-void matvec_generic(aimx_ctx* ctx, double freq, int nrhs, const T* x, T* y, cudaStream_t s) {
+static void generic_product(aimx_ctx* ctx, double freq, const MultiFreq* mf, int nrhs, const T* x, T* y,
+                            cudaStream_t s) {
     using C = cplx_t<T>;
     PrecData<T>& pd = prec<T>(ctx);
-    ensure_spectra<T>(ctx, freq, s);
-    Coefs cf = near_coefs(ctx, freq);
     NearCoefs nc;
-    for (int k = 0; k < 6; ++k) nc.c[k] = cf.near[k];
-    for (int k = 0; k < 4; ++k) nc.lin[k] = cf.lin[k];
-    ensure_aim_near(ctx, freq, s);
-    if (ctx->aim) {
-        nc.c[0] = make_double2(1.0, 0.0);
-        nc.c[1] = make_double2(0.0, 0.0);
+    if (!mf) {
+        ensure_spectra<T>(ctx, freq, s);
+        Coefs cf = near_coefs(ctx, freq);
+        for (int k = 0; k < 6; ++k) nc.c[k] = cf.near[k];
+        for (int k = 0; k < 4; ++k) nc.lin[k] = cf.lin[k];
+        ensure_aim_near(ctx, freq, s);
+        if (ctx->aim) {
+            nc.c[0] = make_double2(1.0, 0.0);
+            nc.c[1] = make_double2(0.0, 0.0);
+            for (auto& v : nc.lin) v = make_double2(0.0, 0.0);
+        }
+    } else {
+        if (ctx->aim) throw Error{AIMX_E_STATE, "the conventional-AIM mode has no multi-frequency product"};
+        for (auto& v : nc.c) v = make_double2(0.0, 0.0);
         for (auto& v : nc.lin) v = make_double2(0.0, 0.0);
     }
     const int F = ctx->F;
@@ -338,15 +363,22 @@ void matvec_generic(aimx_ctx* ctx, double freq, int nrhs, const T* x, T* y, cuda
             cufft_padded<T>(ctx, grid, nb * F, CUFFT_FORWARD, s);
         else
             fft3d_padded<T>(reinterpret_cast<T*>(grid), nb * F, ctx->M, act, false, s);
-        k_mix<T><<<(unsigned)((MT + 255) / 256), 256, 0, s>>>(
-            grid, reinterpret_cast<const C*>(pd.spec), nb, F, ctx->form == AIMX_CFIE ? 1 : 0, ctx->M[0], ctx->M[1],
-            ctx->M[2]);
+        if (mf)
+            k_mix_multi<T><<<(unsigned)((MT * nb + 255) / 256), 256, 0, s>>>(
+                grid, reinterpret_cast<const C*>(mf->spec), mf->d_fidx + b0, mf->fstride, nb, F,
+                ctx->form == AIMX_CFIE ? 1 : 0, ctx->M[0], ctx->M[1], ctx->M[2]);
+        else
+            k_mix<T><<<(unsigned)((MT + 255) / 256), 256, 0, s>>>(
+                grid, reinterpret_cast<const C*>(pd.spec), nb, F, ctx->form == AIMX_CFIE ? 1 : 0, ctx->M[0],
+                ctx->M[1], ctx->M[2]);
         AIMX_CUDA_TRY(cudaGetLastError());
         if (ctx->path == 2)
             cufft_padded<T>(ctx, grid, nb * F, CUFFT_INVERSE, s);
         else
             fft3d_padded<T>(reinterpret_cast<T*>(grid), nb * F, ctx->M, act, true, s);
-        if (chg) charge_potential<T>(ctx, grid, F, 3, nb, cq, cphi, nc.c[1], s);
+        if (chg)
+            charge_potential<T>(ctx, grid, F, 3, nb, cq, cphi, nc.c[1], s, mf ? mf->d_cphi : nullptr,
+                                mf ? mf->d_fidx + b0 : nullptr);
         int64_t tn = (int64_t)ctx->N * nb;
         k_interp_near<T><<<(unsigned)((tn + 127) / 128), 128, 0, s>>>(
             pd.w, ctx->form == AIMX_CFIE ? pd.wg : nullptr, ctx->d_anc, ctx->d_perm, ctx->d_row_ptr, ctx->d_cols,
@@ -354,13 +386,25 @@ void matvec_generic(aimx_ctx* ctx, double freq, int nrhs, const T* x, T* y, cuda
             ctx->linterm && !ctx->aim ? ctx->d_lin_ptr : nullptr, ctx->d_lin_cols, pd.la, pd.lp,
             ctx->aim ? reinterpret_cast<const C*>(pd.zn) : nullptr, grid,
             xc + (int64_t)b0 * ctx->nunk, chg ? cphi : nullptr, ctx->d_btri_t, ctx->d_blen, ctx->nt,
-            yc + (int64_t)b0 * ctx->nunk, nc, nb, F, two ? 1 : 0, ctx->N, ctx->nunk,
-            ctx->P, ctx->M[0], ctx->M[1], ctx->M[2]);
+            yc + (int64_t)b0 * ctx->nunk, nc, mf ? mf->d_ncs : nullptr, mf ? mf->d_fidx + b0 : nullptr, nb, F,
+            two ? 1 : 0, ctx->N, ctx->nunk, ctx->P, ctx->M[0], ctx->M[1], ctx->M[2]);
         AIMX_CUDA_TRY(cudaGetLastError());
     }
 }
 
+template <class T>
+void matvec_generic(aimx_ctx* ctx, double freq, int nrhs, const T* x, T* y, cudaStream_t s) {
+    generic_product<T>(ctx, freq, nullptr, nrhs, x, y, s);
+}
+
+template <class T>
+void matvec_generic_multi(aimx_ctx* ctx, const MultiFreq& mf, int nrhs, const T* x, T* y, cudaStream_t s) {
+    generic_product<T>(ctx, 0.0, &mf, nrhs, x, y, s);
+}
+
 template void matvec_generic<float>(aimx_ctx*, double, int, const float*, float*, cudaStream_t);
 template void matvec_generic<double>(aimx_ctx*, double, int, const double*, double*, cudaStream_t);
+template void matvec_generic_multi<float>(aimx_ctx*, const MultiFreq&, int, const float*, float*, cudaStream_t);
+template void matvec_generic_multi<double>(aimx_ctx*, const MultiFreq&, int, const double*, double*, cudaStream_t);
 
 }  // namespace aimx
