@@ -222,6 +222,30 @@ def measure_solves(ctx, wl, args):
         finally:
             ctx.set_path(args.path)
         plain["path"] = "generic + cuFFT, FP64 products, diagonal preconditioner"
+        # per-RHS cost of its product at 4, 16 and 64 right-hand sides: the solve's cost is its
+        # products, so this shows whether the per-RHS solve cost stays flat up to the full batch
+        per_rhs = {}
+        ctx.set_path(2)
+        try:
+            stream = torch.cuda.current_stream()
+            for nb2 in (4, 16, 64):
+                if nb2 > B:
+                    continue
+                xx = torch.ones((nb2, ctx.nunk), dtype=torch.complex128, device="cuda")
+                yy = torch.empty_like(xx)
+                ctx.matvec(freq, xx, yy)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(2):
+                    ctx.matvec(freq, xx, yy)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                per_rhs[str(nb2)] = round(e0.elapsed_time(e1) / 2 / nb2, 3)
+                del xx, yy
+        finally:
+            ctx.set_path(args.path)
+        plain["product_ms_per_rhs"] = per_rhs
         out["plain_fp64_cufft"] = plain
         best = max(out["diag"]["solves_per_s"], out.get("learned", {}).get("solves_per_s", 0.0))
         if plain["solves_per_s"] > 0:
@@ -234,7 +258,7 @@ def measure_config1(args, ws):
     plane-wave solve to 1e-6 (FP64 products inside GMRES), wall time per solve."""
     import torch
     from synth import workloads, planewave_batch
-    from paper_2009_02281_gb300 import Context, EFIE, F64
+    from paper_2009_02281_gb300 import Context, EFIE, F32, F64
     wl = workloads.pec_sphere_1920()
     t0 = time.time()
     ctx = Context(wl["xyz"], wl["tri"], wl["grid_n"], order=wl["order"], formulation=EFIE, near_radius=wl["radius"])
@@ -281,6 +305,32 @@ def measure_config1(args, ws):
         "converged": sum(1 for q in mst if q["status"] == 0),
         "iterations_mean": round(float(np.mean([q["iterations"] for q in mst])), 1),
         "max_rel_residual": max(q["rel_residual"] for q in mst), "status": mrc}
+    # the batched sweep: all 100 frequencies in one call (device-side GMRES, one CUDA graph per
+    # cycle, one product per Arnoldi step for every open system); right-hand sides included
+    batched = {}
+    for label, inner, mb, warm in (("fp64", F64, 0, False), ("fp32_products_in_fp64_refinement", F32, 0, False),
+                                   ("fp64_warm_half_batch", F64, 50, True),
+                                   ("fp32_warm_half_batch", F32, 50, True)):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        Bb = torch.stack([ctx.rhs_planewave(fq, [[0.0, 0.0, 1.0]], [[1.0, 0.0, 0.0]]) for fq in freqs])
+        _, bst, brc, cnt = ctx.sweep_batched(freqs, Bb, tol=1e-6, inner_precision=inner, max_iter=3000,
+                                             max_batch=mb, warm_start=warm)
+        torch.cuda.synchronize()
+        bs_s = time.perf_counter() - t
+        flat = [q for row in bst for q in row]
+        batched[label] = {"wall_s": round(bs_s, 3), "solves_per_s": round(ws * len(freqs) / bs_s, 2),
+                          "max_iter": 3000, "max_batch": mb or len(freqs),
+                          "initial_guess": "converged neighbour frequency" if warm else "zero",
+                          "converged": sum(1 for q in flat if q["status"] == 0),
+                          "iterations_mean": round(float(np.mean([q["iterations"] for q in flat])), 1),
+                          "max_rel_residual": max(q["rel_residual"] for q in flat), "status": brc,
+                          "cycles": cnt[0], "graphs_captured": cnt[1], "batched_products": cnt[2]}
+    sweep["batched"] = batched
+    best64 = min(batched["fp64"]["wall_s"], batched["fp64_warm_half_batch"]["wall_s"])
+    best32 = min(batched["fp32_products_in_fp64_refinement"]["wall_s"], batched["fp32_warm_half_batch"]["wall_s"])
+    sweep["batched"]["speedup_over_per_frequency_fp64"] = round(sweep_s / best64, 2)
+    sweep["batched"]["speedup_over_per_frequency_fp32"] = round(mixed_s / best32, 2)
     # the same sweep with the conventional AIM (Sec. II-B): the near entries are integrated
     # directly and precorrected again at every frequency (the paper's per-frequency matrix fill)
     aim_cmp = None
@@ -371,12 +421,46 @@ def measure_config3(args, ws):
         per.append(e0.elapsed_time(e1) / 5)
     ms = float(np.median(per))
     info = ctx.info
+    # the sweep itself: the charge-form scalar potential (the RWG form stalls near 3e-2 on these
+    # bars), the 8 unit-voltage port excitations, every tenth frequency of the 100-point log sweep,
+    # all systems in one batched solve (FP64 inner products: the FP32 ones level off at ~1.2e-5)
+    sweep = None
+    if not args.no_config3_sweep:
+        from paper_2009_02281_gb300 import Port, F64
+        ports = [Port.make(*p) for p in wl["ports"]]
+        t = time.time()
+        ctx.set_charge_form(True)
+        torch.cuda.synchronize()
+        charge_setup_s = time.time() - t
+        fs = np.asarray(wl["freqs"])[::10]
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        b1 = ctx.rhs_ports(ports)
+        Bb = b1.unsqueeze(0).repeat(len(fs), 1, 1).contiguous()
+        X, bst, brc, cnt = ctx.sweep_batched(fs, Bb, tol=1e-5, restart=100, max_iter=args.config3_max_iter,
+                                             inner_precision=F64)
+        torch.cuda.synchronize()
+        sw_s = time.perf_counter() - t
+        Y = np.stack([ctx.port_currents(ports, X[i]) for i in range(len(fs))])   # [f][excited][measured]
+        conv_f = [i for i in range(len(fs)) if all(q["status"] == 0 for q in bst[i])]
+        asym = [float(np.linalg.norm(Y[i] - Y[i].T) / np.linalg.norm(Y[i])) for i in conv_f]
+        nconv = sum(1 for row in bst for q in row if q["status"] == 0)
+        sweep = {"formulation": "EFIE, charge-form scalar potential, surface impedance", "ports": len(ports),
+                 "frequencies_hz": [float(v) for v in fs], "systems": len(fs) * len(ports),
+                 "tol": 1e-5, "max_iter": args.config3_max_iter, "wall_s": round(sw_s, 2),
+                 "converged": nconv, "sweep_solves_per_s": round(ws * nconv / sw_s, 3),
+                 "converged_frequencies_hz": [float(fs[i]) for i in conv_f],
+                 "iterations_per_frequency": [int(np.mean([q["iterations"] for q in row])) for row in bst],
+                 "max_rel_residual_per_frequency": [float("%.3g" % max(q["rel_residual"] for q in row))
+                                                    for row in bst],
+                 "y_reciprocity_max": max(asym) if asym else None,
+                 "charge_setup_s": round(charge_setup_s, 2), "cycles": cnt[0], "graphs_captured": cnt[1],
+                 "status": brc}
     ctx.close()
     return {"workload": wl["name"], "n_unknowns": info["n_unknowns"], "near_nnz": info["near_nnz"],
             "grid": list(info["grid_n"]), "padded": list(info["pad"]), "setup_s": round(setup_s, 2),
             "rhs": nrhs, "ms_per_product": round(ms, 3), "value": round(ws * nrhs / (ms * 1e-3), 2), "unit": UNIT,
-            "freqs_hz": freqs, "schedule": tune["best"] if tune else None,
-            "solves": "not timed: plain-EFIE GMRES stalls on this mesh (see the design notes)"}
+            "freqs_hz": freqs, "schedule": tune["best"] if tune else None, "sweep": sweep}
 
 
 def learned_eval(args):
@@ -1042,6 +1126,9 @@ def main():
     ap.add_argument("--no-config1", action="store_true", help="skip the 1920-unknown FP64 latency measurement")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default product schedules")
     ap.add_argument("--no-config3", action="store_true", help="skip the copper-bar product measurement")
+    ap.add_argument("--no-config3-sweep", action="store_true", help="skip the copper-bar batched port sweep")
+    ap.add_argument("--config3-max-iter", type=int, default=800,
+                    help="GMRES iteration cap per system of the copper-bar sweep")
     ap.add_argument("--no-cfie", action="store_true", help="skip the CFIE sweep of the 1920-unknown sphere")
     ap.add_argument("--no-aim", action="store_true",
                     help="skip the conventional-AIM sweep of the 1920-unknown sphere")

@@ -294,12 +294,17 @@ int aimx_sweep(aimx_ctx* ctx, int nf, const double* freqs, int nwave, const doub
  *     frequency per pass).  opts->precond: AIMX_PRECOND_DIAG or _NONE, others
  *     AIMX_E_STATE; AIMX_E_STATE in the conventional-AIM mode.  The linear term
  *     and the charge form apply.
+ *   - warm_start = 1: systems are admitted with even frequency indices first,
+ *     and each later system starts from the converged solution of the same
+ *     right-hand side at the nearest frequency (with max_batch below nf x nrhs
+ *     the odd frequencies then start next to converged neighbours); ignored
+ *     with opts->use_x0 (the caller's guesses are kept).
  *   - counters (host int64 [3] or NULL): cycles, graphs captured, batched
  *     products.  Returns AIMX_E_NOCONV if any system missed tol.  Runs on a
  *     private stream ordered after `stream`; synchronous on return. */
 int aimx_sweep_batched(aimx_ctx* ctx, int nf, const double* freqs, int nrhs, const void* B, void* X,
-                       const aimx_solve_opts* opts, int max_batch, aimx_solve_stats* stats, int64_t* counters,
-                       void* stream);
+                       const aimx_solve_opts* opts, int max_batch, int warm_start, aimx_solve_stats* stats,
+                       int64_t* counters, void* stream);
 
 /* Select the matvec implementation: 0 = automatic (FP32: the plane-fused
  * path whenever the grid is padded to exactly twice a power-of-two size per
@@ -432,6 +437,15 @@ int aimx_get_schedule(const aimx_ctx* ctx, aimx_schedule* s);
  * out leaves that product's output incomplete; 0 is the normal answer.
  * Synchronous. */
 int aimx_wait_timeouts(int* count);
+
+/* Test hook: the limit, in SM clock cycles, of the per-tile copy wait of the
+ * variant-3 z-pass (default about 2e9, a second); cycles <= 0 restores the
+ * default.  A short limit makes that wait run out, so a test can check the
+ * timeout path (aimx_wait_timeouts > 0, the product's output incomplete, the
+ * context still usable).  The wait that drains the copy still in flight after
+ * a timeout always keeps the full bound, so no block exits with a bulk copy
+ * outstanding.  Process-wide on the current device.  Synchronous. */
+int aimx_set_wait_limit(int64_t cycles);
 
 /* Time the FP32 product of nrhs right-hand sides at freq under every candidate
  * schedule (the variants the grid allows x passes {all, nrhs/2, nrhs/4 with at
@@ -582,6 +596,17 @@ int aimx_batch_create(int n, aimx_ctx* const* ctxs, int nstreams, aimx_batch** o
 int aimx_batch_destroy(aimx_batch* b);
 int aimx_batch_matvec(aimx_batch* b, const double* freqs, const int* nrhs, const void* const* x, void* const* y,
                       void* stream);
+/* Solve A_i(k_i) x_i = b_i for every member i (the members' own aimx_solve with
+ * the shared opts): member i runs on internal stream i % nstreams, driven by
+ * one host thread per internal stream, so the members' solves overlap on the
+ * GPU.  freqs [n], nrhs [n]; B[i], X[i]: device complex128 [nrhs[i]][nunk_i]
+ * of member i (X[i] an initial guess when opts->use_x0); stats: host array of
+ * n pointers, each to [nrhs[i]] aimx_solve_stats (or NULL), or NULL.  Ordered
+ * after `stream`, which is ordered after the batch; synchronous on return.
+ * Returns the first member error (aimx_batch_last_error names the member),
+ * else AIMX_E_NOCONV if any member missed tol, else AIMX_OK. */
+int aimx_batch_solve(aimx_batch* b, const double* freqs, const int* nrhs, const void* const* B, void* const* X,
+                     const aimx_solve_opts* opts, aimx_solve_stats* const* stats, void* stream);
 int64_t aimx_batch_graph_nodes(const aimx_batch* b);      /* nodes of the captured graph (0 before the first call) */
 const char* aimx_batch_last_error(const aimx_batch* b);
 

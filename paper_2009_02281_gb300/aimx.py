@@ -96,6 +96,7 @@ _SIGS = [
     ("aimx_set_schedule", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("aimx_get_schedule", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("aimx_wait_timeouts", ctypes.c_int, [ctypes.c_void_p]),
+    ("aimx_set_wait_limit", ctypes.c_int, [ctypes.c_int64]),
     ("aimx_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_char_p, ctypes.c_void_p,
                                      ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     ("aimx_export_aim_near", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p]),
@@ -119,9 +120,11 @@ _SIGS = [
                                   ctypes.c_void_p]),
     ("aimx_sweep_batched", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
-                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+                                          ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("aimx_precond_apply", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("aimx_batch_solve", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("aimx_batch_create", ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_void_p)]),
     ("aimx_batch_destroy", ctypes.c_int, [ctypes.c_void_p]),
@@ -225,6 +228,13 @@ def wait_timeouts():
     if rc != 0:
         raise AimxError(rc)
     return n.value
+
+
+def set_wait_limit(cycles):
+    """Test hook (aimx_set_wait_limit): per-tile copy-wait limit of the TMA z-pass; <= 0 restores the default."""
+    rc = load().aimx_set_wait_limit(int(cycles))
+    if rc != 0:
+        raise AimxError(rc)
 
 
 def measure_fp32_peak(packed=False):
@@ -418,7 +428,7 @@ class Context:
         return X, _stats_list(st), rc
 
     def sweep_batched(self, freqs, B, tol=1e-6, restart=50, max_iter=1000, inner_precision=F32,
-                      precond=PRECOND_DIAG, max_batch=0, x0=None, stream=None):
+                      precond=PRECOND_DIAG, max_batch=0, warm_start=False, x0=None, stream=None):
         """Solve A(k_f) x = b for every frequency f and RHS at once (aimx_sweep_batched).
 
         B: CUDA complex128 [nf, nrhs, nunk].  Returns (X, stats [nf][nrhs], rc, counters) with
@@ -433,7 +443,7 @@ class Context:
         o = _opts(tol, restart, max_iter, inner_precision, precond, 1 if x0 is not None else 0, 0, 0)
         rc = self._check(self._lib.aimx_sweep_batched(self._ctx, nf, _ptr(freqs), nrhs, ctypes.c_void_p(B.data_ptr()),
                                                       ctypes.c_void_p(X.data_ptr()), ctypes.byref(o), int(max_batch),
-                                                      st, _ptr(cnt), _stream_handle(stream)))
+                                                      1 if warm_start else 0, st, _ptr(cnt), _stream_handle(stream)))
         stats = _stats_list(st)
         return X, [stats[f * nrhs:(f + 1) * nrhs] for f in range(nf)], rc, tuple(int(v) for v in cnt)
 
@@ -755,6 +765,26 @@ class Batch:
         if rc != 0:
             raise AimxError(rc, (self._lib.aimx_batch_last_error(self._b) or b"").decode())
         return ys
+
+    def solve(self, freqs, bs, tol=1e-6, restart=50, max_iter=1000, inner_precision=F32, precond=PRECOND_DIAG,
+              stream=None):
+        """Solve every member (aimx_batch_solve): bs[i] complex128 CUDA [nrhs_i, n_unknowns_i].
+        Returns (xs, stats per member, status)."""
+        import torch
+        n = len(self.contexts)
+        bs = [b.contiguous() for b in bs]
+        xs = [torch.empty_like(b) for b in bs]
+        f = (ctypes.c_double * n)(*[float(v) for v in freqs])
+        nr = (ctypes.c_int * n)(*[int(b.shape[0]) for b in bs])
+        bp = (ctypes.c_void_p * n)(*[b.data_ptr() for b in bs])
+        xp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+        st = [(_SolveStats * int(b.shape[0]))() for b in bs]
+        sp = (ctypes.c_void_p * n)(*[ctypes.addressof(a) for a in st])
+        o = _opts(tol, restart, max_iter, inner_precision, precond)
+        rc = self._lib.aimx_batch_solve(self._b, f, nr, bp, xp, ctypes.byref(o), sp, _stream_handle(stream))
+        if rc < 0:
+            raise AimxError(rc, (self._lib.aimx_batch_last_error(self._b) or b"").decode())
+        return xs, [_stats_list(a) for a in st], rc
 
     @property
     def graph_nodes(self):

@@ -7,6 +7,7 @@
 // and host round trips per mesh.
 
 #include <algorithm>
+#include <thread>
 #include <vector>
 
 #include "aimx_internal.h"
@@ -178,6 +179,54 @@ int aimx_batch_matvec(aimx_batch* b, const double* freqs, const int* nrhs, const
         return e.code;
     }
     return AIMX_OK;
+}
+
+// Solve every member's systems: member i on internal stream i % k, driven by host thread i % k
+// (aimx_solve synchronises its stream at every Arnoldi step, so one thread per stream lets the
+// members' GPU work overlap).  The work is ordered after `stream`, and `stream` after it.
+int aimx_batch_solve(aimx_batch* b, const double* freqs, const int* nrhs, const void* const* B, void* const* X,
+                     const aimx_solve_opts* opts, aimx_solve_stats* const* stats, void* stream) {
+    if (!b || !freqs || !nrhs || !B || !X) return AIMX_E_ARG;
+    const int n = (int)b->ctx.size();
+    for (int i = 0; i < n; ++i)
+        if (!(freqs[i] > 0) || nrhs[i] <= 0 || !B[i] || !X[i]) {
+            b->last_error = "aimx_batch_solve: bad member argument " + std::to_string(i);
+            return AIMX_E_ARG;
+        }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaEventRecord(b->fork, s) != cudaSuccess) {
+        cudaGetLastError();
+        b->last_error = "aimx_batch_solve: could not order the batch after the caller's stream";
+        return AIMX_E_CUDA;
+    }
+    const int k = (int)b->streams.size();
+    for (int t = 0; t < k; ++t) cudaStreamWaitEvent(b->streams[t], b->fork, 0);
+    std::vector<int> rc(n, AIMX_OK);
+    auto work = [&](int t) {
+        cudaSetDevice(dev);
+        for (int i = t; i < n; i += k)
+            rc[i] = aimx_solve(b->ctx[i], freqs[i], nrhs[i], B[i], X[i], opts, stats ? stats[i] : nullptr,
+                               b->streams[t]);
+    };
+    std::vector<std::thread> th;
+    for (int t = 1; t < k; ++t) th.emplace_back(work, t);
+    work(0);
+    for (auto& x : th) x.join();
+    int worst = AIMX_OK;
+    for (int i = 0; i < n; ++i) {
+        if (rc[i] < 0 && worst >= 0) {
+            worst = rc[i];
+            b->last_error = "member " + std::to_string(i) + ": " + aimx_last_error(b->ctx[i]);
+        } else if (rc[i] > 0 && worst == AIMX_OK) {
+            worst = rc[i];
+        }
+    }
+    for (int t = 0; t < k; ++t) {
+        cudaEventRecord(b->done[t], b->streams[t]);
+        cudaStreamWaitEvent(s, b->done[t], 0);
+    }
+    return worst;
 }
 
 int64_t aimx_batch_graph_nodes(const aimx_batch* b) { return b ? (int64_t)b->nodes : 0; }

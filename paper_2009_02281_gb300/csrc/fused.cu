@@ -777,13 +777,40 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
         : "memory");
     return ok != 0;
 }
-// bounded wait on phase `parity`: false after ~2e9 cycles (about a second)
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+// non-blocking probe of phase `parity`
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait on phase `parity`: false after `limit` cycles (~2e9: about a second).  try_wait
+// may suspend the thread for a hardware-chosen time before it reports false, so a limit
+// shortened below the default (the test hook) polls with the non-blocking test_wait instead.
+constexpr long long kWaitLimit = 2000000000LL;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, long long limit = kWaitLimit) {
     const long long t0 = clock64();
+    if (limit < kWaitLimit) {
+        while (!mbar_test_wait(bar, parity))
+            if (clock64() - t0 > limit) return false;
+        return true;
+    }
     while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > 2000000000LL) return false;
+        if (clock64() - t0 > limit) return false;
     return true;
 }
+
+// limit of the per-tile copy wait (aimx_set_wait_limit shortens it to make the wait run out in a
+// test; the drain wait after a timeout always keeps the full bound)
+__device__ long long g_tile_wait_limit = kWaitLimit;
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
                                             uint64_t* bar) {
@@ -835,7 +862,7 @@ __global__ void __launch_bounds__(2 * F * 8) k_zpass_tma(const __grid_constant__
     unsigned parity = 0;
     bool failed = false;
     for (; t < T; t += gridDim.x) {
-        const bool ok = mbar_wait_bounded(bar, parity);
+        const bool ok = mbar_wait_bounded(bar, parity, g_tile_wait_limit);
         if (__syncthreads_or(!ok)) {
             failed = true;
             break;
@@ -859,7 +886,7 @@ __global__ void __launch_bounds__(2 * F * 8) k_zpass_tma(const __grid_constant__
     }
     if (failed && threadIdx.x == 0) {
         atomicAdd(&g_wait_timeouts, 1);
-        mbar_wait_bounded(bar, parity);                    // the copy still in flight, bounded
+        mbar_wait_bounded(bar, parity, kWaitLimit);        // the copy still in flight, full bound
     }
 }
 
@@ -1425,6 +1452,15 @@ void matvec_fused_into(aimx_ctx* ctx, double freq, int B, const float* x, float*
 }
 
 }  // namespace aimx
+
+extern "C" int aimx_set_wait_limit(int64_t cycles) {
+    const long long v = cycles > 0 ? (long long)cycles : aimx::kWaitLimit;
+    if (cudaMemcpyToSymbol(aimx::g_tile_wait_limit, &v, sizeof(v)) != cudaSuccess) {
+        cudaGetLastError();
+        return AIMX_E_CUDA;
+    }
+    return AIMX_OK;
+}
 
 extern "C" int aimx_wait_timeouts(int* count) {
     if (!count) return AIMX_E_ARG;

@@ -200,7 +200,6 @@ struct BatchSweep {
             matvec_generic_multi<float>(ctx, multi(prec), S, (const float*)x, (float*)yv, s);
         else
             matvec_generic_multi<double>(ctx, multi(prec), S, (const double*)x, (double*)yv, s);
-        ++products;
     }
     // r = BS - A XS and |r| per slot
     void residual(bool low) {
@@ -270,8 +269,8 @@ struct BatchSweep {
 using namespace aimx;
 
 extern "C" int aimx_sweep_batched(aimx_ctx* ctx, int nf, const double* freqs, int nrhs, const void* Bdev, void* Xdev,
-                                  const aimx_solve_opts* opts_in, int max_batch, aimx_solve_stats* stats,
-                                  int64_t* counters, void* stream) {
+                                  const aimx_solve_opts* opts_in, int max_batch, int warm_start,
+                                  aimx_solve_stats* stats, int64_t* counters, void* stream) {
     if (!ctx) return AIMX_E_ARG;
     if (nf <= 0 || !freqs || nrhs <= 0 || !Bdev || !Xdev || max_batch < 0) {
         ctx->last_error = "aimx_sweep_batched: bad argument";
@@ -399,6 +398,26 @@ extern "C" int aimx_sweep_batched(aimx_ctx* ctx, int nf, const double* freqs, in
         std::vector<double> relres(nsys, 1.0);
         bool low = o.inner_precision == AIMX_F32 && o.tol >= 1e-5;
         int S = S0, next = 0;
+        // admission order: frequency-major; with warm starts even frequency indices first, so that
+        // the odd ones enter next to converged neighbours whose solutions start them
+        std::vector<int> order;
+        order.reserve(nsys);
+        for (int par = 0; par < (warm_start ? 2 : 1); ++par)
+            for (int f = warm_start ? par : 0; f < nf; f += warm_start ? 2 : 1)
+                for (int wv = 0; wv < nrhs; ++wv) order.push_back(f * nrhs + wv);
+        auto warm = [&](int q) {
+            // the converged system of the same right-hand side at the nearest frequency
+            const int f = q / nrhs, wv = q % nrhs;
+            int best = -1;
+            for (int d = 1; d < nf && best < 0; ++d)
+                for (int f2 : {f - d, f + d})
+                    if (f2 >= 0 && f2 < nf && best < 0 &&
+                        (state[f2 * nrhs + wv] == DONE || state[f2 * nrhs + wv] == DONE32))
+                        best = f2 * nrhs + wv;
+            if (best >= 0)
+                AIMX_CUDA_TRY(cudaMemcpyAsync(X + (size_t)q * nunk, X + (size_t)best * nunk, sizeof(double2) * nunk,
+                                              cudaMemcpyDeviceToDevice, ps));
+        };
         std::vector<int> slot_sys(S0, -1), hmap(S0), hfidx(S0), hk(S0);
         std::vector<double> hrel(S0);
         bool changed = true;
@@ -426,10 +445,12 @@ extern "C" int aimx_sweep_batched(aimx_ctx* ctx, int nf, const double* freqs, in
                         changed = true;
                     }
                     if (slot_sys[sl] < 0) {
-                        while (next < nsys && state[next] != PENDING) ++next;
+                        while (next < nsys && state[order[next]] != PENDING) ++next;
                         if (next < nsys) {
-                            slot_sys[sl] = next;
-                            state[next++] = ACTIVE;
+                            const int q = order[next++];
+                            if (warm_start && !o.use_x0 && pass == 0) warm(q);
+                            slot_sys[sl] = q;
+                            state[q] = ACTIVE;
                             changed = true;
                         }
                     }
@@ -449,6 +470,7 @@ extern "C" int aimx_sweep_batched(aimx_ctx* ctx, int nf, const double* freqs, in
                 if (changed) {
                     upload_slots();
                     bs.residual(low);
+                    ++bs.products;
                     changed = false;
                 }
                 if (!bs.exec || bs.graph_S != S || bs.graph_low != (int)low) {
@@ -483,6 +505,7 @@ extern "C" int aimx_sweep_batched(aimx_ctx* ctx, int nf, const double* freqs, in
                 }
                 AIMX_CUDA_TRY(cudaGraphLaunch(bs.exec, ps));
                 ++bs.cycles;
+                bs.products += m + 1;          // m Arnoldi products and the closing residual
                 AIMX_CUDA_TRY(cudaMemcpyAsync(hrel.data(), bs.rel, sizeof(double) * S, cudaMemcpyDeviceToHost, ps));
                 AIMX_CUDA_TRY(cudaMemcpyAsync(hk.data(), bs.kused, sizeof(int) * S, cudaMemcpyDeviceToHost, ps));
                 AIMX_CUDA_TRY(cudaStreamSynchronize(ps));
@@ -506,6 +529,7 @@ extern "C" int aimx_sweep_batched(aimx_ctx* ctx, int nf, const double* freqs, in
                 for (int sl = 0; sl < S; ++sl) slot_sys[sl] = q0 + sl < nsys ? q0 + sl : -1;
                 upload_slots();
                 bs.residual(false);
+                ++bs.products;
                 k_relres<<<(unsigned)((S + 127) / 128), 128, 0, ps>>>(S, bs.rnorm, bs.bnorm, bs.rel);
                 AIMX_CUDA_TRY(cudaMemcpyAsync(hrel.data(), bs.rel, sizeof(double) * S, cudaMemcpyDeviceToHost, ps));
                 AIMX_CUDA_TRY(cudaStreamSynchronize(ps));

@@ -103,3 +103,36 @@ def test_batch_rejects_bad_arguments(torch_cuda):
     batch.close()
     for m in ms:
         m[0].close()
+
+
+def test_batch_solve_matches_member_solves(torch_cuda):
+    """aimx_batch_solve (members' GMRES overlapped on internal streams and host threads) gives
+    each member what its own aimx_solve gives, with the reported true residuals within tol."""
+    torch = torch_cuda
+    from synth import planewave_batch
+    from paper_2009_02281_gb300 import Batch
+    ms = _members()
+    ctxs = [m[0] for m in ms]
+    freqs = [m[1] for m in ms]
+    bs = []
+    for i, (c, f, nr) in enumerate(ms):
+        dirs, pols = planewave_batch(nr, seed=40 + i)
+        bs.append(c.rhs_planewave(f, dirs, pols))
+    tol = 1e-6
+    batch = Batch(ctxs, nstreams=3)
+    xs, stats, rc = batch.solve(freqs, bs, tol=tol, restart=60, max_iter=3000)
+    worst = 0
+    for i, (c, f, nr) in enumerate(ms):
+        x, st, rc1 = c.solve(f, bs[i], tol=tol, restart=60, max_iter=3000)
+        worst = max(worst, rc1)
+        # the same solver on the same data: the same iterations, residuals and solutions
+        assert [s["iterations"] for s in stats[i]] == [s["iterations"] for s in st], i
+        for s, s1 in zip(stats[i], st):
+            assert s["status"] == s1["status"]
+            assert s["status"] != 0 or s["rel_residual"] <= tol
+        a, b = xs[i].cpu().numpy(), x.cpu().numpy()
+        assert np.linalg.norm(a - b) <= 1e-10 * np.linalg.norm(b), i
+    assert rc == worst
+    batch.close()
+    for c in ctxs:
+        c.close()

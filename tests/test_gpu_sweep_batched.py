@@ -160,3 +160,26 @@ def test_no_preconditioner_and_errors(efie12, torch_cuda):
     # a cap that is too small is a positive warning with per-system status
     X, stats, rc, _ = ctx.sweep_batched(freqs, B, tol=1e-13, restart=3, max_iter=3)
     assert rc == 1 and all(s["status"] == 1 for row in stats for s in row)
+
+
+def test_warm_start_fewer_iterations(efie12, torch_cuda):
+    """Interleaved admission with warm starts from converged neighbours: the same solutions
+    (dense LU), fewer iterations in total than cold starts."""
+    torch = torch_cuda
+    from oracle import operator as op, solve as osolve
+    ctx, prob = efie12
+    freqs = np.linspace(0.8, 1.6, 12) * C0 / (2 * np.pi)
+    d, p = [[0.0, 0.0, 1.0]], [[1.0, 0.0, 0.0]]
+    B = _rhs_all(ctx, freqs, d, p, torch)
+    tol = 1e-9
+    Xc, sc, rc, _ = ctx.sweep_batched(freqs, B, tol=tol, restart=40, max_batch=6)
+    Xw, sw, rw, _ = ctx.sweep_batched(freqs, B, tol=tol, restart=40, max_batch=6, warm_start=True)
+    assert rc == 0 and rw == 0
+    cold = sum(s["iterations"] for row in sc for s in row)
+    warm = sum(s["iterations"] for row in sw for s in row)
+    assert warm < cold, (warm, cold)
+    Xh = Xw.cpu().numpy()
+    for i in (0, 5, 11):
+        Z = op.dense_efie(prob, freqs[i])
+        ref = osolve.lu_solve(Z, _oracle_rhs(prob, freqs[i], d[0], p[0]))
+        assert _rel(Xh[i, 0], ref) <= 1e-4
