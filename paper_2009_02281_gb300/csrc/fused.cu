@@ -893,7 +893,7 @@ __global__ void __launch_bounds__(2 * F * 8) k_zpass_tma(const __grid_constant__
 // K4 (register form): inverse of K2 plus the interpolation partials.
 // Charge form (tpart given, EFIE): the rho field's output plane is interpolated with the pulse
 // weights per triangle touching the plane (partials tpart[b][slot][t]) instead of per basis.
-template <int N>
+template <int N, bool CHG>
 __global__ void __launch_bounds__(2 * N) k_xy_inv_reg(const float2* __restrict__ S, const float* __restrict__ w,
                                                       const int* __restrict__ anc, const int* __restrict__ plane_lo,
                                                       const int* __restrict__ plane_hi, float2* part, int F, int Nz,
@@ -958,7 +958,7 @@ __global__ void __launch_bounds__(2 * N) k_xy_inv_reg(const float2* __restrict__
             for (int x = 0; x < N; ++x) O[r * PITCH + x] = O[r * PITCH + x] + v[x];
         }
         __syncthreads();
-        if (tpart && f == 3) {
+        if (CHG && f == 3) {
             // charge form: triangle partials of the rho field, one per (triangle, stencil slot)
             const int tlo = tplane[z], thi = tplane[Nz + z];
             for (int k = tlo + threadIdx.x; k < thi; k += blockDim.x) {
@@ -1070,11 +1070,18 @@ template <int N>
 static void launch_xy_inv_reg(const aimx_ctx* ctx, const float2* S, const int* plo, const int* phi, float2* part,
                               int B, cudaStream_t s) {
     size_t sm = (2 * (size_t)N * (N + 1) + 2 * (size_t)ctx->max_plane_bases) * sizeof(float2);
-    set_smem(k_xy_inv_reg<N>, sm);
-    const bool chg = ctx->charge != 0;
-    k_xy_inv_reg<N><<<dim3(ctx->n[2], ctx->F / 4, B), 2 * N, sm, s>>>(
-        S, ctx->d_wsoa, ctx->d_anc, plo, phi, part, ctx->F, ctx->n[2], ctx->N, ctx->P, ctx->d_tanc, ctx->d_tplane,
-        ctx->d_lp_soa, chg ? reinterpret_cast<float2*>(ctx->d_tpart) : nullptr, ctx->nt);
+    const dim3 grid(ctx->n[2], ctx->F / 4, B);
+    if (ctx->charge) {
+        set_smem(k_xy_inv_reg<N, true>, sm);
+        k_xy_inv_reg<N, true><<<grid, 2 * N, sm, s>>>(S, ctx->d_wsoa, ctx->d_anc, plo, phi, part, ctx->F, ctx->n[2],
+                                                       ctx->N, ctx->P, ctx->d_tanc, ctx->d_tplane, ctx->d_lp_soa,
+                                                       reinterpret_cast<float2*>(ctx->d_tpart), ctx->nt);
+    } else {
+        set_smem(k_xy_inv_reg<N, false>, sm);
+        k_xy_inv_reg<N, false><<<grid, 2 * N, sm, s>>>(S, ctx->d_wsoa, ctx->d_anc, plo, phi, part, ctx->F,
+                                                        ctx->n[2], ctx->N, ctx->P, nullptr, nullptr, nullptr, nullptr,
+                                                        ctx->nt);
+    }
 }
 
 template <int NZ, int F>
