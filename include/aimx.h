@@ -100,8 +100,9 @@ typedef struct {
  * m = floor((order + 1) / 2); an axis along which the mesh is flat takes the
  * largest spacing of the other axes.  When h is given, origin must be given too.
  * near_radius: near-region radius in cells (Chebyshev distance of stencil
- * anchors), 0 = 3.  pad: zero-padded FFT length per axis, 0 = smallest power
- * of two >= 2 n_a - 1 (any value >= 2 n_a - 1 gives the same product). */
+ * anchors), 0 = 3.  pad: zero-padded FFT length per axis, of the form 2^k or
+ * 3 * 2^k, >= 2 n_a - 1 and <= 4096; 0 = the smallest such length (any valid
+ * value gives the same product). */
 typedef struct {
     int32_t n[3];
     double h[3];

@@ -19,7 +19,8 @@ constexpr double kEps0 = 1.0 / (kMu0 * kC0 * kC0);
 constexpr double kEta0 = kMu0 * kC0;
 
 constexpr int kMaxQuad = 64;        // points of the largest triangle rule kept on the device
-constexpr int kTwiddleLen = 4096;   // largest power-of-two FFT length supported
+constexpr int kTwiddleLen = 4096;   // largest FFT length supported (2^k or 3 * 2^k)
+constexpr int kTwiddleTab = 3 * kTwiddleLen;   // device twiddle table length: every supported length divides it
 
 template <class T>
 struct Cplx;

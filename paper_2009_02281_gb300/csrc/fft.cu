@@ -36,11 +36,11 @@ static int tw_device() {
 static void init_twiddles(int dev) {
     std::lock_guard<std::mutex> lock(g_tw_mutex);
     if (g_tw64[dev]) return;
-    const int H = kTwiddleLen;   // full circle: e^{-2 pi i k / 4096}, k < 4096
+    const int H = kTwiddleTab;   // full circle: e^{-2 pi i k / 12288}, k < 12288
     std::vector<double2> t64(H);
     std::vector<float2> t32(H);
     for (int k = 0; k < H; ++k) {
-        double a = -2.0 * kPi * (double)k / (double)kTwiddleLen;
+        double a = -2.0 * kPi * (double)k / (double)kTwiddleTab;
         t64[k] = make_double2(std::cos(a), std::sin(a));
         t32[k] = make_float2((float)t64[k].x, (float)t64[k].y);
     }
@@ -76,30 +76,65 @@ const double2* twiddles<double>() {
     return twiddles64();
 }
 
-// ------------------------------------------------------------------ radix-2 FFT on smem lines
+// ------------------------------------------------------------------ FFT on smem lines, lengths 2^k and 3 * 2^k
 
 __device__ inline int bitrev(int v, int bits) { return (int)(__brev((unsigned)v) >> (32 - bits)); }
 
-// In-place iterative decimation-in-time FFT of nl lines (pitch elements apart)
-// that were loaded in bit-reversed order.  inv selects e^{+j..} twiddles.
+// Slot of input p in a shared-memory line before the in-place passes.  Length 2^k: bit-reversed
+// (decimation in time).  Length L = 3 P: the three decimated sequences x[3 n + r] are placed in
+// blocks r of P, each bit-reversed within its block.
+__device__ inline int fft_load_pos(int p, int L, int logP, int r3) {
+    if (!r3) return bitrev(p, logP);
+    return (p % 3) * (L / 3) + bitrev(p / 3, logP);
+}
+
+// In-place FFT of nl lines (pitch elements apart) loaded by fft_load_pos: radix-2
+// decimation-in-time passes over each block of P = 2^logP, then for L = 3 P one radix-3 pass
+// X[k + m P] = sum_r W_L^{r k} W_3^{r m} Y_r[k].  inv selects e^{+j..} twiddles.  tw: the
+// kTwiddleTab-point table e^{-2 pi i k / kTwiddleTab}.
 template <class C>
-__device__ void smem_fft_lines(C* s, int nl, int pitch, int L, int logL, bool inv, const C* tw) {
-    const int halfL = L >> 1;
-    for (int st = 1; st <= logL; ++st) {
+__device__ void smem_fft_lines(C* s, int nl, int pitch, int L, int logP, int r3, bool inv, const C* tw) {
+    const int P = r3 ? L / 3 : L, nsub = r3 ? 3 : 1;
+    const int halfP = P >> 1;
+    for (int st = 1; st <= logP; ++st) {
         const int half = 1 << (st - 1);
-        const int tstep = kTwiddleLen / (2 * half);
-        for (int idx = threadIdx.x; idx < nl * halfL; idx += blockDim.x) {
-            int l = idx / halfL, j = idx - l * halfL;
-            int pos = j & (half - 1);
-            int i0 = ((j >> (st - 1)) << st) + pos;
-            int i1 = i0 + half;
+        const int tstep = kTwiddleTab / (2 * half);
+        for (int idx = threadIdx.x; idx < nl * nsub * halfP; idx += blockDim.x) {
+            const int l = idx / (nsub * halfP), rem = idx - l * (nsub * halfP);
+            const int r = rem / halfP, j = rem - r * halfP;
+            const int pos = j & (half - 1);
+            const int i0 = ((j >> (st - 1)) << st) + pos;
+            const int i1 = i0 + half;
             C w = tw[pos * tstep];
             if (inv) w = conj(w);
-            C* line = s + l * pitch;
+            C* line = s + l * pitch + r * P;
             C b = w * line[i1];
             C a = line[i0];
             line[i0] = a + b;
             line[i1] = a - b;
+        }
+        __syncthreads();
+    }
+    if (r3) {
+        using R = decltype(C{}.x);
+        const R hs = (R)0.86602540378443864676;   // sqrt(3) / 2
+        const int step = kTwiddleTab / L;
+        for (int idx = threadIdx.x; idx < nl * P; idx += blockDim.x) {
+            const int l = idx / P, k = idx - l * P;
+            C* line = s + l * pitch;
+            C w1 = tw[k * step], w2 = tw[2 * k * step];
+            if (inv) {
+                w1 = conj(w1);
+                w2 = conj(w2);
+            }
+            const C a = line[k], b = w1 * line[k + P], c = w2 * line[k + 2 * P];
+            const C t = b + c, d = b - c;
+            const C m = a - (R)0.5 * t;
+            // forward: X1 = m - i hs d, X2 = m + i hs d (omega = e^{-2 pi i / 3}); inverse: conjugate
+            const C jd = inv ? mk(-hs * d.y, hs * d.x) : mk(hs * d.y, -hs * d.x);
+            line[k] = a + t;
+            line[k + P] = m + jd;
+            line[k + 2 * P] = m - jd;
         }
         __syncthreads();
     }
@@ -109,7 +144,7 @@ __device__ void smem_fft_lines(C* s, int nl, int pitch, int L, int logL, bool in
 // r = (a*D1 + b)*D2 + c.  RPB rows per block.
 template <class T>
 __global__ void k_fft_rows(cplx_t<T>* base, int64_t nrows, int D1, int D2, int64_t S1, int64_t S2,
-                           int64_t S3, int L, int logL, int RPB, int inv, const cplx_t<T>* tw) {
+                           int64_t S3, int L, int logP, int r3, int RPB, int inv, const cplx_t<T>* tw) {
     using C = cplx_t<T>;
     extern __shared__ unsigned char smraw[];
     C* s = reinterpret_cast<C*>(smraw);
@@ -121,10 +156,10 @@ __global__ void k_fft_rows(cplx_t<T>* base, int64_t nrows, int D1, int D2, int64
         int rr = idx / L, p = idx - rr * L;
         int64_t r = r0 + rr;
         int64_t c = r % D2, b = (r / D2) % D1, a = r / ((int64_t)D1 * D2);
-        s[rr * pitch + bitrev(p, logL)] = base[a * S1 + b * S2 + c * S3 + p];
+        s[rr * pitch + fft_load_pos(p, L, logP, r3)] = base[a * S1 + b * S2 + c * S3 + p];
     }
     __syncthreads();
-    smem_fft_lines<C>(s, nl, pitch, L, logL, inv != 0, tw);
+    smem_fft_lines<C>(s, nl, pitch, L, logP, r3, inv != 0, tw);
     for (int idx = threadIdx.x; idx < nl * L; idx += blockDim.x) {
         int rr = idx / L, p = idx - rr * L;
         int64_t r = r0 + rr;
@@ -137,7 +172,7 @@ __global__ void k_fft_rows(cplx_t<T>* base, int64_t nrows, int D1, int D2, int64
 // its points are S apart; each block takes TC consecutive x of one o.
 template <class T>
 __global__ void k_fft_cols(cplx_t<T>* base, int64_t nouter, int D1, int64_t S1, int64_t S2, int64_t S,
-                           int Mx, int L, int logL, int TC, int inv, const cplx_t<T>* tw) {
+                           int Mx, int L, int logP, int r3, int TC, int inv, const cplx_t<T>* tw) {
     using C = cplx_t<T>;
     extern __shared__ unsigned char smraw[];
     C* s = reinterpret_cast<C*>(smraw);
@@ -149,20 +184,23 @@ __global__ void k_fft_cols(cplx_t<T>* base, int64_t nouter, int D1, int64_t S1, 
     C* lb = base + (o / D1) * S1 + (o % D1) * S2 + x0;
     for (int idx = threadIdx.x; idx < nl * L; idx += blockDim.x) {
         int p = idx / nl, c = idx - p * nl;
-        s[c * pitch + bitrev(p, logL)] = lb[(int64_t)p * S + c];
+        s[c * pitch + fft_load_pos(p, L, logP, r3)] = lb[(int64_t)p * S + c];
     }
     __syncthreads();
-    smem_fft_lines<C>(s, nl, pitch, L, logL, inv != 0, tw);
+    smem_fft_lines<C>(s, nl, pitch, L, logP, r3, inv != 0, tw);
     for (int idx = threadIdx.x; idx < nl * L; idx += blockDim.x) {
         int p = idx / nl, c = idx - p * nl;
         lb[(int64_t)p * S + c] = s[c * pitch + p];
     }
 }
 
-static int ilog2(int v) {
-    int l = 0;
-    while ((1 << l) < v) ++l;
-    return l;
+// (log2 P, 1) for L = 3 * 2^logP, (log2 L, 0) for L = 2^logP
+static void fft_factors(int L, int& logP, int& r3) {
+    r3 = (L % 3 == 0) ? 1 : 0;
+    int P = r3 ? L / 3 : L;
+    logP = 0;
+    while ((1 << logP) < P) ++logP;
+    if ((1 << logP) != P) throw Error{AIMX_E_ARG, "FFT length must be 2^k or 3 * 2^k"};
 }
 
 template <class T>
@@ -176,7 +214,9 @@ static void fft_rows(cplx_t<T>* g, int64_t nrows, int D1, int D2, int64_t S1, in
         sm = (size_t)RPB * (L + 1) * sizeof(cplx_t<T>);
     }
     unsigned nb = (unsigned)((nrows + RPB - 1) / RPB);
-    k_fft_rows<T><<<nb, 256, sm, s>>>(g, nrows, D1, D2, S1, S2, S3, L, ilog2(L), RPB, inv ? 1 : 0,
+    int logP, r3;
+    fft_factors(L, logP, r3);
+    k_fft_rows<T><<<nb, 256, sm, s>>>(g, nrows, D1, D2, S1, S2, S3, L, logP, r3, RPB, inv ? 1 : 0,
                                       twiddles<T>());
     AIMX_CUDA_TRY(cudaGetLastError());
 }
@@ -191,7 +231,9 @@ static void fft_cols(cplx_t<T>* g, int64_t nouter, int D1, int64_t S1, int64_t S
     size_t sm = (size_t)TC * (L + 1) * sizeof(cplx_t<T>);
     int ntiles = (Mx + TC - 1) / TC;
     unsigned nb = (unsigned)(nouter * ntiles);
-    k_fft_cols<T><<<nb, 256, sm, s>>>(g, nouter, D1, S1, S2, S, Mx, L, ilog2(L), TC, inv ? 1 : 0,
+    int logP, r3;
+    fft_factors(L, logP, r3);
+    k_fft_cols<T><<<nb, 256, sm, s>>>(g, nouter, D1, S1, S2, S, Mx, L, logP, r3, TC, inv ? 1 : 0,
                                       twiddles<T>());
     AIMX_CUDA_TRY(cudaGetLastError());
 }

@@ -137,7 +137,7 @@ __device__ inline void dit_stage(float2* buf, int nlines, int lstride, int es, i
                                  const float2* __restrict__ tw) {
     const int Q = L / R;
     const int G = Gp * R;
-    const int tstep = kTwiddleLen / G;
+    const int tstep = kTwiddleTab / G;
     for (int item = threadIdx.x; item < nlines * Q; item += blockDim.x) {
         int line = item % nlines, j = item / nlines;
         int g = j / Gp, k = j - g * Gp;
@@ -165,7 +165,7 @@ __device__ inline void dif_stage(float2* buf, int nlines, int lstride, int es, i
                                  const float2* __restrict__ tw) {
     const int Tn = T / R;
     const int Q = L / R;
-    const int tstep = kTwiddleLen / T;
+    const int tstep = kTwiddleTab / T;
     for (int item = threadIdx.x; item < nlines * Q; item += blockDim.x) {
         int line = item % nlines, j = item / nlines;
         int blk = j / Tn, k = j - blk * Tn;

@@ -61,7 +61,7 @@ bool fused_supported(const aimx_ctx* ctx) {
 
 __device__ inline float2 twist(const float2* __restrict__ tw, int p, int n, int M) {
     if (!p) return make_float2(1.f, 0.f);
-    return __ldg(tw + (size_t)n * (kTwiddleLen / M));
+    return __ldg(tw + (size_t)n * (kTwiddleTab / M));
 }
 
 // ------------------------------------------------------------------ K0

@@ -391,6 +391,18 @@ static int next_pow2(int v) {
     return p;
 }
 
+// smallest FFT length >= v of the form 2^k or 3 * 2^k
+static int next_fft_len(int v) {
+    int p3 = 3;
+    while (p3 < v) p3 <<= 1;
+    return std::min(next_pow2(v), p3);
+}
+
+static bool fft_len_ok(int L) {
+    int P = (L % 3 == 0) ? L / 3 : L;
+    return P >= 1 && (P & (P - 1)) == 0;
+}
+
 // Gram values on the near pattern (FP64 and FP32) and their self terms, when a surface impedance is set
 static void build_gram(aimx_ctx* ctx, const GeomView& gv, const int* d_row_of) {
     if (!(ctx->sigma > 0) && ctx->form != AIMX_CFIE) return;
@@ -578,9 +590,9 @@ void setup_context(aimx_ctx* ctx, const aimx_mesh* mesh, const aimx_material* ma
             ctx->origin[a] = grid->origin[a];
         }
         int pmin = 2 * grid->n[a] - 1;
-        int pad = grid->pad[a] > 0 ? grid->pad[a] : next_pow2(pmin);
-        if (pad < pmin || (pad & (pad - 1)) || pad > kTwiddleLen)
-            throw Error{AIMX_E_ARG, "pad must be a power of two >= 2n-1 and <= 4096"};
+        int pad = grid->pad[a] > 0 ? grid->pad[a] : next_fft_len(pmin);
+        if (pad < pmin || !fft_len_ok(pad) || pad > kTwiddleLen)
+            throw Error{AIMX_E_ARG, "pad must be 2^k or 3 * 2^k, >= 2n-1 and <= 4096"};
         ctx->M[a] = pad;
     }
 

@@ -156,7 +156,7 @@ def test_setup_errors(torch_cuda):
 
 
 def test_config1_sized_efie(torch_cuda):
-    """1920-unknown PEC sphere on a 24^3 grid (padded to 64^3), every row checked."""
+    """1920-unknown PEC sphere on a 24^3 grid (padded to 48^3 = 3 * 16 per axis), every row checked."""
     torch = torch_cuda
     from synth import icosphere, random_complex
     from oracle import operator as op
@@ -196,3 +196,34 @@ def test_cufft_comparison_path_parity(efie_l2, pmchwt_l1, torch_cuda, form):
         ctx.set_path(0)
     assert _relerr(y64, ref) <= TOL64
     assert _relerr(y32, ref) <= TOL32
+
+
+@pytest.mark.parametrize("form", ["efie", "pmchwt"])
+def test_mixed_radix_pads(torch_cuda, form):
+    """FFT lengths 3 * 2^k: the default pad of a 12^3 grid is 24 per axis (radix 3 then radix 2);
+    explicit pads mixing 24, 32 and 48 per axis, and the power-of-two pad, give the oracle's
+    product (it sums over the grid directly and has no pad) in FP64 and FP32."""
+    torch = torch_cuda
+    from synth import icosphere, random_complex
+    from oracle import operator as op
+    from paper_2009_02281_gb300 import Context, EFIE, PMCHWT
+    xyz, tri = icosphere(2)
+    grid = (12, 12, 12)
+    prob = op.setup(xyz, tri, 2, grid, radius=3)
+    f = 1.3 * C0 / (2 * np.pi)
+    fm = EFIE if form == "efie" else PMCHWT
+    ref = None
+    for pad in (None, (24, 32, 48), (32, 32, 32), (48, 24, 24)):
+        ctx = Context(xyz, tri, grid, order=2, formulation=fm, eps_out=1.0, eps_in=4.0, pad=pad)
+        assert ctx.info["pad"] == (pad or (24, 24, 24))
+        x = random_complex((2, ctx.nunk), seed=91)
+        if ref is None:
+            if form == "efie":
+                ref = np.stack([op.matvec_efie(prob, f, xi) for xi in x])
+            else:
+                ref = np.stack([op.matvec_pmchwt(prob, f, xi, 1.0, 4.0) for xi in x])
+        y64 = ctx.matvec(f, torch.tensor(x, dtype=torch.complex128, device="cuda")).cpu().numpy()
+        y32 = ctx.matvec(f, torch.tensor(x, dtype=torch.complex64, device="cuda")).cpu().numpy()
+        ctx.close()
+        assert np.linalg.norm(y64 - ref) / np.linalg.norm(ref) <= 1e-9, pad
+        assert np.linalg.norm(y32 - ref) / np.linalg.norm(ref) <= 1e-5, pad

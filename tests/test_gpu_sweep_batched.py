@@ -49,7 +49,7 @@ def _oracle_rhs(prob, f, d, p, two_region=False):
 
 @pytest.fixture(scope="module")
 def efie12(torch_cuda):
-    """Level-2 icosphere, 12^3 grid (padded 32^3: the generic path)."""
+    """Level-2 icosphere, 12^3 grid (padded 24^3 = 3 * 8 per axis: the generic path)."""
     from synth import icosphere
     from oracle import operator as op
     from paper_2009_02281_gb300 import Context, EFIE, F32
