@@ -472,8 +472,13 @@ def learned_eval(args):
     from synth import workloads, planewave_batch
     from paper_2009_02281_gb300 import Context, EFIE, Gnn, PRECOND_DIAG, PRECOND_LEARNED
 
+    charge = args.learned_form == "charge"
+
     def make(w):
-        return Context(w["xyz"], w["tri"], w["grid_n"], order=2, formulation=EFIE, eps_out=1.0, sigma=w["sigma"])
+        c = Context(w["xyz"], w["tri"], w["grid_n"], order=2, formulation=EFIE, eps_out=1.0, sigma=w["sigma"])
+        if charge:
+            c.set_charge_form(True)
+        return c
 
     train_w = [workloads.copper_blocks(s, region=10e-3, footprint=(1e-3, 4e-3)) for s in range(8)]
     train = [make(w) for w in train_w]
@@ -485,7 +490,8 @@ def learned_eval(args):
     losses = net.fit(samples, steps=args.gnn_eval_steps, nprobe=8, lr=2e-3, clip=1.0, seed=1)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
-    out = {"train_layouts": len(train), "train_unknowns": [c.nunk for c in train], "train_freqs_ghz": [10, 25, 40],
+    out = {"scalar_potential": "charge form (D^T Pt D)" if charge else "RWG form",
+           "train_layouts": len(train), "train_unknowns": [c.nunk for c in train], "train_freqs_ghz": [10, 25, 40],
            "steps": args.gnn_eval_steps, "train_s": round(train_s, 2), "loss_first": round(losses[0], 4),
            "loss_last": round(float(np.mean(losses[-50:])), 4), "eval": []}
     dirs, pols = planewave_batch(8, seed=5)
@@ -1137,6 +1143,8 @@ def main():
     ap.add_argument("--no-learned-eval", action="store_true",
                     help="skip training on small copper layouts and evaluating on held-out larger ones")
     ap.add_argument("--gnn-eval-steps", type=int, default=1500, help="training steps of the generalisation study")
+    ap.add_argument("--learned-form", default="charge", choices=["charge", "rwg"],
+                    help="scalar-potential form of the generalisation study's contexts")
     ap.add_argument("--batch-members", type=int, default=16,
                     help="members of the seeded uneven batch to time (0 = skip; 48 = the full batch)")
     ap.add_argument("--path", type=int, default=0, choices=[0, 1], help="product path for the timed steps (aimx_set_path)")

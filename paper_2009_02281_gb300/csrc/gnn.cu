@@ -22,9 +22,12 @@
 // Training minimises the probe loss (1/P) sum_p |M y_p - z_p|^2 / |z_p|^2 with
 // y_p = A z_p, which is quadratic in C, so the operator only enters through
 // the probe pairs.  Forward, loss, backward and Adam run here; weights are
-// BF16 (an FP32 master copy and FP32 Adam moments are kept), all activations
-// and accumulations are FP32, and every weight-gradient reduction uses a fixed
-// partition and a fixed summation order, so a training step is deterministic.
+// BF16 (an FP32 master copy and FP32 Adam moments are kept), activations and
+// accumulations are FP32, and the 64-wide contractions (node GEMMs, the edge
+// head and its backward, the weight-gradient row reductions) run on the tensor
+// cores with BF16 operands (FP32 operands split into two BF16 terms) and FP32
+// accumulation.  Every weight-gradient reduction uses a fixed partition and a
+// fixed summation order, so a training step is deterministic.
 //
 // Layouts (internal basis order, i.e. sorted by anchor):
 //   node features x [N][8], edge features e [nnz][16] and bases b [nnz][8] in
@@ -50,8 +53,8 @@ constexpr int kNin = 8;              // node features
 constexpr int kNed = 16;             // edge features (orientation invariant)
 constexpr int kNB = 8;               // signed bases
 constexpr int kMaxLayers = 8;
-constexpr int kPersistWarps = 2048;  // fixed warp count of the reducing per-node kernels
-constexpr int kWgradBlocks = 304;    // fixed block count of the row-reduction kernels
+constexpr int kPersistWarps = 1824;  // fixed warp count of the reducing per-node kernels (12 per SM)
+constexpr int kWgradBlocks = 456;    // fixed block count of the row-reduction kernels (3 per SM)
 
 static inline unsigned gb(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
@@ -214,129 +217,213 @@ __global__ void k_input_layer(const float* __restrict__ x, const __nv_bfloat16* 
     H0[t] = fmaxf(acc, 0.f);
 }
 
-// Y[n][o] (=|+=) act( sum_i X[n][i] W'[o][i] + bias[o] + add[n][o] ), 64 x 64 weights:
-// W' = W (row-major [out][in]) or, with TRANS, W^T.  64 nodes per block of 256 threads.
+// ------------------------------------------------------------------ tensor-core contractions
+//
+// The 64-wide contractions run on the tensor cores as mma.sync m16n8k16 with BF16 operands
+// and FP32 accumulation.  Weights are BF16 numbers and enter exactly.  An FP32 activation or
+// gradient x enters as the sum of two BF16 numbers, hi = bf16(x) and lo = bf16(x - hi), which
+// together carry x to about 2^-17 of its magnitude: a product with an exact weight takes two
+// MMAs (hi, lo) and a product of two split operands three (hi hi, hi lo, lo hi; lo lo lies
+// below the FP32 rounding of the sum).  Each accumulator sees its MMAs in a fixed order, so
+// results stay bitwise reproducible.
+//
+// Fragments of m16n8k16 (g = lane / 4, q = lane % 4; a 32-bit register holds two BF16 values,
+// the lower column or row index in its low half):
+//   A (16 x 16, row major)    a0 = (g, 2q..2q+1)  a1 = (g+8, 2q..)  a2 = (g, 2q+8..)  a3 = (g+8, 2q+8..)
+//   B (16 x 8, column major)  b0 = (k = 2q..2q+1, n = g)  b1 = (k = 2q+8.., n = g)
+//   C (16 x 8, FP32)          c0, c1 = (g, 2q..2q+1)  c2, c3 = (g+8, 2q..2q+1)
+
+__device__ __forceinline__ uint32_t bf2_bits(__nv_bfloat162 h) {
+    uint32_t r;
+    memcpy(&r, &h, sizeof(r));
+    return r;
+}
+
+// (x0, x1) -> BF16 pairs hi and lo with x = hi + lo to about 2^-17 |x|
+__device__ __forceinline__ void split_bf2(float x0, float x1, uint32_t& hi, uint32_t& lo) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+    const float2 hf = __bfloat1622float2(h);
+    hi = bf2_bits(h);
+    lo = bf2_bits(__floats2bfloat162_rn(x0 - hf.x, x1 - hf.y));
+}
+
+// two consecutive BF16 values (even element offset) as one B-fragment register
+__device__ __forceinline__ uint32_t ld_bf2(const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+
+__device__ __forceinline__ float2 ld_f2(const float* p) { return *reinterpret_cast<const float2*>(p); }
+
+// d += A B on the tensor cores (m16n8k16, BF16 in, FP32 accumulate)
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// A fragment (hi, lo) of rows (ra, rb) of a row-major FP32 matrix, columns [c0, c0 + 16)
+__device__ __forceinline__ void a_frag_rows(const float* ra, const float* rb, int c0, int q, uint32_t (&hi)[4],
+                                            uint32_t (&lo)[4]) {
+    const float2 x0 = ld_f2(ra + c0 + 2 * q), x1 = ld_f2(rb + c0 + 2 * q);
+    const float2 x2 = ld_f2(ra + c0 + 2 * q + 8), x3 = ld_f2(rb + c0 + 2 * q + 8);
+    split_bf2(x0.x, x0.y, hi[0], lo[0]);
+    split_bf2(x1.x, x1.y, hi[1], lo[1]);
+    split_bf2(x2.x, x2.y, hi[2], lo[2]);
+    split_bf2(x3.x, x3.y, hi[3], lo[3]);
+}
+
+// Y[n][o] (=|+=) act( sum_i X[n][i] W'[o][i] + bias[o] + add[n][o] ), 64 x 64 BF16 weights:
+// W' = W (row-major [out][in]) or, with TRANS, W^T.  W' is staged in shared memory as the B
+// operand; each warp owns 16 nodes and all 64 outputs, a block of 4 warps 64 nodes.
 template <bool TRANS>
-__global__ void __launch_bounds__(256) k_node_gemm(const float* __restrict__ X, const __nv_bfloat16* __restrict__ W,
+__global__ void __launch_bounds__(128) k_node_gemm(const float* __restrict__ X, const __nv_bfloat16* __restrict__ W,
                                                    const __nv_bfloat16* __restrict__ bias,
                                                    const float* __restrict__ add, float* __restrict__ Y, int N,
                                                    int relu, int accumulate) {
-    __shared__ float Ws[kW][kW + 1];
-    __shared__ float Xs[64][kW + 1];
-    const int t = threadIdx.x;
-    const int n0 = blockIdx.x * 64;
-    for (int k = t; k < kW * kW; k += 256) {
-        int r = k / kW, c = k % kW;
-        float v = __bfloat162float(W[k]);
+    __shared__ __align__(16) __nv_bfloat16 Ws[kW][kW + 8];   // W'[o][i]; pitch 36 words: conflict-free fragments
+    for (int k = threadIdx.x; k < kW * kW; k += blockDim.x) {
+        const int r = k / kW, c = k % kW;
         if (TRANS)
-            Ws[c][r] = v;
+            Ws[c][r] = W[k];
         else
-            Ws[r][c] = v;
-    }
-    for (int k = t; k < 64 * kW; k += 256) {
-        int r = k / kW, c = k % kW;
-        Xs[r][c] = (n0 + r < N) ? X[(int64_t)(n0 + r) * kW + c] : 0.f;
+            Ws[r][c] = W[k];
     }
     __syncthreads();
-    const int o = t & 63, grp = t >> 6;
-    float acc[16];
+    const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+    const int n0 = blockIdx.x * 64 + (threadIdx.x >> 5) * 16;
+    if (n0 >= N) return;
+    const int na = min(n0 + g, N - 1), nb = min(n0 + g + 8, N - 1);
+    float acc[8][4];
 #pragma unroll
-    for (int j = 0; j < 16; ++j) acc[j] = 0.f;
-    for (int i = 0; i < kW; ++i) {
-        const float wv = Ws[o][i];
+    for (int nt = 0; nt < 8; ++nt)
 #pragma unroll
-        for (int j = 0; j < 16; ++j) acc[j] = fmaf(Xs[grp * 16 + j][i], wv, acc[j]);
+        for (int i = 0; i < 4; ++i) acc[nt][i] = 0.f;
+#pragma unroll
+    for (int kt = 0; kt < kW / 16; ++kt) {
+        uint32_t ah[4], al[4];
+        a_frag_rows(X + (int64_t)na * kW, X + (int64_t)nb * kW, 16 * kt, q, ah, al);
+        uint32_t b[8][2];
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            b[nt][0] = ld_bf2(&Ws[nt * 8 + g][16 * kt + 2 * q]);
+            b[nt][1] = ld_bf2(&Ws[nt * 8 + g][16 * kt + 2 * q + 8]);
+        }
+        // one pass per operand half over the eight independent accumulators, so that
+        // consecutive MMAs never wait on each other
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) mma_bf16(acc[nt], ah, b[nt][0], b[nt][1]);
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) mma_bf16(acc[nt], al, b[nt][0], b[nt][1]);
     }
-    const float b = bias ? __bfloat162float(bias[o]) : 0.f;
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-        const int n = n0 + grp * 16 + j;
-        if (n >= N) break;
-        const int64_t idx = (int64_t)n * kW + o;
-        float v = acc[j] + b + (add ? add[idx] : 0.f);
-        if (relu) v = fmaxf(v, 0.f);
-        Y[idx] = accumulate ? Y[idx] + v : v;
+    for (int h = 0; h < 2; ++h) {
+        const int n = n0 + g + 8 * h;
+        if (n >= N) continue;
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            const int o = nt * 8 + 2 * q;
+            const int64_t idx = (int64_t)n * kW + o;
+            float v0 = acc[nt][2 * h], v1 = acc[nt][2 * h + 1];
+            if (bias) {
+                v0 += __bfloat162float(bias[o]);
+                v1 += __bfloat162float(bias[o + 1]);
+            }
+            if (add) {
+                const float2 a2 = ld_f2(add + idx);
+                v0 += a2.x;
+                v1 += a2.y;
+            }
+            if (relu) {
+                v0 = fmaxf(v0, 0.f);
+                v1 = fmaxf(v1, 0.f);
+            }
+            if (accumulate) {
+                const float2 y2 = ld_f2(Y + idx);
+                v0 = y2.x + v0;
+                v1 = y2.y + v1;
+            }
+            *reinterpret_cast<float2*>(Y + idx) = make_float2(v0, v1);
+        }
     }
 }
 
-template <int NF>
-__device__ __forceinline__ void load_row(const float* __restrict__ a, int64_t t, float v[NF]) {
-    const float4* p = reinterpret_cast<const float4*>(a + t * NF);
-#pragma unroll
-    for (int q = 0; q < NF / 4; ++q) {
-        const float4 r = __ldg(p + q);
-        v[4 * q] = r.x;
-        v[4 * q + 1] = r.y;
-        v[4 * q + 2] = r.z;
-        v[4 * q + 3] = r.w;
-    }
-}
-
-// S[m] = (1/deg_m) sum_{n != m} relu(P[n] + C e_mn + c); one warp per node, lane owns channels lane, lane+32
-__global__ void k_edge_message(const float* __restrict__ P, const float* __restrict__ e,
-                               const __nv_bfloat16* __restrict__ w, int64_t oC, int64_t oc,
-                               const int* __restrict__ row_ptr, const int* __restrict__ cols,
-                               const float* __restrict__ deginv, int N, float* __restrict__ S) {
-    const int lane = threadIdx.x & 31;
+// S[m] = (1/deg_m) sum_{n != m} relu(P[n] + C e_mn + c) on the tensor cores: one warp per node m
+// (warp-strided), its CSR row in tiles of 16 edges.  Per tile z = P[n] + c + e C^T
+// (e [16 x 16] split hi/lo, C^T exact: 8 n-tiles), masked ReLU summed per lane; at the end of
+// the row the 8 lanes of each column pair combine with a fixed shuffle tree.
+__global__ void __launch_bounds__(256) k_edge_message(const float* __restrict__ P, const float* __restrict__ e,
+                                                      const __nv_bfloat16* __restrict__ w, int64_t oC, int64_t oc,
+                                                      const int* __restrict__ row_ptr, const int* __restrict__ cols,
+                                                      const float* __restrict__ deginv, int N, float* __restrict__ S) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarp = (gridDim.x * blockDim.x) >> 5;
-    float C0[kNed], C1[kNed];
-    for (int f = 0; f < kNed; ++f) {
-        C0[f] = bf(w, oC + lane * kNed + f);
-        C1[f] = bf(w, oC + (lane + 32) * kNed + f);
-    }
-    const float cb0 = bf(w, oc + lane), cb1 = bf(w, oc + lane + 32);
-    for (int m = warp; m < N; m += nwarp) {
-        float s0 = 0.f, s1 = 0.f;
-        auto edge = [&](int t) {
-            const int n = cols[t];
-            if (n == m) return;
-            float ef[kNed];
-            load_row<kNed>(e, t, ef);
-            float w0 = P[(int64_t)n * kW + lane] + cb0, w1 = P[(int64_t)n * kW + lane + 32] + cb1;
+    uint32_t cb[8][2];   // B fragments of C^T: k = feature, n = channel
+    float cv[8][2];
 #pragma unroll
-            for (int f = 0; f < kNed; ++f) {
-                w0 = fmaf(C0[f], ef[f], w0);
-                w1 = fmaf(C1[f], ef[f], w1);
+    for (int nt = 0; nt < 8; ++nt) {
+        const __nv_bfloat16* cr = w + oC + (int64_t)(nt * 8 + g) * kNed + 2 * q;
+        cb[nt][0] = ld_bf2(cr);
+        cb[nt][1] = ld_bf2(cr + 8);
+        cv[nt][0] = __bfloat162float(w[oc + nt * 8 + 2 * q]);
+        cv[nt][1] = __bfloat162float(w[oc + nt * 8 + 2 * q + 1]);
+    }
+    for (int m = warp; m < N; m += nwarp) {
+        const int ts = row_ptr[m], te = row_ptr[m + 1];
+        float s[8][2];
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) s[nt][0] = s[nt][1] = 0.f;
+        for (int t0 = ts; t0 < te; t0 += 16) {
+            const int ta = min(t0 + g, te - 1), tb = min(t0 + g + 8, te - 1);
+            const int na = cols[ta], nb = cols[tb];
+            const bool ka = t0 + g < te && na != m, kb = t0 + g + 8 < te && nb != m;
+            float z[8][4];
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) {
+                const int j = nt * 8 + 2 * q;
+                const float2 pa = ld_f2(P + (int64_t)na * kW + j), pb = ld_f2(P + (int64_t)nb * kW + j);
+                z[nt][0] = pa.x + cv[nt][0];
+                z[nt][1] = pa.y + cv[nt][1];
+                z[nt][2] = pb.x + cv[nt][0];
+                z[nt][3] = pb.y + cv[nt][1];
             }
-            s0 += fmaxf(w0, 0.f);
-            s1 += fmaxf(w1, 0.f);
-        };
-        // two edges per iteration keep two independent gathers in flight (four measured slower here)
-        int t = row_ptr[m];
-        const int te = row_ptr[m + 1];
-        for (; t + 1 < te; t += 2) {
-            edge(t);
-            edge(t + 1);
+            uint32_t ah[4], al[4];
+            a_frag_rows(e + (int64_t)ta * kNed, e + (int64_t)tb * kNed, 0, q, ah, al);
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) mma_bf16(z[nt], ah, cb[nt][0], cb[nt][1]);
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) mma_bf16(z[nt], al, cb[nt][0], cb[nt][1]);
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) {
+                s[nt][0] += (ka ? fmaxf(z[nt][0], 0.f) : 0.f) + (kb ? fmaxf(z[nt][2], 0.f) : 0.f);
+                s[nt][1] += (ka ? fmaxf(z[nt][1], 0.f) : 0.f) + (kb ? fmaxf(z[nt][3], 0.f) : 0.f);
+            }
         }
-        if (t < te) edge(t);
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                float v = s[nt][c];
+                v += __shfl_xor_sync(0xffffffffu, v, 4);
+                v += __shfl_xor_sync(0xffffffffu, v, 8);
+                v += __shfl_xor_sync(0xffffffffu, v, 16);
+                s[nt][c] = v;
+            }
+        // every lane of a column pair holds the sums; lane (g, q) stores n-tile g
         const float di = deginv[m];
-        S[(int64_t)m * kW + lane] = s0 * di;
-        S[(int64_t)m * kW + lane + 32] = s1 * di;
+        float2 out = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt)
+            if (nt == g) out = make_float2(s[nt][0] * di, s[nt][1] * di);
+        *reinterpret_cast<float2*>(S + (int64_t)m * kW + g * 8 + 2 * q) = out;
     }
 }
 
-// shared copy of the edge head: Uc [64][16], u [64], E [K*8][64], f [K*8]
-template <int K>
-struct HeadSmem {
-    float Uc[kW][kNed];
-    float u[kW];
-    float E[K * kNB][kW];
-    float f[K * kNB];
-};
-
-template <int K>
-__device__ void load_head(HeadSmem<K>& sm, const __nv_bfloat16* __restrict__ w, int64_t oUc, int64_t ou,
-                          int64_t oE, int64_t of) {
-    for (int i = threadIdx.x; i < kW * kNed; i += blockDim.x) sm.Uc[i / kNed][i % kNed] = bf(w, oUc + i);
-    for (int i = threadIdx.x; i < kW; i += blockDim.x) sm.u[i] = bf(w, ou + i);
-    for (int i = threadIdx.x; i < K * kNB * kW; i += blockDim.x) sm.E[i / kW][i % kW] = bf(w, oE + i);
-    for (int i = threadIdx.x; i < K * kNB; i += blockDim.x) sm.f[i] = bf(w, of + i);
-}
-
-// Edge head, one thread per stored pair t = (m, n):
-//   u = relu(Pa[m] + Pb[n] + Uc e + u),  o[k] = sum_c b_c (E u + f)[k*8 + c]  (0 on the diagonal);
-// U (optional) keeps u for the backward pass.
+// Edge head on the tensor cores, 16 stored pairs t = (m, n) per warp:
+//   z = Pa[m] + Pb[n] + u + Uc e_t      (e [16] x Uc^T [16 x 64]: 8 n-tiles, hi and lo of e)
+//   u_t = relu(z)                       (kept in U for the backward pass; 0 on the diagonal)
+//   r = f + E u_t                       (u [64] x E^T [64 x K*8], the accumulators of z reused
+//                                        as A fragments: n-tiles 2j, 2j+1 form k-tile j)
+//   o[k] = sum_c b_c r[k*8 + c]         (each n-tile is one k; a quad shuffle sums over c)
 template <int K>
 __global__ void __launch_bounds__(128) k_head_forward(const float* __restrict__ Pa, const float* __restrict__ Pb,
                                                       const float* __restrict__ e, const float* __restrict__ basis,
@@ -344,58 +431,101 @@ __global__ void __launch_bounds__(128) k_head_forward(const float* __restrict__ 
                                                       int64_t oE, int64_t of, const int* __restrict__ rows,
                                                       const int* __restrict__ cols, int64_t nnz,
                                                       float* __restrict__ o, float* __restrict__ U) {
-    __shared__ HeadSmem<K> sm;
-    load_head<K>(sm, w, oUc, ou, oE, of);
+    constexpr int NO = K * kNB;
+    __shared__ __align__(16) __nv_bfloat16 Es[NO][kW + 8];   // E[n][j]: B operand of u E^T
+    for (int k = threadIdx.x; k < NO * kW; k += blockDim.x) Es[k / kW][k % kW] = w[oE + k];
     __syncthreads();
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= nnz) return;
-    const int m = rows[t], n = cols[t];
-    if (m == n) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+    const int64_t t0 = ((int64_t)blockIdx.x * 4 + (threadIdx.x >> 5)) * 16;
+    if (t0 >= nnz) return;
+    const int64_t ta = min(t0 + g, nnz - 1), tb = min(t0 + g + 8, nnz - 1);
+    const bool va = t0 + g < nnz, vb = t0 + g + 8 < nnz;
+    const int ma = rows[ta], na = cols[ta], mb = rows[tb], nb = cols[tb];
+    float z[8][4];
 #pragma unroll
-        for (int k = 0; k < K; ++k) o[t * K + k] = 0.f;
-        if (U) {
-            float4* Ur = reinterpret_cast<float4*>(U + t * kW);
-            for (int q = 0; q < kW / 4; ++q) Ur[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        return;
+    for (int nt = 0; nt < 8; ++nt) {
+        const int j = nt * 8 + 2 * q;
+        const float u0 = __bfloat162float(w[ou + j]), u1 = __bfloat162float(w[ou + j + 1]);
+        const float2 pa = ld_f2(Pa + (int64_t)ma * kW + j), pb = ld_f2(Pb + (int64_t)na * kW + j);
+        const float2 qa = ld_f2(Pa + (int64_t)mb * kW + j), qb = ld_f2(Pb + (int64_t)nb * kW + j);
+        z[nt][0] = pa.x + pb.x + u0;
+        z[nt][1] = pa.y + pb.y + u1;
+        z[nt][2] = qa.x + qb.x + u0;
+        z[nt][3] = qa.y + qb.y + u1;
     }
-    float ef[kNed], b[kNB];
-    load_row<kNed>(e, t, ef);
-    load_row<kNB>(basis, t, b);
-    float acc[K];
+    {
+        uint32_t ah[4], al[4];
+        a_frag_rows(e + ta * kNed, e + tb * kNed, 0, q, ah, al);
+        uint32_t b[8][2];
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            const __nv_bfloat16* uc = w + oUc + (int64_t)(nt * 8 + g) * kNed + 2 * q;   // Uc[j][f]
+            b[nt][0] = ld_bf2(uc);
+            b[nt][1] = ld_bf2(uc + 8);
+        }
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) mma_bf16(z[nt], ah, b[nt][0], b[nt][1]);
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) mma_bf16(z[nt], al, b[nt][0], b[nt][1]);
+    }
+    const bool ka = ma != na, kb = mb != nb;
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+        z[nt][0] = ka ? fmaxf(z[nt][0], 0.f) : 0.f;
+        z[nt][1] = ka ? fmaxf(z[nt][1], 0.f) : 0.f;
+        z[nt][2] = kb ? fmaxf(z[nt][2], 0.f) : 0.f;
+        z[nt][3] = kb ? fmaxf(z[nt][3], 0.f) : 0.f;
+    }
+    if (U) {
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            const int j = nt * 8 + 2 * q;
+            if (va) *reinterpret_cast<float2*>(U + ta * kW + j) = make_float2(z[nt][0], z[nt][1]);
+            if (vb) *reinterpret_cast<float2*>(U + tb * kW + j) = make_float2(z[nt][2], z[nt][3]);
+        }
+    }
+    float r[K][4];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        float a = 0.f;
-#pragma unroll
-        for (int c = 0; c < kNB; ++c) a = fmaf(b[c], sm.f[k * kNB + c], a);
-        acc[k] = a;
+        const float f0 = __bfloat162float(w[of + k * kNB + 2 * q]), f1 = __bfloat162float(w[of + k * kNB + 2 * q + 1]);
+        r[k][0] = f0;
+        r[k][1] = f1;
+        r[k][2] = f0;
+        r[k][3] = f1;
     }
-    const float4* pa = reinterpret_cast<const float4*>(Pa + (int64_t)m * kW);
-    const float4* pb = reinterpret_cast<const float4*>(Pb + (int64_t)n * kW);
-    for (int q = 0; q < kW / 4; ++q) {
-        const float4 A4 = __ldg(pa + q), B4 = __ldg(pb + q);
-        const float za[4] = {A4.x + B4.x, A4.y + B4.y, A4.z + B4.z, A4.w + B4.w};
-        float uq[4];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int j = 4 * q + r;
-            float z = za[r] + sm.u[j];
+    for (int kt = 0; kt < kW / 16; ++kt) {
+        uint32_t ah[4], al[4];
+        split_bf2(z[2 * kt][0], z[2 * kt][1], ah[0], al[0]);
+        split_bf2(z[2 * kt][2], z[2 * kt][3], ah[1], al[1]);
+        split_bf2(z[2 * kt + 1][0], z[2 * kt + 1][1], ah[2], al[2]);
+        split_bf2(z[2 * kt + 1][2], z[2 * kt + 1][3], ah[3], al[3]);
+        uint32_t b[K][2];
 #pragma unroll
-            for (int f = 0; f < kNed; ++f) z = fmaf(sm.Uc[j][f], ef[f], z);
-            const float uj = fmaxf(z, 0.f);
-            uq[r] = uj;
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                float et = 0.f;
-#pragma unroll
-                for (int c = 0; c < kNB; ++c) et = fmaf(b[c], sm.E[k * kNB + c][j], et);
-                acc[k] = fmaf(uj, et, acc[k]);
-            }
+        for (int k = 0; k < K; ++k) {
+            b[k][0] = ld_bf2(&Es[k * kNB + g][16 * kt + 2 * q]);
+            b[k][1] = ld_bf2(&Es[k * kNB + g][16 * kt + 2 * q + 8]);
         }
-        if (U) reinterpret_cast<float4*>(U + t * kW)[q] = make_float4(uq[0], uq[1], uq[2], uq[3]);
-    }
 #pragma unroll
-    for (int k = 0; k < K; ++k) o[t * K + k] = acc[k];
+        for (int k = 0; k < K; ++k) mma_bf16(r[k], ah, b[k][0], b[k][1]);
+#pragma unroll
+        for (int k = 0; k < K; ++k) mma_bf16(r[k], al, b[k][0], b[k][1]);
+    }
+    const float2 ba = ld_f2(basis + ta * kNB + 2 * q), bb = ld_f2(basis + tb * kNB + 2 * q);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        float sa = fmaf(ba.y, r[k][1], ba.x * r[k][0]);
+        float sb = fmaf(bb.y, r[k][3], bb.x * r[k][2]);
+        // butterfly over the quad: every lane ends with the same sum (each add is commutative)
+        sa += __shfl_xor_sync(0xffffffffu, sa, 1);
+        sb += __shfl_xor_sync(0xffffffffu, sb, 1);
+        sa += __shfl_xor_sync(0xffffffffu, sa, 2);
+        sb += __shfl_xor_sync(0xffffffffu, sb, 2);
+        if ((k & 3) == q) {
+            if (va) o[ta * K + k] = ka ? sa : 0.f;
+            if (vb) o[tb * K + k] = kb ? sb : 0.f;
+        }
+    }
 }
 
 // diagonal head g_m = G h_m + g; one thread per (node, output)
@@ -562,48 +692,64 @@ __global__ void k_output_grads(const int* __restrict__ rows, const int* __restri
 
 // ------------------------------------------------------------------ backward kernels
 
-// Edge head backward, one thread per stored pair: dz_j = [u_j > 0] sum_k Ge[k] sum_c b_c E[k*8+c][j]
+// Edge head backward on the tensor cores, 16 stored pairs per warp:
+//   dz_t[j] = [u_t[j] > 0] sum_n G'_t[n] E[n][j],  G'_t[k*8 + c] = Ge_t[k] b_c(t)
+// (G' [K*8] x E [K*8 x 64]: A fragments formed from Ge and the bases, hi and lo; E^T staged in
+// shared memory as the B operand).  u = 0 on the diagonal, so dz = 0 there.
 template <int K>
 __global__ void __launch_bounds__(128) k_head_backward(const float* __restrict__ U, const float* __restrict__ Ge,
                                                        const float* __restrict__ basis,
-                                                       const __nv_bfloat16* __restrict__ w, int64_t oUc,
-                                                       int64_t ou, int64_t oE, int64_t of,
-                                                       const int* __restrict__ rows, const int* __restrict__ cols,
+                                                       const __nv_bfloat16* __restrict__ w, int64_t oE,
                                                        int64_t nnz, float* __restrict__ DZ) {
-    __shared__ HeadSmem<K> sm;
-    load_head<K>(sm, w, oUc, ou, oE, of);
+    constexpr int NO = K * kNB;
+    __shared__ __align__(16) __nv_bfloat16 Et[kW][NO + 8];   // E^T[j][n]
+    for (int k = threadIdx.x; k < NO * kW; k += blockDim.x) Et[k % kW][k / kW] = w[oE + k];
     __syncthreads();
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= nnz) return;
-    float4* dz4 = reinterpret_cast<float4*>(DZ + t * kW);
-    if (rows[t] == cols[t]) {
-        for (int q = 0; q < kW / 4; ++q) dz4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-        return;
-    }
-    float b[kNB], ge[K];
-    load_row<kNB>(basis, t, b);
+    const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+    const int64_t t0 = ((int64_t)blockIdx.x * 4 + (threadIdx.x >> 5)) * 16;
+    if (t0 >= nnz) return;
+    const int64_t ta = min(t0 + g, nnz - 1), tb = min(t0 + g + 8, nnz - 1);
+    const bool va = t0 + g < nnz, vb = t0 + g + 8 < nnz;
+    const float2 ba = ld_f2(basis + ta * kNB + 2 * q), bb = ld_f2(basis + tb * kNB + 2 * q);
+    float acc[8][4];
 #pragma unroll
-    for (int k = 0; k < K; ++k) ge[k] = Ge[t * K + k];
-    // fold the output gradient into one weight per (k, c): gb[k*8+c] = Ge[k] b_c
-    const float4* u4 = reinterpret_cast<const float4*>(U + t * kW);
-    for (int q = 0; q < kW / 4; ++q) {
-        const float4 uu = __ldg(u4 + q);
-        const float uv[4] = {uu.x, uu.y, uu.z, uu.w};
-        float dz[4];
+    for (int nt = 0; nt < 8; ++nt)
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int j = 4 * q + r;
-            float s = 0.f;
+        for (int i = 0; i < 4; ++i) acc[nt][i] = 0.f;
 #pragma unroll
-            for (int k = 0; k < K; ++k) {
-                float et = 0.f;
+    for (int kt = 0; kt < NO / 16; ++kt) {
+        // k-tile kt covers n = 16 kt + [0, 16): outputs k = 2 kt (columns 0..7) and 2 kt + 1 (8..15)
+        const float ga0 = Ge[ta * K + 2 * kt], ga1 = Ge[ta * K + 2 * kt + 1];
+        const float gb0 = Ge[tb * K + 2 * kt], gb1 = Ge[tb * K + 2 * kt + 1];
+        uint32_t ah[4], al[4];
+        split_bf2(ga0 * ba.x, ga0 * ba.y, ah[0], al[0]);
+        split_bf2(gb0 * bb.x, gb0 * bb.y, ah[1], al[1]);
+        split_bf2(ga1 * ba.x, ga1 * ba.y, ah[2], al[2]);
+        split_bf2(gb1 * bb.x, gb1 * bb.y, ah[3], al[3]);
+        uint32_t b[8][2];
 #pragma unroll
-                for (int c = 0; c < kNB; ++c) et = fmaf(b[c], sm.E[k * kNB + c][j], et);
-                s = fmaf(ge[k], et, s);
-            }
-            dz[r] = uv[r] > 0.f ? s : 0.f;
+        for (int nt = 0; nt < 8; ++nt) {
+            b[nt][0] = ld_bf2(&Et[nt * 8 + g][16 * kt + 2 * q]);
+            b[nt][1] = ld_bf2(&Et[nt * 8 + g][16 * kt + 2 * q + 8]);
         }
-        dz4[q] = make_float4(dz[0], dz[1], dz[2], dz[3]);
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) mma_bf16(acc[nt], ah, b[nt][0], b[nt][1]);
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) mma_bf16(acc[nt], al, b[nt][0], b[nt][1]);
+    }
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+        const int j = nt * 8 + 2 * q;
+        if (va) {
+            const float2 u = ld_f2(U + ta * kW + j);
+            *reinterpret_cast<float2*>(DZ + ta * kW + j) =
+                make_float2(u.x > 0.f ? acc[nt][0] : 0.f, u.y > 0.f ? acc[nt][1] : 0.f);
+        }
+        if (vb) {
+            const float2 u = ld_f2(U + tb * kW + j);
+            *reinterpret_cast<float2*>(DZ + tb * kW + j) =
+                make_float2(u.x > 0.f ? acc[nt][2] : 0.f, u.y > 0.f ? acc[nt][3] : 0.f);
+        }
     }
 }
 
@@ -649,156 +795,318 @@ __global__ void k_relu_back(const float* __restrict__ dH, const float* __restric
     if (dS) dS[t] = v * deginv[t / kW];
 }
 
-// Message backward for layer l, one warp per node n over its row (near pattern symmetric):
-//   dP[n] = sum_{m != n} dS[m] * [B h_n + C e_mn + c > 0],  per-warp partials of dC (64 x 16) and dc (64).
-__global__ void k_edge_backward(const float* __restrict__ P, const float* __restrict__ e,
-                                const __nv_bfloat16* __restrict__ w, int64_t oC, int64_t oc,
-                                const int* __restrict__ row_ptr, const int* __restrict__ cols,
-                                const int* __restrict__ trans, const float* __restrict__ dS, int N,
-                                float* __restrict__ dP, float* __restrict__ part) {
-    const int lane = threadIdx.x & 31;
+// Message backward for layer l on the tensor cores, one warp per node n (warp-strided) over
+// its CSR row in tiles of 16 edges (the near pattern is symmetric; edge (m, n) is trans[t]):
+//   z^T = P[n] + c + C e_mn^T          (C exact as the A operand: 4 m-tiles of channels)
+//   G^T = [z > 0, m != n] dS[m]        (per channel and edge, in the accumulator layout)
+//   dP[n] = sum_m G^T,   dC^T += e^T G  (G's accumulators are the B fragments directly),
+//   dc += sum_m G^T;  dC and dc as per-warp partials, combined by a fixed reduction.
+__global__ void __launch_bounds__(128, 3) k_edge_backward(const float* __restrict__ P, const float* __restrict__ e,
+                                                       const __nv_bfloat16* __restrict__ w, int64_t oC, int64_t oc,
+                                                       const int* __restrict__ row_ptr, const int* __restrict__ cols,
+                                                       const int* __restrict__ trans, const float* __restrict__ dS,
+                                                       int N, float* __restrict__ dP, float* __restrict__ part) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarp = (gridDim.x * blockDim.x) >> 5;
-    float C0[kNed], C1[kNed], aC0[kNed], aC1[kNed];
-    for (int f = 0; f < kNed; ++f) {
-        C0[f] = bf(w, oC + lane * kNed + f);
-        C1[f] = bf(w, oC + (lane + 32) * kNed + f);
-        aC0[f] = aC1[f] = 0.f;
+    uint32_t ca[4][4];   // A fragments of C (64 x 16, row-major [channel][feature]), exact
+    float cv[4][2];      // c at this lane's channels 16 mt + g (+8)
+#pragma unroll
+    for (int mt = 0; mt < 4; ++mt) {
+        const __nv_bfloat16* c0 = w + oC + (int64_t)(16 * mt + g) * kNed + 2 * q;
+        ca[mt][0] = ld_bf2(c0);
+        ca[mt][1] = ld_bf2(c0 + 8 * kNed);
+        ca[mt][2] = ld_bf2(c0 + 8);
+        ca[mt][3] = ld_bf2(c0 + 8 * kNed + 8);
+        cv[mt][0] = __bfloat162float(w[oc + 16 * mt + g]);
+        cv[mt][1] = __bfloat162float(w[oc + 16 * mt + g + 8]);
     }
-    const float cb0 = bf(w, oc + lane), cb1 = bf(w, oc + lane + 32);
-    float ac0 = 0.f, ac1 = 0.f;
+    float dct[8][4];     // dC^T accumulators: features g (+8) x channels 8 j + 2 q (+1)
+    float dcs[4][2];     // dc partial sums at this lane's channels
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) dct[j][i] = 0.f;
+#pragma unroll
+    for (int mt = 0; mt < 4; ++mt) dcs[mt][0] = dcs[mt][1] = 0.f;
     for (int n = warp; n < N; n += nwarp) {
-        const float p0 = P[(int64_t)n * kW + lane] + cb0, p1 = P[(int64_t)n * kW + lane + 32] + cb1;
-        float d0 = 0.f, d1 = 0.f;
-        auto edge = [&](int t) {
-            const int m = cols[t];
-            const bool keep = m != n;   // the self pair contributes exact zeros (branch-free)
-            const int tr = trans[t];  // edge (m, n) in row m
-            float ef[kNed];
-            load_row<kNed>(e, tr, ef);
-            const float ds0 = dS[(int64_t)m * kW + lane], ds1 = dS[(int64_t)m * kW + lane + 32];
-            float w0 = p0, w1 = p1;
+        const int ts = row_ptr[n], te = row_ptr[n + 1];
+        float pv[4][2], d[4][2];
 #pragma unroll
-            for (int f = 0; f < kNed; ++f) {
-                w0 = fmaf(C0[f], ef[f], w0);
-                w1 = fmaf(C1[f], ef[f], w1);
-            }
-            const float g0 = (keep && w0 > 0.f) ? ds0 : 0.f;
-            const float g1 = (keep && w1 > 0.f) ? ds1 : 0.f;
-            d0 += g0;
-            d1 += g1;
-#pragma unroll
-            for (int f = 0; f < kNed; ++f) {
-                aC0[f] = fmaf(g0, ef[f], aC0[f]);
-                aC1[f] = fmaf(g1, ef[f], aC1[f]);
-            }
-        };
-        int t = row_ptr[n];
-        const int te = row_ptr[n + 1];
-        for (; t + 3 < te; t += 4) {
-            edge(t);
-            edge(t + 1);
-            edge(t + 2);
-            edge(t + 3);
+        for (int mt = 0; mt < 4; ++mt) {
+            pv[mt][0] = P[(int64_t)n * kW + 16 * mt + g] + cv[mt][0];
+            pv[mt][1] = P[(int64_t)n * kW + 16 * mt + g + 8] + cv[mt][1];
+            d[mt][0] = d[mt][1] = 0.f;
         }
-        for (; t < te; ++t) edge(t);
-        ac0 += d0;
-        ac1 += d1;
-        dP[(int64_t)n * kW + lane] = d0;
-        dP[(int64_t)n * kW + lane + 32] = d1;
+        for (int t0 = ts; t0 < te; t0 += 16) {
+            // B operand e^T (k = feature, n = edge): edge g of each 8-edge n-tile
+            int tr[2];
+            bool kp[2][2];   // keep flags of edges 2q, 2q+1 (+8) owned in the accumulator layout
+#pragma unroll
+            for (int et = 0; et < 2; ++et) tr[et] = trans[min(t0 + 8 * et + g, te - 1)];
+            int me[2][2];
+#pragma unroll
+            for (int et = 0; et < 2; ++et)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const int t = t0 + 8 * et + 2 * q + c;
+                    me[et][c] = cols[min(t, te - 1)];
+                    kp[et][c] = t < te && me[et][c] != n;
+                }
+            float z[4][2][4];
+#pragma unroll
+            for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+                for (int et = 0; et < 2; ++et) {
+                    z[mt][et][0] = z[mt][et][1] = pv[mt][0];
+                    z[mt][et][2] = z[mt][et][3] = pv[mt][1];
+                }
+            uint32_t ebh[2][2], ebl[2][2];
+#pragma unroll
+            for (int et = 0; et < 2; ++et) {
+                const float* er = e + (int64_t)tr[et] * kNed + 2 * q;
+                const float2 e0 = ld_f2(er), e1 = ld_f2(er + 8);
+                split_bf2(e0.x, e0.y, ebh[et][0], ebl[et][0]);
+                split_bf2(e1.x, e1.y, ebh[et][1], ebl[et][1]);
+            }
+            // hi pass, then lo pass, over the eight independent accumulators
+#pragma unroll
+            for (int et = 0; et < 2; ++et)
+#pragma unroll
+                for (int mt = 0; mt < 4; ++mt) mma_bf16(z[mt][et], ca[mt], ebh[et][0], ebh[et][1]);
+#pragma unroll
+            for (int et = 0; et < 2; ++et)
+#pragma unroll
+                for (int mt = 0; mt < 4; ++mt) mma_bf16(z[mt][et], ca[mt], ebl[et][0], ebl[et][1]);
+            // gate: G^T(channel, edge) = [z > 0, keep] dS[m_edge][channel]
+#pragma unroll
+            for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+                for (int et = 0; et < 2; ++et)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int c = i & 1, h = i >> 1;
+                        const float ds = dS[(int64_t)me[et][c] * kW + 16 * mt + g + 8 * h];
+                        const float gv = (kp[et][c] && z[mt][et][i] > 0.f) ? ds : 0.f;
+                        z[mt][et][i] = gv;
+                        d[mt][h] += gv;
+                    }
+            // dC^T += e^T G: A = e^T (m = feature g (+8), k = edges 2q.. (+8)), split hi/lo
+            uint32_t ah[4], al[4];
+            {
+                float ev[4][2];
+#pragma unroll
+                for (int et = 0; et < 2; ++et)
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        const int t = min(t0 + 8 * et + 2 * q + c, te - 1);
+                        const int trc = trans[t];
+                        ev[2 * et][c] = e[(int64_t)trc * kNed + g];         // feature g
+                        ev[2 * et + 1][c] = e[(int64_t)trc * kNed + g + 8]; // feature g + 8
+                    }
+                // a0 = (g, edges 2q..), a1 = (g + 8, edges 2q..), a2 = (g, edges 8 + 2q..), a3 = (g + 8, ...)
+                split_bf2(ev[0][0], ev[0][1], ah[0], al[0]);
+                split_bf2(ev[1][0], ev[1][1], ah[1], al[1]);
+                split_bf2(ev[2][0], ev[2][1], ah[2], al[2]);
+                split_bf2(ev[3][0], ev[3][1], ah[3], al[3]);
+            }
+            // B fragments of G (k = edges, n = channels 8 j + g): rows (2q, 2q+1) of edge tiles 0, 1
+            uint32_t gh[8][2], gl[8][2];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int mt = j >> 1, h = j & 1;
+                split_bf2(z[mt][0][2 * h], z[mt][0][2 * h + 1], gh[j][0], gl[j][0]);
+                split_bf2(z[mt][1][2 * h], z[mt][1][2 * h + 1], gh[j][1], gl[j][1]);
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) mma_bf16(dct[j], ah, gh[j][0], gh[j][1]);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) mma_bf16(dct[j], ah, gl[j][0], gl[j][1]);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) mma_bf16(dct[j], al, gh[j][0], gh[j][1]);
+        }
+        // dP[n]: sum over the four lanes of each channel row (edges 2q, 2q + 1 of both tiles)
+#pragma unroll
+        for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                float v = d[mt][h];
+                dcs[mt][h] += v;
+                v += __shfl_xor_sync(0xffffffffu, v, 1);
+                v += __shfl_xor_sync(0xffffffffu, v, 2);
+                if (q == 0) dP[(int64_t)n * kW + 16 * mt + g + 8 * h] = v;
+            }
     }
     float* pw = part + (int64_t)warp * (kW * kNed + kW);
-    for (int f = 0; f < kNed; ++f) {
-        pw[lane * kNed + f] = aC0[f];
-        pw[(lane + 32) * kNed + f] = aC1[f];
-    }
-    pw[kW * kNed + lane] = ac0;
-    pw[kW * kNed + lane + 32] = ac1;
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int f = g + 8 * (i >> 1), ch = 8 * j + 2 * q + (i & 1);
+            pw[ch * kNed + f] = dct[j][i];
+        }
+#pragma unroll
+    for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float v = dcs[mt][h];
+            v += __shfl_xor_sync(0xffffffffu, v, 1);
+            v += __shfl_xor_sync(0xffffffffu, v, 2);
+            if (q == 0) pw[kW * kNed + 16 * mt + g + 8 * h] = v;
+        }
 }
 
-// Per-block partials of a row reduction over R rows in fixed chunks:
+// Per-block partials of a row reduction over R rows in fixed chunks, on the tensor cores:
 //   out[o][i] = sum_r A(r, o) B[r][i] (o < na <= 64, i < nb <= 64), then (bias) sum_r A(r, o).
 // MODE 0: A(r, o) = A[r * na + o];  MODE 1: A(r, o) = Ge[r * K + o / 8] * basis[r * 8 + o % 8].
-// Thread t owns the 4 x 4 output tile o in [4 (t / 16), +4), i in [4 (t % 16), +4): two 128-bit
-// shared loads feed 16 FMAs per row.
-template <int MODE>
-__global__ void __launch_bounds__(256) k_rows_wgrad(const float* __restrict__ A, const float* __restrict__ Ge,
+// Each 32-row stage is staged transposed in shared memory as split BF16 ([column][row], rows
+// contiguous), so A^T is the MMA's A operand (m = o, k = r) and B its B operand (k = r,
+// n = i), both read with ldmatrix; warp w owns outputs o in [16 w, 16 w + 16).  Stages are
+// double-buffered (one barrier each) and the next one is loaded into registers while the
+// current one is multiplied.  The bias sums run in FP32 on the staging threads (two per
+// column, combined in a fixed order).
+constexpr int kWgPitch = 40;   // BF16 per staged column: 32 rows + 8 (16-byte rows, conflict-free ldmatrix)
+
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const __nv_bfloat16* p) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+
+template <int MODE, int NP>
+__global__ void __launch_bounds__(128) k_rows_wgrad(const float* __restrict__ A, const float* __restrict__ Ge,
                                                     const float* __restrict__ basis, int K, int na,
                                                     const float* __restrict__ B, int nb, int bias, int64_t R,
                                                     int64_t chunk, float* __restrict__ part) {
-    __shared__ __align__(16) float As[32][kW];
-    __shared__ __align__(16) float Bs[32][kW];
-    const int t = threadIdx.x;
-    const int ot = t >> 4, it = t & 15;
-    const bool active = 4 * ot < na && 4 * it < nb;
+    // [buffer][hi, lo][column][row]
+    __shared__ __align__(16) __nv_bfloat16 sA[2][2][kW][kWgPitch];
+    __shared__ __align__(16) __nv_bfloat16 sB[2][2][kW][kWgPitch];
+    __shared__ float sbias[4][kW];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, g = lane >> 2, q = lane & 3;
+    // staging: item i of thread tid is column 8 (tid / 32 + 4 (i & 1)) + tid % 8 and row pair
+    // 4 (i / 2) + (tid / 8) % 4, so that a warp's stores of one item cover 8 columns x 4 row
+    // pairs (32 distinct banks) and its loads 4 rows x 8 consecutive columns
+    const int scol = 8 * (tid >> 5) + (tid & 7), spair = (tid >> 3) & 3;
     const int64_t lo = blockIdx.x * chunk, hi = min(R, lo + chunk);
-    float acc[4][4], accb[4] = {0.f, 0.f, 0.f, 0.f};
+    // NP pairs of n-tiles (nb <= 16 NP).  With one pair the three products (hi hi, hi lo, lo hi)
+    // keep separate accumulators, so that every MMA of a k-step is independent of the others.
+    constexpr int SETS = NP == 1 ? 3 : 1;
+    float acc[SETS][2 * NP][4];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int st = 0; st < SETS; ++st)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[a][c] = 0.f;
-    // the next 32-row chunk is loaded into registers while the current one is multiplied
-    constexpr int PER = 32 * kW / 256;
-    float ra[PER], rb[PER];
-    auto load_chunk = [&](int64_t r0) {
+        for (int nt = 0; nt < 2 * NP; ++nt)
 #pragma unroll
-        for (int i = 0; i < PER; ++i) {
-            const int k = t + 256 * i;
-            const int r = k / kW, c = k % kW;
-            float va = 0.f, vb = 0.f;
-            if (r0 + r < hi) {
-                if (c < na) {
-                    if (MODE == 0)
-                        va = A[(r0 + r) * na + c];
-                    else
-                        va = Ge[(r0 + r) * K + c / kNB] * basis[(r0 + r) * kNB + c % kNB];
+            for (int i = 0; i < 4; ++i) acc[st][nt][i] = 0.f;
+    float accb[2] = {0.f, 0.f};
+    constexpr int PP = 8;   // (column, row pair) items per thread and stage
+    // next stage in registers: A (MODE 0) or its two factors Ge and basis (MODE 1, multiplied
+    // at staging time, so that no instruction waits on these loads before the MMAs), and B
+    float ra[2 * PP], rb[2 * PP], rc[MODE == 1 ? 2 * PP : 1];
+    auto load_stage = [&](int64_t r0) {
+#pragma unroll
+        for (int p = 0; p < PP; ++p) {
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const int col = scol + 32 * (p & 1);
+                const int64_t r = r0 + 2 * (4 * (p >> 1) + spair) + s;
+                float va = 0.f, vb = 0.f, vc = 0.f;
+                if (r < hi) {
+                    if (col < na) {
+                        if (MODE == 0) {
+                            va = A[r * na + col];
+                        } else {
+                            va = Ge[r * K + col / kNB];
+                            vc = basis[r * kNB + col % kNB];
+                        }
+                    }
+                    if (col < nb) vb = B[r * nb + col];
                 }
-                if (c < nb) vb = B[(r0 + r) * nb + c];
+                ra[2 * p + s] = va;
+                rb[2 * p + s] = vb;
+                if (MODE == 1) rc[2 * p + s] = vc;
             }
-            ra[i] = va;
-            rb[i] = vb;
         }
     };
-    if (lo < hi) load_chunk(lo);
-    for (int64_t r0 = lo; r0 < hi; r0 += 32) {
+    // staged rows are 16-byte chunks of 8 BF16 values (every 8-row ldmatrix phase conflict-free)
+    auto chunk_at = [](int x, int c) { return 8 * c; };
+    const bool mts = warp * 16 < na;                // this warp's m-tile holds outputs
+    // ldmatrix row addresses of this lane: A (16 x 16 per k-step), B (two n-tiles x 16 per k-step)
+    const int arow = warp * 16 + (lane & 7) + 8 * ((lane >> 3) & 1), acol = 8 * (lane >> 4);
+    const int brow = (lane & 7) + 8 * (lane >> 4), bcol = 8 * ((lane >> 3) & 1);
+    if (lo < hi) load_stage(lo);
+    int buf = 0;
+    for (int64_t r0 = lo; r0 < hi; r0 += 32, buf ^= 1) {
 #pragma unroll
-        for (int i = 0; i < PER; ++i) {
-            const int k = t + 256 * i;
-            As[k / kW][k % kW] = ra[i];
-            Bs[k / kW][k % kW] = rb[i];
+        for (int p = 0; p < PP; ++p) {
+            const int col = scol + 32 * (p & 1);
+            const int pr = 4 * (p >> 1) + spair;          // row pair: rows 2 pr, 2 pr + 1
+            const int at = chunk_at(col, pr >> 2) + 2 * (pr & 3);
+            const float a0 = MODE == 1 ? ra[2 * p] * rc[2 * p] : ra[2 * p];
+            const float a1 = MODE == 1 ? ra[2 * p + 1] * rc[2 * p + 1] : ra[2 * p + 1];
+            uint32_t h, l;
+            split_bf2(a0, a1, h, l);
+            *reinterpret_cast<uint32_t*>(&sA[buf][0][col][at]) = h;
+            *reinterpret_cast<uint32_t*>(&sA[buf][1][col][at]) = l;
+            split_bf2(rb[2 * p], rb[2 * p + 1], h, l);
+            *reinterpret_cast<uint32_t*>(&sB[buf][0][col][at]) = h;
+            *reinterpret_cast<uint32_t*>(&sB[buf][1][col][at]) = l;
+            accb[p & 1] += a0;
+            accb[p & 1] += a1;
         }
         __syncthreads();
-        if (r0 + 32 < hi) load_chunk(r0 + 32);
-        if (active) {
-#pragma unroll 8
-            for (int r = 0; r < 32; ++r) {
-                const float4 a4 = *reinterpret_cast<const float4*>(&As[r][4 * ot]);
-                const float4 b4 = *reinterpret_cast<const float4*>(&Bs[r][4 * it]);
-                const float av[4] = {a4.x, a4.y, a4.z, a4.w}, bv[4] = {b4.x, b4.y, b4.z, b4.w};
+        if (r0 + 32 < hi) load_stage(r0 + 32);
+        if (mts) {
 #pragma unroll
-                for (int a = 0; a < 4; ++a) {
+            for (int kt = 0; kt < 2; ++kt) {
+                uint32_t ah[4], al[4];
+                const int ac = chunk_at(arow, 2 * kt + acol / 8);
+                ldsm_x4(ah, &sA[buf][0][arow][ac]);
+                ldsm_x4(al, &sA[buf][1][arow][ac]);
+                uint32_t bh[NP][4], bl[NP][4];   // n-tiles 2 np (regs 0, 1) and 2 np + 1 (regs 2, 3)
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) acc[a][c] = fmaf(av[a], bv[c], acc[a][c]);
-                    if (it == 0) accb[a] += av[a];
+                for (int np = 0; np < NP; ++np) {
+                    const int bc = chunk_at(16 * np + brow, 2 * kt + bcol / 8);
+                    ldsm_x4(bh[np], &sB[buf][0][16 * np + brow][bc]);
+                    ldsm_x4(bl[np], &sB[buf][1][16 * np + brow][bc]);
                 }
+#pragma unroll
+                for (int nt = 0; nt < 2 * NP; ++nt)
+                    mma_bf16(acc[0][nt], ah, bh[nt >> 1][2 * (nt & 1)], bh[nt >> 1][2 * (nt & 1) + 1]);
+#pragma unroll
+                for (int nt = 0; nt < 2 * NP; ++nt)
+                    mma_bf16(acc[1 % SETS][nt], ah, bl[nt >> 1][2 * (nt & 1)], bl[nt >> 1][2 * (nt & 1) + 1]);
+#pragma unroll
+                for (int nt = 0; nt < 2 * NP; ++nt)
+                    mma_bf16(acc[2 % SETS][nt], al, bh[nt >> 1][2 * (nt & 1)], bh[nt >> 1][2 * (nt & 1) + 1]);
             }
         }
-        __syncthreads();
     }
     const int len = na * nb + (bias ? na : 0);
     float* pb = part + (int64_t)blockIdx.x * len;
-    if (active) {
+    if (mts) {
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            const int o = 4 * ot + a;
-            if (o >= na) continue;
+        for (int nt = 0; nt < 2 * NP; ++nt) {
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int i = 4 * it + c;
-                if (i < nb) pb[o * nb + i] = acc[a][c];
+            for (int h = 0; h < 2; ++h) {
+                const int o = warp * 16 + g + 8 * h;
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const int i = nt * 8 + 2 * q + c;
+                    float v = acc[0][nt][2 * h + c];
+#pragma unroll
+                    for (int st = 1; st < SETS; ++st) v += acc[st][nt][2 * h + c];
+                    if (o < na && i < nb) pb[o * nb + i] = v;
+                }
             }
-            if (bias && it == 0) pb[na * nb + o] = accb[a];
         }
+    }
+    if (bias) {
+        sbias[spair][scol] = accb[0];
+        sbias[spair][scol + 32] = accb[1];
+        __syncthreads();
+        if (tid < na) pb[na * nb + tid] = (sbias[0][tid] + sbias[1][tid]) + (sbias[2][tid] + sbias[3][tid]);
     }
 }
 
@@ -1006,20 +1314,20 @@ static void gnn_forward(aimx_ctx* ctx, const __nv_bfloat16* w, int K, int L, flo
     for (int l = 0; l < L; ++l) {
         const float* Hp = G.d_H + l * NW;
         float* Pl = G.d_P + l * NW;
-        k_node_gemm<false><<<nodeblk, 256, 0, s>>>(Hp, w + lay.B[l], nullptr, nullptr, Pl, N, 0, 0);
+        k_node_gemm<false><<<nodeblk, 128, 0, s>>>(Hp, w + lay.B[l], nullptr, nullptr, Pl, N, 0, 0);
         k_edge_message<<<warpblk, 256, 0, s>>>(Pl, G.d_e, w, lay.C[l], lay.c[l], ctx->d_row_ptr, ctx->d_cols,
                                                G.d_deginv, N, G.d_S);
-        k_node_gemm<false><<<nodeblk, 256, 0, s>>>(Hp, w + lay.D[l], w + lay.d[l], G.d_S, G.d_H + (l + 1) * NW, N, 1,
+        k_node_gemm<false><<<nodeblk, 128, 0, s>>>(Hp, w + lay.D[l], w + lay.d[l], G.d_S, G.d_H + (l + 1) * NW, N, 1,
                                                    0);
     }
     const float* HL = G.d_H + L * NW;
-    k_node_gemm<false><<<nodeblk, 256, 0, s>>>(HL, w + lay.Ua, nullptr, nullptr, G.d_Pa, N, 0, 0);
-    k_node_gemm<false><<<nodeblk, 256, 0, s>>>(HL, w + lay.Ub, nullptr, nullptr, G.d_Pb, N, 0, 0);
+    k_node_gemm<false><<<nodeblk, 128, 0, s>>>(HL, w + lay.Ua, nullptr, nullptr, G.d_Pa, N, 0, 0);
+    k_node_gemm<false><<<nodeblk, 128, 0, s>>>(HL, w + lay.Ub, nullptr, nullptr, G.d_Pb, N, 0, 0);
     if (K == 2)
-        k_head_forward<2><<<gb(nnz, 128), 128, 0, s>>>(G.d_Pa, G.d_Pb, G.d_e, G.d_basis, w, lay.Uc, lay.u, lay.E,
+        k_head_forward<2><<<gb(nnz, 64), 128, 0, s>>>(G.d_Pa, G.d_Pb, G.d_e, G.d_basis, w, lay.Uc, lay.u, lay.E,
                                                        lay.f, G.d_rows, ctx->d_cols, nnz, G.d_o, U);
     else
-        k_head_forward<8><<<gb(nnz, 128), 128, 0, s>>>(G.d_Pa, G.d_Pb, G.d_e, G.d_basis, w, lay.Uc, lay.u, lay.E,
+        k_head_forward<8><<<gb(nnz, 64), 128, 0, s>>>(G.d_Pa, G.d_Pb, G.d_e, G.d_basis, w, lay.Uc, lay.u, lay.E,
                                                        lay.f, G.d_rows, ctx->d_cols, nnz, G.d_o, U);
     k_diag_head<<<gb((int64_t)N * K), 256, 0, s>>>(HL, w, lay.G, lay.g, N, K, G.d_g);
     AIMX_CUDA_TRY(cudaGetLastError());
@@ -1044,7 +1352,14 @@ template <int MODE>
 static void rows_wgrad(const float* A, const float* Ge, const float* basis, int K, int na, const float* B, int nb,
                        int bias, int64_t R, float* part, float* grad, cudaStream_t s) {
     const int64_t chunk = std::max<int64_t>((R + kWgradBlocks - 1) / kWgradBlocks, 1);
-    k_rows_wgrad<MODE><<<kWgradBlocks, 256, 0, s>>>(A, Ge, basis, K, na, B, nb, bias, R, chunk, part);
+    if constexpr (MODE == 0) {
+        if (nb <= 16) {
+            k_rows_wgrad<0, 1><<<kWgradBlocks, 128, 0, s>>>(A, Ge, basis, K, na, B, nb, bias, R, chunk, part);
+            reduce_into(part, kWgradBlocks, (int64_t)na * nb + (bias ? na : 0), grad, s);
+            return;
+        }
+    }
+    k_rows_wgrad<MODE, 4><<<kWgradBlocks, 128, 0, s>>>(A, Ge, basis, K, na, B, nb, bias, R, chunk, part);
     reduce_into(part, kWgradBlocks, (int64_t)na * nb + (bias ? na : 0), grad, s);
 }
 
@@ -1191,11 +1506,9 @@ static double gnn_loss_grad(aimx_gnn* net, aimx_ctx* ctx, double freq, int P, co
         // edge head: dE, df; dz; dUc, du; dza, dzb; dUa, dUb
         rows_wgrad<1>(nullptr, net->d_Ge, G.d_basis, K, K * kNB, net->d_U, kW, 1, nnz, part, grad + lay.E, s);
         if (K == 2)
-            k_head_backward<2><<<gb(nnz, 128), 128, 0, s>>>(net->d_U, net->d_Ge, G.d_basis, w, lay.Uc, lay.u, lay.E,
-                                                            lay.f, G.d_rows, ctx->d_cols, nnz, net->d_DZ);
+            k_head_backward<2><<<gb(nnz, 64), 128, 0, s>>>(net->d_U, net->d_Ge, G.d_basis, w, lay.E, nnz, net->d_DZ);
         else
-            k_head_backward<8><<<gb(nnz, 128), 128, 0, s>>>(net->d_U, net->d_Ge, G.d_basis, w, lay.Uc, lay.u, lay.E,
-                                                            lay.f, G.d_rows, ctx->d_cols, nnz, net->d_DZ);
+            k_head_backward<8><<<gb(nnz, 64), 128, 0, s>>>(net->d_U, net->d_Ge, G.d_basis, w, lay.E, nnz, net->d_DZ);
         rows_wgrad<0>(net->d_DZ, nullptr, nullptr, 0, kW, G.d_e, kNed, 1, nnz, part, grad + lay.Uc, s);
         k_head_node_back<<<gb((int64_t)N * 32), 256, 0, s>>>(net->d_DZ, ctx->d_row_ptr, G.d_trans, N, dza, dzb);
         rows_wgrad<0>(dza, nullptr, nullptr, 0, kW, HL, kW, 0, N, part, grad + lay.Ua, s);
@@ -1204,22 +1517,22 @@ static double gnn_loss_grad(aimx_gnn* net, aimx_ctx* ctx, double freq, int P, co
         rows_wgrad<0>(net->d_Gn, nullptr, nullptr, 0, K, HL, kW, 1, N, part, grad + lay.G, s);
         // dH_L = dza Ua + dzb Ub + Gn G
         const unsigned nodeblk = (unsigned)((N + 63) / 64);
-        k_node_gemm<true><<<nodeblk, 256, 0, s>>>(dza, w + lay.Ua, nullptr, nullptr, dH, N, 0, 0);
-        k_node_gemm<true><<<nodeblk, 256, 0, s>>>(dzb, w + lay.Ub, nullptr, nullptr, dH, N, 0, 1);
+        k_node_gemm<true><<<nodeblk, 128, 0, s>>>(dza, w + lay.Ua, nullptr, nullptr, dH, N, 0, 0);
+        k_node_gemm<true><<<nodeblk, 128, 0, s>>>(dzb, w + lay.Ub, nullptr, nullptr, dH, N, 0, 1);
         k_diag_head_back<<<gb(NW), 256, 0, s>>>(net->d_Gn, w, lay.G, N, K, dH);
-        const unsigned pblk = kPersistWarps / 8;
+        const unsigned pblk = kPersistWarps / 4;
         for (int l = L - 1; l >= 0; --l) {
             const float* Hl = G.d_H + (l + 1) * NW;
             const float* Hp = G.d_H + l * NW;
             const float* Pl = G.d_P + l * NW;
             k_relu_back<<<gb(NW), 256, 0, s>>>(dH, Hl, G.d_deginv, N, dU, dS);
             rows_wgrad<0>(dU, nullptr, nullptr, 0, kW, Hp, kW, 1, N, part, grad + lay.D[l], s);
-            k_edge_backward<<<pblk, 256, 0, s>>>(Pl, G.d_e, w, lay.C[l], lay.c[l], ctx->d_row_ptr, ctx->d_cols,
+            k_edge_backward<<<pblk, 128, 0, s>>>(Pl, G.d_e, w, lay.C[l], lay.c[l], ctx->d_row_ptr, ctx->d_cols,
                                                  G.d_trans, dS, N, dP, part);
             reduce_into(part, kPersistWarps, kW * kNed + kW, grad + lay.C[l], s);
             rows_wgrad<0>(dP, nullptr, nullptr, 0, kW, Hp, kW, 0, N, part, grad + lay.B[l], s);
-            k_node_gemm<true><<<nodeblk, 256, 0, s>>>(dU, w + lay.D[l], nullptr, nullptr, dT, N, 0, 0);
-            k_node_gemm<true><<<nodeblk, 256, 0, s>>>(dP, w + lay.B[l], nullptr, nullptr, dT, N, 0, 1);
+            k_node_gemm<true><<<nodeblk, 128, 0, s>>>(dU, w + lay.D[l], nullptr, nullptr, dT, N, 0, 0);
+            k_node_gemm<true><<<nodeblk, 128, 0, s>>>(dP, w + lay.B[l], nullptr, nullptr, dT, N, 0, 1);
             std::swap(dH, dT);
         }
         k_relu_back<<<gb(NW), 256, 0, s>>>(dH, G.d_H, G.d_deginv, N, dU, nullptr);
