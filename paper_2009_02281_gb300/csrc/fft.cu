@@ -14,6 +14,7 @@
 
 #include "aimx_internal.h"
 #include "cplx.cuh"
+#include "regfft.cuh"
 
 namespace aimx {
 
@@ -194,6 +195,159 @@ __global__ void k_fft_cols(cplx_t<T>* base, int64_t nouter, int D1, int64_t S1, 
     }
 }
 
+// ------------------------------------------------------------------ register-line FFTs
+//
+// One thread holds one whole line of compile-time length L in registers (reg_fft_any:
+// radix 4/2 and one radix-3 pass, twiddles as instruction immediates).  Only the first nin
+// inputs are read (the rest is the zero padding) and only the first nout outputs are written
+// (the pruned inverse).  Lengths without a register kernel take the shared-memory kernels
+// above, which read and write whole lines.
+
+// Strided lines as in k_fft_cols; consecutive threads take consecutive x (coalesced).
+template <class C, int L, bool INV>
+__global__ void __launch_bounds__(128) k_fft_cols_reg(C* base, int64_t nlines, int D1, int64_t S1, int64_t S2,
+                                                      int64_t S, int Mx, int nin, int nout) {
+    using R = decltype(C{}.x);
+    const int64_t line = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (line >= nlines) return;
+    const int64_t o = line / Mx;
+    const int x = (int)(line - o * Mx);
+    C* lb = base + (o / D1) * S1 + (o % D1) * S2 + x;
+    C v[L];
+#pragma unroll
+    for (int p = 0; p < L; ++p) v[p] = p < nin ? lb[(int64_t)p * S] : mk(R(0), R(0));
+    reg_fft_any<C, L, INV>(v);
+#pragma unroll
+    for (int p = 0; p < L; ++p)
+        if (p < nout) lb[(int64_t)p * S] = v[p];
+}
+
+// Contiguous rows as in k_fft_rows, kRowsReg rows per block staged through shared memory
+// (coalesced row loads and stores), one row per thread in registers.
+constexpr int kRowsReg = 64;
+
+template <class C, int L, bool INV>
+__global__ void __launch_bounds__(kRowsReg) k_fft_rows_reg(C* base, int64_t nrows, int D1, int D2, int64_t S1,
+                                                           int64_t S2, int64_t S3, int nin, int nout) {
+    using R = decltype(C{}.x);
+    constexpr int PITCH = L + 1;
+    extern __shared__ unsigned char smraw[];
+    __shared__ C* rowp[kRowsReg];
+    C* t = reinterpret_cast<C*>(smraw);
+    const int64_t r0 = (int64_t)blockIdx.x * kRowsReg;
+    const int nl = (int)min((int64_t)kRowsReg, nrows - r0);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NW = kRowsReg / 32;
+    if ((int)threadIdx.x < nl) {   // row start of row threadIdx.x (64-bit index arithmetic once per row)
+        const int64_t r = r0 + threadIdx.x;
+        const int64_t c = r % D2, b = (r / D2) % D1, a = r / ((int64_t)D1 * D2);
+        rowp[threadIdx.x] = base + a * S1 + b * S2 + c * S3;
+    }
+    __syncthreads();
+    // each warp copies whole rows, its lanes on consecutive points
+    for (int rr = warp; rr < nl; rr += NW) {
+        const C* src = rowp[rr];
+        for (int p = lane; p < nin; p += 32) t[rr * PITCH + p] = src[p];
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < nl) {
+        C v[L];
+#pragma unroll
+        for (int p = 0; p < L; ++p) v[p] = p < nin ? t[threadIdx.x * PITCH + p] : mk(R(0), R(0));
+        reg_fft_any<C, L, INV>(v);
+#pragma unroll
+        for (int p = 0; p < L; ++p)
+            if (p < nout) t[threadIdx.x * PITCH + p] = v[p];
+    }
+    __syncthreads();
+    for (int rr = warp; rr < nl; rr += NW) {
+        C* dst = rowp[rr];
+        for (int p = lane; p < nout; p += 32) dst[p] = t[rr * PITCH + p];
+    }
+}
+
+template <class C, int L, bool INV>
+static void launch_cols_reg(C* g, int64_t nouter, int D1, int64_t S1, int64_t S2, int64_t S, int Mx, int nin,
+                            int nout, cudaStream_t s) {
+    const int64_t nlines = nouter * Mx;
+    k_fft_cols_reg<C, L, INV><<<(unsigned)((nlines + 127) / 128), 128, 0, s>>>(g, nlines, D1, S1, S2, S, Mx, nin,
+                                                                               nout);
+}
+
+template <class C, int L, bool INV>
+static void launch_rows_reg(C* g, int64_t nrows, int D1, int D2, int64_t S1, int64_t S2, int64_t S3, int nin,
+                            int nout, cudaStream_t s) {
+    const size_t sm = (size_t)kRowsReg * (L + 1) * sizeof(C);
+    static bool attr[64] = {};   // per device: the dynamic shared-memory opt-in of this instantiation
+    int dev = 0;
+    AIMX_CUDA_TRY(cudaGetDevice(&dev));
+    if (sm > 48 * 1024 && dev < 64 && !attr[dev]) {
+        AIMX_CUDA_TRY(cudaFuncSetAttribute(k_fft_rows_reg<C, L, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)sm));
+        attr[dev] = true;
+    }
+    k_fft_rows_reg<C, L, INV><<<(unsigned)((nrows + kRowsReg - 1) / kRowsReg), kRowsReg, sm, s>>>(
+        g, nrows, D1, D2, S1, S2, S3, nin, nout);
+}
+
+// launch arguments of the register-line kernels, dispatched on the compile-time length
+template <class C>
+struct RowsRun {
+    C* g;
+    int64_t nrows;
+    int D1, D2;
+    int64_t S1, S2, S3;
+    int nin, nout;
+    bool inv;
+    cudaStream_t s;
+    template <int LL>
+    void run() {
+        if (inv)
+            launch_rows_reg<C, LL, true>(g, nrows, D1, D2, S1, S2, S3, nin, nout, s);
+        else
+            launch_rows_reg<C, LL, false>(g, nrows, D1, D2, S1, S2, S3, nin, nout, s);
+    }
+};
+template <class C>
+struct ColsRun {
+    C* g;
+    int64_t nouter;
+    int D1;
+    int64_t S1, S2, S;
+    int Mx, nin, nout;
+    bool inv;
+    cudaStream_t s;
+    template <int LL>
+    void run() {
+        if (inv)
+            launch_cols_reg<C, LL, true>(g, nouter, D1, S1, S2, S, Mx, nin, nout, s);
+        else
+            launch_cols_reg<C, LL, false>(g, nouter, D1, S1, S2, S, Mx, nin, nout, s);
+    }
+};
+
+// Calls f.template run<L>() for the register-line lengths of this precision; false if L has none.
+template <class C, class F>
+static bool reg_length_dispatch(int L, F&& f) {
+    // FP32 lines up to 64 points, FP64 lines up to 32 (a line's values fill at most half of
+    // the 255 registers a thread can hold)
+    constexpr bool sp = sizeof(C) == sizeof(float2);
+    switch (L) {
+        case 16: f.template run<16>(); return true;
+        case 24: f.template run<24>(); return true;
+        case 32: f.template run<32>(); return true;
+        case 48:
+            if (!sp) return false;
+            f.template run<sp ? 48 : 16>();
+            return true;
+        case 64:
+            if (!sp) return false;
+            f.template run<sp ? 64 : 16>();
+            return true;
+        default: return false;
+    }
+}
+
 // (log2 P, 1) for L = 3 * 2^logP, (log2 L, 0) for L = 2^logP
 static void fft_factors(int L, int& logP, int& r3) {
     r3 = (L % 3 == 0) ? 1 : 0;
@@ -205,8 +359,16 @@ static void fft_factors(int L, int& logP, int& r3) {
 
 template <class T>
 static void fft_rows(cplx_t<T>* g, int64_t nrows, int D1, int D2, int64_t S1, int64_t S2, int64_t S3,
-                     int L, bool inv, cudaStream_t s) {
+                     int L, bool inv, cudaStream_t s, int nin = -1, int nout = -1) {
     if (nrows <= 0) return;
+    using C = cplx_t<T>;
+    nin = nin < 0 ? L : nin;
+    nout = nout < 0 ? L : nout;
+    RowsRun<C> run{g, nrows, D1, D2, S1, S2, S3, nin, nout, inv, s};
+    if (reg_length_dispatch<C>(L, run)) {
+        AIMX_CUDA_TRY(cudaGetLastError());
+        return;
+    }
     int RPB = std::max(1, 8192 / L);
     size_t sm = (size_t)RPB * (L + 1) * sizeof(cplx_t<T>);
     if (sm > 48 * 1024) {
@@ -223,8 +385,16 @@ static void fft_rows(cplx_t<T>* g, int64_t nrows, int D1, int D2, int64_t S1, in
 
 template <class T>
 static void fft_cols(cplx_t<T>* g, int64_t nouter, int D1, int64_t S1, int64_t S2, int64_t S, int Mx,
-                     int L, bool inv, cudaStream_t s) {
+                     int L, bool inv, cudaStream_t s, int nin = -1, int nout = -1) {
     if (nouter <= 0) return;
+    using C = cplx_t<T>;
+    nin = nin < 0 ? L : nin;
+    nout = nout < 0 ? L : nout;
+    ColsRun<C> run{g, nouter, D1, S1, S2, S, Mx, nin, nout, inv, s};
+    if (reg_length_dispatch<C>(L, run)) {
+        AIMX_CUDA_TRY(cudaGetLastError());
+        return;
+    }
     int TC = sizeof(T) == 4 ? 32 : 16;
     TC = std::min(TC, Mx);
     while ((size_t)TC * (L + 1) * sizeof(cplx_t<T>) > 48 * 1024 && TC > 1) TC >>= 1;
@@ -248,11 +418,20 @@ void fft3d_padded(T* grid, int batch, const int M[3], const int act[3], bool inv
     C* g = reinterpret_cast<C*>(grid);
     const int64_t Mx = M[0], My = M[1], Mz = M[2];
     const int64_t SB = Mx * My * Mz;
+    // forward passes read only the non-zero inputs (first act), inverse passes write only the
+    // outputs later passes and the interpolation read (first act); register-line kernels use this
+    auto in = [&](int a) { return inverse ? M[a] : act[a]; };
+    auto out = [&](int a) { return inverse ? act[a] : M[a]; };
     auto xpass = [&]() {
-        fft_rows<T>(g, (int64_t)batch * act[2] * act[1], act[2], act[1], SB, My * Mx, Mx, M[0], inverse, s);
+        fft_rows<T>(g, (int64_t)batch * act[2] * act[1], act[2], act[1], SB, My * Mx, Mx, M[0], inverse, s, in(0),
+                    out(0));
     };
-    auto ypass = [&]() { fft_cols<T>(g, (int64_t)batch * act[2], act[2], SB, My * Mx, Mx, M[0], M[1], inverse, s); };
-    auto zpass = [&]() { fft_cols<T>(g, (int64_t)batch * My, (int)My, SB, Mx, My * Mx, M[0], M[2], inverse, s); };
+    auto ypass = [&]() {
+        fft_cols<T>(g, (int64_t)batch * act[2], act[2], SB, My * Mx, Mx, M[0], M[1], inverse, s, in(1), out(1));
+    };
+    auto zpass = [&]() {
+        fft_cols<T>(g, (int64_t)batch * My, (int)My, SB, Mx, My * Mx, M[0], M[2], inverse, s, in(2), out(2));
+    };
     if (!inverse) {
         xpass();
         ypass();
@@ -269,6 +448,22 @@ void fft3d_full(T* grid, int batch, const int M[3], bool inverse, cudaStream_t s
     int act[3] = {M[0], M[1], M[2]};
     fft3d_padded<T>(grid, batch, M, act, inverse, s);
 }
+
+// True when every pass of fft3d_padded runs on register lines for this precision: the forward
+// transform then reads only the active input region, so the padding needs no zeroing.
+struct LenProbe {
+    template <int LL>
+    void run() {}
+};
+template <class T>
+bool fft3d_reads_active_only(const int M[3]) {
+    LenProbe probe;
+    for (int a = 0; a < 3; ++a)
+        if (!reg_length_dispatch<cplx_t<T>>(M[a], probe)) return false;
+    return true;
+}
+template bool fft3d_reads_active_only<float>(const int*);
+template bool fft3d_reads_active_only<double>(const int*);
 
 template void fft3d_padded<float>(float*, int, const int*, const int*, bool, cudaStream_t);
 template void fft3d_padded<double>(double*, int, const int*, const int*, bool, cudaStream_t);

@@ -19,13 +19,13 @@ __host__ __device__ constexpr int brevc(int v, int bits) {
     return r;
 }
 
-// Twiddles as compile-time constants.  Every line length here is a power of two <= 128, so
-// all twiddles are W_128^k = e^{-2 pi i k / 128}.  The angle is reduced exactly with integers
-// to [0, pi/4] (quadrant, then the complementary angle), where Taylor series of sin and cos
-// summed in double precision are accurate to rounding; the table is then rounded to FP32.
-// Indices are compile-time constants after unrolling, so the values become instruction
-// immediates instead of constant-memory loads.
-constexpr int kTwTab = 128;
+// Twiddles as compile-time constants.  Every line length here divides 384 = 3 * 128 (powers
+// of two up to 128 and 3 * 2^k up to 384), so all twiddles are W_384^k = e^{-2 pi i k / 384}.
+// The angle is reduced exactly with integers to [0, pi/4] (quadrant, then the complementary
+// angle), where Taylor series of sin and cos summed in double precision are accurate to
+// rounding; FP32 lines round the table to FP32.  Indices are compile-time constants after
+// unrolling, so the values become instruction immediates instead of constant-memory loads.
+constexpr int kTwTab = 384;
 __host__ __device__ constexpr double taylor_sin(double x) {
     double x2 = x * x, term = x, sum = x;
     for (int n = 1; n < 12; ++n) {
@@ -43,14 +43,14 @@ __host__ __device__ constexpr double taylor_cos(double x) {
     return sum;
 }
 struct TwTable {
-    float re[kTwTab];
-    float im[kTwTab];
+    double re[kTwTab];
+    double im[kTwTab];
 };
 __host__ __device__ constexpr TwTable make_tw_table() {
     TwTable t{};
     constexpr double two_pi = 6.283185307179586476925286766559;
     for (int k = 0; k < kTwTab; ++k) {
-        const int q = k / (kTwTab / 4), r = k % (kTwTab / 4);   // angle = q pi/2 + 2 pi r / 128
+        const int q = k / (kTwTab / 4), r = k % (kTwTab / 4);   // angle = q pi/2 + 2 pi r / 384
         double c0 = 0.0, s0 = 0.0;
         if (r <= kTwTab / 8) {
             const double a = two_pi * r / kTwTab;
@@ -63,19 +63,32 @@ __host__ __device__ constexpr TwTable make_tw_table() {
         }
         const double c = q == 0 ? c0 : q == 1 ? -s0 : q == 2 ? -c0 : s0;
         const double sn = q == 0 ? s0 : q == 1 ? c0 : q == 2 ? -s0 : -c0;
-        t.re[k] = (float)c;
-        t.im[k] = (float)(-sn);
+        t.re[k] = c;
+        t.im[k] = -sn;
     }
     return t;
 }
 
 // W_M^k (forward) or its conjugate (inverse) for k and M compile-time constants after
-// unrolling, M a power of two dividing 128
+// unrolling, M dividing 384
 template <bool INV>
 __device__ __forceinline__ float2 twc(int k, int M) {
     constexpr TwTable tab = make_tw_table();
     const int i = (k % M) * (kTwTab / M);
-    return make_float2(tab.re[i], INV ? -tab.im[i] : tab.im[i]);
+    return make_float2((float)tab.re[i], INV ? -(float)tab.im[i] : (float)tab.im[i]);
+}
+template <bool INV>
+__device__ __forceinline__ double2 twc_d(int k, int M) {
+    constexpr TwTable tab = make_tw_table();
+    const int i = (k % M) * (kTwTab / M);
+    return make_double2(tab.re[i], INV ? -tab.im[i] : tab.im[i]);
+}
+template <class C, bool INV>
+__device__ __forceinline__ C tw_any(int k, int M) {
+    if constexpr (sizeof(C) == sizeof(float2))
+        return twc<INV>(k, M);
+    else
+        return twc_d<INV>(k, M);
 }
 
 __host__ __device__ constexpr bool pow4c(int v) { return v == 1 || (v % 4 == 0 && pow4c(v / 4)); }
@@ -215,6 +228,77 @@ __device__ __forceinline__ void reg_fft(float2 (&v)[L]) {
                 }
                 v[start + k] = a + b;
                 v[start + k + half] = a - b;
+            }
+        }
+    }
+}
+
+// Whole-line register FFT of any length L = 2^k (k >= 1) or 3 * 2^k dividing 384, on float2
+// or double2.  Lengths 3 P: the decimated sequences x[3 n + r] are transformed (length P)
+// and recombined by one radix-3 pass, X[k + m P] = sum_r W_L^{r k} W_3^{r m} Y_r[k], whose
+// cube roots of unity are -1/2 and +-(sqrt 3 / 2) i.  FP32 powers of two take reg_fft
+// (radix 4, packed sums); FP64 powers of two a radix-2 decimation in time.  Natural order
+// in and out; INV gives the unnormalised inverse.
+template <class C, int L, bool INV>
+__device__ __forceinline__ void reg_fft_any(C (&v)[L]) {
+    using R = decltype(C{}.x);
+    if constexpr (L == 1) {
+        return;
+    } else if constexpr (L % 3 == 0) {
+        constexpr int P = L / 3;
+        C y[3][P];
+#pragma unroll
+        for (int n = 0; n < P; ++n) {
+            y[0][n] = v[3 * n];
+            y[1][n] = v[3 * n + 1];
+            y[2][n] = v[3 * n + 2];
+        }
+        reg_fft_any<C, P, INV>(y[0]);
+        reg_fft_any<C, P, INV>(y[1]);
+        reg_fft_any<C, P, INV>(y[2]);
+        const R hs = (R)0.86602540378443864676;   // sqrt(3) / 2
+#pragma unroll
+        for (int k = 0; k < P; ++k) {
+            const C a = y[0][k];
+            const C b = k ? y[1][k] * tw_any<C, INV>(k, L) : y[1][k];
+            const C c = k ? y[2][k] * tw_any<C, INV>(2 * k, L) : y[2][k];
+            const C t = b + c, d = b - c;
+            const C m = a - (R)0.5 * t;
+            const C jd = INV ? mk(-hs * d.y, hs * d.x) : mk(hs * d.y, -hs * d.x);
+            v[k] = a + t;
+            v[k + P] = m + jd;
+            v[k + 2 * P] = m - jd;
+        }
+    } else if constexpr (sizeof(C) == sizeof(float2)) {
+        reg_fft<L, INV>(v);
+    } else {
+        constexpr int LOG = ilog2c(L);
+#pragma unroll
+        for (int i = 0; i < L; ++i) {
+            const int j = brevc(i, LOG);
+            if (j > i) {
+                const C t = v[i];
+                v[i] = v[j];
+                v[j] = t;
+            }
+        }
+#pragma unroll
+        for (int half = 1; half < L; half <<= 1) {
+#pragma unroll
+            for (int start = 0; start < L; start += 2 * half) {
+#pragma unroll
+                for (int k = 0; k < half; ++k) {
+                    const C a = v[start + k];
+                    C b = v[start + k + half];
+                    if (k == 0) {
+                    } else if (4 * k == 2 * half) {
+                        b = INV ? mk(-b.y, b.x) : mk(b.y, -b.x);
+                    } else {
+                        b = b * tw_any<C, INV>(k, 2 * half);
+                    }
+                    v[start + k] = a + b;
+                    v[start + k + half] = a - b;
+                }
             }
         }
     }
