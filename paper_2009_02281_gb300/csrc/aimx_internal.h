@@ -333,9 +333,10 @@ void fft3d_padded(T* grid, int batch, const int M[3], const int act[3], bool inv
                   cudaStream_t s);
 template <class T>
 void fft3d_full(T* grid, int batch, const int M[3], bool inverse, cudaStream_t s);
-// fft3d_padded reads only the active input region of a forward transform (no zero padding needed)
+// fft3d_padded of `batch` grids reads only the active input region of a forward transform (its
+// passes run on register lines, so no zero padding is needed)
 template <class T>
-bool fft3d_reads_active_only(const int M[3]);
+bool fft3d_reads_active_only(const int M[3], int batch);
 
 // kernelgen.cu
 template <class T>

@@ -213,13 +213,15 @@ __global__ void __launch_bounds__(128) k_fft_cols_reg(C* base, int64_t nlines, i
     const int64_t o = line / Mx;
     const int x = (int)(line - o * Mx);
     C* lb = base + (o / D1) * S1 + (o % D1) * S2 + x;
+    // L <= 64 and padded sides <= 4096, so a line spans L S < 2^31 elements: 32-bit point offsets
+    const int s32 = (int)S;
     C v[L];
 #pragma unroll
-    for (int p = 0; p < L; ++p) v[p] = p < nin ? lb[(int64_t)p * S] : mk(R(0), R(0));
+    for (int p = 0; p < L; ++p) v[p] = p < nin ? lb[p * s32] : mk(R(0), R(0));
     reg_fft_any<C, L, INV>(v);
 #pragma unroll
     for (int p = 0; p < L; ++p)
-        if (p < nout) lb[(int64_t)p * S] = v[p];
+        if (p < nout) lb[p * s32] = v[p];
 }
 
 // Contiguous rows as in k_fft_rows, kRowsReg rows per block staged through shared memory
@@ -329,17 +331,14 @@ struct ColsRun {
 // Calls f.template run<L>() for the register-line lengths of this precision; false if L has none.
 template <class C, class F>
 static bool reg_length_dispatch(int L, F&& f) {
-    // FP32 lines up to 64 points, FP64 lines up to 32 (a line's values fill at most half of
-    // the 255 registers a thread can hold)
+    // FP32 lines up to 64 points, FP64 lines up to 48 (a line's values take at most 192 of the
+    // 255 registers a thread can hold)
     constexpr bool sp = sizeof(C) == sizeof(float2);
     switch (L) {
         case 16: f.template run<16>(); return true;
         case 24: f.template run<24>(); return true;
         case 32: f.template run<32>(); return true;
-        case 48:
-            if (!sp) return false;
-            f.template run<sp ? 48 : 16>();
-            return true;
+        case 48: f.template run<48>(); return true;
         case 64:
             if (!sp) return false;
             f.template run<sp ? 64 : 16>();
@@ -359,13 +358,13 @@ static void fft_factors(int L, int& logP, int& r3) {
 
 template <class T>
 static void fft_rows(cplx_t<T>* g, int64_t nrows, int D1, int D2, int64_t S1, int64_t S2, int64_t S3,
-                     int L, bool inv, cudaStream_t s, int nin = -1, int nout = -1) {
+                     int L, bool inv, cudaStream_t s, int nin = -1, int nout = -1, bool reg = false) {
     if (nrows <= 0) return;
     using C = cplx_t<T>;
     nin = nin < 0 ? L : nin;
     nout = nout < 0 ? L : nout;
     RowsRun<C> run{g, nrows, D1, D2, S1, S2, S3, nin, nout, inv, s};
-    if (reg_length_dispatch<C>(L, run)) {
+    if (reg && reg_length_dispatch<C>(L, run)) {
         AIMX_CUDA_TRY(cudaGetLastError());
         return;
     }
@@ -385,13 +384,13 @@ static void fft_rows(cplx_t<T>* g, int64_t nrows, int D1, int D2, int64_t S1, in
 
 template <class T>
 static void fft_cols(cplx_t<T>* g, int64_t nouter, int D1, int64_t S1, int64_t S2, int64_t S, int Mx,
-                     int L, bool inv, cudaStream_t s, int nin = -1, int nout = -1) {
+                     int L, bool inv, cudaStream_t s, int nin = -1, int nout = -1, bool reg = false) {
     if (nouter <= 0) return;
     using C = cplx_t<T>;
     nin = nin < 0 ? L : nin;
     nout = nout < 0 ? L : nout;
     ColsRun<C> run{g, nouter, D1, S1, S2, S, Mx, nin, nout, inv, s};
-    if (reg_length_dispatch<C>(L, run)) {
+    if (reg && reg_length_dispatch<C>(L, run)) {
         AIMX_CUDA_TRY(cudaGetLastError());
         return;
     }
@@ -422,15 +421,17 @@ void fft3d_padded(T* grid, int batch, const int M[3], const int act[3], bool inv
     // outputs later passes and the interpolation read (first act); register-line kernels use this
     auto in = [&](int a) { return inverse ? M[a] : act[a]; };
     auto out = [&](int a) { return inverse ? act[a] : M[a]; };
+    const bool reg = fft3d_reads_active_only<T>(M, batch);   // all passes on register lines, or none
     auto xpass = [&]() {
         fft_rows<T>(g, (int64_t)batch * act[2] * act[1], act[2], act[1], SB, My * Mx, Mx, M[0], inverse, s, in(0),
-                    out(0));
+                    out(0), reg);
     };
     auto ypass = [&]() {
-        fft_cols<T>(g, (int64_t)batch * act[2], act[2], SB, My * Mx, Mx, M[0], M[1], inverse, s, in(1), out(1));
+        fft_cols<T>(g, (int64_t)batch * act[2], act[2], SB, My * Mx, Mx, M[0], M[1], inverse, s, in(1), out(1),
+                    reg);
     };
     auto zpass = [&]() {
-        fft_cols<T>(g, (int64_t)batch * My, (int)My, SB, Mx, My * Mx, M[0], M[2], inverse, s, in(2), out(2));
+        fft_cols<T>(g, (int64_t)batch * My, (int)My, SB, Mx, My * Mx, M[0], M[2], inverse, s, in(2), out(2), reg);
     };
     if (!inverse) {
         xpass();
@@ -455,15 +456,19 @@ struct LenProbe {
     template <int LL>
     void run() {}
 };
+// Every pass of a batch of `batch` grids on register lines: all three lengths have register
+// kernels and, in FP64 (up to 222 registers a thread), the z pass has lines enough to fill the
+// GPU at two blocks per SM; smaller FP64 batches keep the shared-memory kernels.
+constexpr int64_t kMinRegLinesF64 = 32768;
 template <class T>
-bool fft3d_reads_active_only(const int M[3]) {
+bool fft3d_reads_active_only(const int M[3], int batch) {
     LenProbe probe;
     for (int a = 0; a < 3; ++a)
         if (!reg_length_dispatch<cplx_t<T>>(M[a], probe)) return false;
-    return true;
+    return sizeof(T) == sizeof(float) || (int64_t)batch * M[0] * M[1] >= kMinRegLinesF64;
 }
-template bool fft3d_reads_active_only<float>(const int*);
-template bool fft3d_reads_active_only<double>(const int*);
+template bool fft3d_reads_active_only<float>(const int*, int);
+template bool fft3d_reads_active_only<double>(const int*, int);
 
 template void fft3d_padded<float>(float*, int, const int*, const int*, bool, cudaStream_t);
 template void fft3d_padded<double>(double*, int, const int*, const int*, bool, cudaStream_t);

@@ -353,7 +353,7 @@ static void generic_product(aimx_ctx* ctx, double freq, const MultiFreq* mf, int
         int nb = std::min(chunk, nrhs - b0);
         StageScope sc0(ctx, ST_G_PROJECT, s);
         // the register-line forward transform reads only the projected nodes; the others need zeros
-        if (ctx->path == 2 || !fft3d_reads_active_only<T>(ctx->M))
+        if (ctx->path == 2 || !fft3d_reads_active_only<T>(ctx->M, nb * F))
             AIMX_CUDA_TRY(cudaMemsetAsync(grid, 0, sizeof(C) * per_rhs * nb, s));
         int64_t tot = NG * nb;
         k_project<T><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
