@@ -1145,7 +1145,7 @@ def main():
     ap.add_argument("--gnn-eval-steps", type=int, default=1500, help="training steps of the generalisation study")
     ap.add_argument("--learned-form", default="charge", choices=["charge", "rwg"],
                     help="scalar-potential form of the generalisation study's contexts")
-    ap.add_argument("--batch-members", type=int, default=16,
+    ap.add_argument("--batch-members", type=int, default=48,
                     help="members of the seeded uneven batch to time (0 = skip; 48 = the full batch)")
     ap.add_argument("--path", type=int, default=0, choices=[0, 1], help="product path for the timed steps (aimx_set_path)")
     ap.add_argument("--solve-tol", type=float, default=1e-5)

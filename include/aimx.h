@@ -448,6 +448,15 @@ int aimx_wait_timeouts(int* count);
  * outstanding.  Process-wide on the current device.  Synchronous. */
 int aimx_set_wait_limit(int64_t cycles);
 
+/* Test hook: at most `cap` bases of one grid plane are kept in shared memory by
+ * the register inverse-xy kernel of the plane-fused FP32 product (the default,
+ * cap <= 0, is whatever fits in 200 KB).  A plane with more bases (a dense mesh
+ * on a coarse grid) sums its four fields' interpolation partials in the output
+ * array instead; both forms add in the same order, so the product is bitwise
+ * the same.  A small cap lets a test run that form on a small mesh.  Host-side
+ * setting of ctx, effective from the next product.  Errors: AIMX_E_ARG (null ctx). */
+int aimx_set_plane_cap(aimx_ctx* ctx, int cap);
+
 /* Time the FP32 product of nrhs right-hand sides at freq under every candidate
  * schedule (the variants the grid allows x passes {all, nrhs/2, nrhs/4 with at
  * least 4}), two untimed and three timed products each with CUDA events on

@@ -97,6 +97,7 @@ _SIGS = [
     ("aimx_get_schedule", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("aimx_wait_timeouts", ctypes.c_int, [ctypes.c_void_p]),
     ("aimx_set_wait_limit", ctypes.c_int, [ctypes.c_int64]),
+    ("aimx_set_plane_cap", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("aimx_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_char_p, ctypes.c_void_p,
                                      ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     ("aimx_export_aim_near", ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p]),
@@ -457,6 +458,11 @@ class Context:
     def set_linear_term(self, enable=True):
         """Linear-term modification of Sec. III-A-3 on overlapping pairs (built on the first enable)."""
         self._check(self._lib.aimx_set_linear_term(self._ctx, 1 if enable else 0))
+
+    def set_plane_cap(self, cap):
+        """Test hook (aimx_set_plane_cap): bases per grid plane kept in shared memory by the
+        register inverse-xy kernel; <= 0 restores the default."""
+        self._check(self._lib.aimx_set_plane_cap(self._ctx, int(cap)))
 
     def set_schedule(self, variant, pass_=0):
         """Product schedule: variant 0 fused/register, 1 fused/shared memory, 2 generic; RHS per pass (0 = all)."""

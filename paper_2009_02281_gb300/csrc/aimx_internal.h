@@ -278,6 +278,7 @@ struct aimx_ctx {
     int* d_nb_ucols = nullptr;     // [sum of unions] internal column ids, ascending per block
     float4* d_nb_ent = nullptr;    // [nnz] CSR order: (union-local column as int bits, N^A, N^Phi, N^K or Gram)
     int max_plane_bases = 0;
+    int plane_cap = 0;                  // test hook: bases per plane kept in shared memory (0: all that fit)
     int* d_plane = nullptr;        // [2][Nz] plane_lo then plane_hi
     int path = 0;                  // 0 = automatic, 1 = generic FFT path, 2 = generic with cuFFT (comparison)
     int cufft_plan[2] = {0, 0};    // cached cuFFT plans (FP32, FP64) of the comparison path

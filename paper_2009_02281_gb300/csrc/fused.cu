@@ -42,6 +42,8 @@ constexpr int kRG = 8;     // RHS per z-pass block (kernel spectra reuse)
 constexpr int kFinalRows = 32;
 constexpr int kFinalB = 64;
 
+static bool reg_shape(const aimx_ctx* ctx);
+
 bool fused_supported(const aimx_ctx* ctx) {
     if (ctx->form == AIMX_CFIE) return false;   // the CFIE's K_g interpolation runs on the generic path
     for (int a = 0; a < 3; ++a) {
@@ -53,9 +55,11 @@ bool fused_supported(const aimx_ctx* ctx) {
     if (Nx > 4096 || Ny > 4096 || 2 * Nz > 4096) return false;
     if ((size_t)ctx->F * kTX * (2 * Nz + 1) * sizeof(float2) > 96 * 1024) return false;
     if (kTX * 2 * Nz > 4 * kThreads) return false;
+    // the shared-memory inverse kernel (schedule variant 1, or shapes without register kernels)
+    // keeps a plane's bases in shared memory
     int mpb = 0;
     for (int z = 0; z < Nz; ++z) mpb = std::max(mpb, ctx->plane_hi[z] - ctx->plane_lo[z]);
-    if ((size_t)mpb * sizeof(float2) > 64 * 1024) return false;
+    if ((size_t)mpb * sizeof(float2) > 64 * 1024 && !(reg_shape(ctx) && ctx->sched_variant != 1)) return false;
     return true;
 }
 
@@ -893,18 +897,18 @@ __global__ void __launch_bounds__(2 * F * 8) k_zpass_tma(const __grid_constant__
 // K4 (register form): inverse of K2 plus the interpolation partials.
 // Charge form (tpart given, EFIE): the rho field's output plane is interpolated with the pulse
 // weights per triangle touching the plane (partials tpart[b][slot][t]) instead of per basis.
-template <int N, bool CHG>
+template <int N, bool CHG, bool BIG>
 __global__ void __launch_bounds__(2 * N) k_xy_inv_reg(const float2* __restrict__ S, const float* __restrict__ w,
                                                       const int* __restrict__ anc, const int* __restrict__ plane_lo,
                                                       const int* __restrict__ plane_hi, float2* part, int F, int Nz,
                                                       int Ntot, int P, const int* __restrict__ tanc,
                                                       const int* __restrict__ tplane, const float* __restrict__ lps,
-                                                      float2* tpart, int nt) {
+                                                      float2* tpart, int nt, int cap) {
     extern __shared__ float2 sm[];
     constexpr int PITCH = N + 1;
     float2* acc = sm + 2 * N * PITCH;
     const int z = blockIdx.x, grp = blockIdx.y, b = blockIdx.z;
-    int2* meta = reinterpret_cast<int2*>(acc + (plane_hi[z] - plane_lo[z]));
+    int2* meta = reinterpret_cast<int2*>(acc + (BIG ? min(plane_hi[z] - plane_lo[z], cap) : plane_hi[z] - plane_lo[z]));
     const int px = threadIdx.x / N, r = threadIdx.x - px * N;
     float2* pl = sm + px * N * PITCH;
     float2* O = sm;                       // parity-0 plane doubles as the output plane
@@ -913,12 +917,25 @@ __global__ void __launch_bounds__(2 * N) k_xy_inv_reg(const float2* __restrict__
     const int nb = hi - lo;
     const int U = P * P * P;
     // per basis touching this plane: stencil corner (sx, sy) in the plane and the offset of its
-    // weights for this plane's stencil slot, computed once and reused for the four fields
-    for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+    // weights for this plane's stencil slot, computed once and reused for the four fields.  A
+    // plane with more bases than shared memory holds (cap) recomputes them per field and sums
+    // the four fields' partials in the output array instead (same order, so the same sums).
+    const bool gl = BIG && nb > cap;   // only instantiated for contexts with such planes
+    auto meta_of = [&](int k) {
         const int i = lo + k;
-        const int sx = anc[3 * i], sy = anc[3 * i + 1], slot = z - anc[3 * i + 2];
-        acc[k] = make_float2(0.f, 0.f);
-        meta[k] = make_int2(sy * PITCH + sx, slot * P * P * Ntot + i);
+        return make_int2(anc[3 * i + 1] * PITCH + anc[3 * i], (z - anc[3 * i + 2]) * P * P * Ntot + i);
+    };
+    auto part_at = [&](int k) -> float2& {
+        const int i = lo + k;
+        return part[(((int64_t)b * G + grp) * P + (z - anc[3 * i + 2])) * Ntot + i];
+    };
+    if (!gl) {
+        for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+            const int i = lo + k;
+            const int sx = anc[3 * i], sy = anc[3 * i + 1], slot = z - anc[3 * i + 2];
+            acc[k] = make_float2(0.f, 0.f);
+            meta[k] = make_int2(sy * PITCH + sx, slot * P * P * Ntot + i);
+        }
     }
     float2 v[N];
 #pragma unroll 1
@@ -981,7 +998,7 @@ __global__ void __launch_bounds__(2 * N) k_xy_inv_reg(const float2* __restrict__
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     kk[j] = k + j * bd;
-                    m[j] = meta[kk[j] < nb ? kk[j] : k];
+                    m[j] = gl ? meta_of(kk[j] < nb ? kk[j] : k) : meta[kk[j] < nb ? kk[j] : k];
                     // field-major weights ws[fl][u][i]: neighbouring bases of one slot are adjacent
                     const float* wj = w + (int64_t)fl * U * Ntot + m[j].y;
 #pragma unroll
@@ -994,7 +1011,12 @@ __global__ void __launch_bounds__(2 * N) k_xy_inv_reg(const float2* __restrict__
                     for (int uy = 0; uy < 3; ++uy)
 #pragma unroll
                         for (int ux = 0; ux < 3; ++ux) rfma(sj, a[j][uy * 3 + ux], O[m[j].x + uy * PITCH + ux]);
-                    if (kk[j] < nb) acc[kk[j]] = acc[kk[j]] + sj;
+                    if (kk[j] < nb) {
+                        if (!gl)
+                            acc[kk[j]] = acc[kk[j]] + sj;
+                        else
+                            part_at(kk[j]) = fl ? part_at(kk[j]) + sj : make_float2(0.f, 0.f) + sj;
+                    }
                 }
             }
         } else
@@ -1002,7 +1024,8 @@ __global__ void __launch_bounds__(2 * N) k_xy_inv_reg(const float2* __restrict__
         for (int k = threadIdx.x; k < nb; k += 2 * blockDim.x) {
             const int k2 = k + blockDim.x;
             const bool two = k2 < nb;
-            const int2 m0 = meta[k], m1 = two ? meta[k2] : m0;
+            const int2 m0 = gl ? meta_of(k) : meta[k];
+            const int2 m1 = two ? (gl ? meta_of(k2) : meta[k2]) : m0;
             const float* w0 = w + (int64_t)fl * U * Ntot + m0.y;
             const float* w1 = w + (int64_t)fl * U * Ntot + m1.y;
             {
@@ -1012,16 +1035,23 @@ __global__ void __launch_bounds__(2 * N) k_xy_inv_reg(const float2* __restrict__
                         rfma(s0, __ldg(w0 + (int64_t)(uy * P + ux) * Ntot), O[m0.x + uy * PITCH + ux]);
                         rfma(s1, __ldg(w1 + (int64_t)(uy * P + ux) * Ntot), O[m1.x + uy * PITCH + ux]);
                     }
-                acc[k] = acc[k] + s0;
-                if (two) acc[k2] = acc[k2] + s1;
+                if (!gl) {
+                    acc[k] = acc[k] + s0;
+                    if (two) acc[k2] = acc[k2] + s1;
+                } else {
+                    part_at(k) = fl ? part_at(k) + s0 : make_float2(0.f, 0.f) + s0;
+                    if (two) part_at(k2) = fl ? part_at(k2) + s1 : make_float2(0.f, 0.f) + s1;
+                }
             }
         }
         __syncthreads();
     }
-    for (int k = threadIdx.x; k < nb; k += blockDim.x) {
-        const int i = lo + k;
-        const int slot = z - anc[3 * i + 2];
-        part[(((int64_t)b * G + grp) * P + slot) * Ntot + i] = acc[k];
+    if (!gl) {
+        for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+            const int i = lo + k;
+            const int slot = z - anc[3 * i + 2];
+            part[(((int64_t)b * G + grp) * P + slot) * Ntot + i] = acc[k];
+        }
     }
 }
 
@@ -1033,9 +1063,7 @@ static bool reg_shape(const aimx_ctx* ctx) {
     if (N != 8 && N != 16 && N != 32 && N != 64) return false;
     const int Nz = ctx->n[2];
     if (Nz != 8 && Nz != 16 && Nz != 32 && Nz != 64) return false;
-    int mpb = 0;
-    for (size_t z = 0; z < ctx->plane_lo.size(); ++z) mpb = std::max(mpb, ctx->plane_hi[z] - ctx->plane_lo[z]);
-    return (size_t)(2 * N * (N + 1) + 2 * mpb) * sizeof(float2) <= 200 * 1024;
+    return true;   // planes with more bases than shared memory holds sum in the output array
 }
 
 bool fused_reg_supported(const aimx_ctx* ctx) { return fused_supported(ctx) && reg_shape(ctx); }
@@ -1069,19 +1097,25 @@ static void launch_xy_fwd_reg(const aimx_ctx* ctx, const float2* G, float2* S, i
 template <int N>
 static void launch_xy_inv_reg(const aimx_ctx* ctx, const float2* S, const int* plo, const int* phi, float2* part,
                               int B, cudaStream_t s) {
-    size_t sm = (2 * (size_t)N * (N + 1) + 2 * (size_t)ctx->max_plane_bases) * sizeof(float2);
+    // bases of a plane kept in shared memory (accumulator + metadata, 16 bytes each) up to 200 KB
+    const int cap_fit = (int)std::min<size_t>(ctx->max_plane_bases,
+                                          (200 * 1024 - 2 * (size_t)N * (N + 1) * sizeof(float2)) / 16);
+    const int cap = ctx->plane_cap > 0 ? std::min(cap_fit, ctx->plane_cap) : cap_fit;
+    size_t sm = (2 * (size_t)N * (N + 1) + 2 * (size_t)cap) * sizeof(float2);
     const dim3 grid(ctx->n[2], ctx->F / 4, B);
-    if (ctx->charge) {
-        set_smem(k_xy_inv_reg<N, true>, sm);
-        k_xy_inv_reg<N, true><<<grid, 2 * N, sm, s>>>(S, ctx->d_wsoa, ctx->d_anc, plo, phi, part, ctx->F, ctx->n[2],
-                                                       ctx->N, ctx->P, ctx->d_tanc, ctx->d_tplane, ctx->d_lp_soa,
-                                                       reinterpret_cast<float2*>(ctx->d_tpart), ctx->nt);
-    } else {
-        set_smem(k_xy_inv_reg<N, false>, sm);
-        k_xy_inv_reg<N, false><<<grid, 2 * N, sm, s>>>(S, ctx->d_wsoa, ctx->d_anc, plo, phi, part, ctx->F,
-                                                        ctx->n[2], ctx->N, ctx->P, nullptr, nullptr, nullptr, nullptr,
-                                                        ctx->nt);
-    }
+    auto go = [&](auto kern, bool chg) {
+        set_smem(kern, sm);
+        kern<<<grid, 2 * N, sm, s>>>(S, ctx->d_wsoa, ctx->d_anc, plo, phi, part, ctx->F, ctx->n[2], ctx->N, ctx->P,
+                                     chg ? ctx->d_tanc : nullptr, chg ? ctx->d_tplane : nullptr,
+                                     chg ? ctx->d_lp_soa : nullptr,
+                                     chg ? reinterpret_cast<float2*>(ctx->d_tpart) : nullptr, ctx->nt, cap);
+    };
+    // the common case (every plane's bases in shared memory) keeps the kernel without the other form
+    const bool big = ctx->max_plane_bases > cap;
+    if (ctx->charge)
+        big ? go(k_xy_inv_reg<N, true, true>, true) : go(k_xy_inv_reg<N, true, false>, true);
+    else
+        big ? go(k_xy_inv_reg<N, false, true>, false) : go(k_xy_inv_reg<N, false, false>, false);
 }
 
 template <int NZ, int F>
@@ -1459,6 +1493,12 @@ void matvec_fused_into(aimx_ctx* ctx, double freq, int B, const float* x, float*
 }
 
 }  // namespace aimx
+
+extern "C" int aimx_set_plane_cap(aimx_ctx* ctx, int cap) {
+    if (!ctx) return AIMX_E_ARG;
+    ctx->plane_cap = cap > 0 ? cap : 0;
+    return AIMX_OK;
+}
 
 extern "C" int aimx_set_wait_limit(int64_t cycles) {
     const long long v = cycles > 0 ? (long long)cycles : aimx::kWaitLimit;

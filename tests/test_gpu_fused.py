@@ -94,6 +94,40 @@ def test_fused_deterministic(torch_cuda):
     assert np.array_equal(a.view(np.float32), b.view(np.float32))
 
 
+@pytest.mark.parametrize("form,order", [("pmchwt", 2), ("efie", 1), ("efie", 3)])
+def test_fused_planes_beyond_shared_memory(torch_cuda, form, order):
+    """A grid plane with more bases than the inverse-xy kernel keeps in shared memory sums its
+    interpolation partials in the output array (forced here with a cap of 8 bases per plane):
+    bitwise the product of the shared-memory form, and the oracle's within the FP32 tolerance.
+    Orders 1 and 3 take the two-bases-per-iteration loop, order 2 the four-bases one."""
+    torch = torch_cuda
+    from synth import icosphere, random_complex
+    from oracle import operator as op
+    from paper_2009_02281_gb300 import Context, EFIE, PMCHWT, F32
+    xyz, tri = icosphere(2)
+    grid = (16, 16, 16)
+    fm = EFIE if form == "efie" else PMCHWT
+    ctx = Context(xyz, tri, grid, order=order, formulation=fm, eps_out=1.0, eps_in=4.0)
+    assert ctx.matvec_path(F32) == 0
+    f = 1.2 * C0 / (2 * np.pi)
+    x = random_complex((3, ctx.nunk), seed=77)
+    xt = torch.tensor(x, dtype=torch.complex64, device="cuda")
+    a = ctx.matvec(f, xt).cpu().numpy()
+    ctx.set_plane_cap(8)
+    b = ctx.matvec(f, xt).cpu().numpy()
+    ctx.set_plane_cap(0)
+    c = ctx.matvec(f, xt).cpu().numpy()
+    ctx.close()
+    assert np.array_equal(a.view(np.float32), b.view(np.float32))
+    assert np.array_equal(a.view(np.float32), c.view(np.float32))
+    prob = op.setup(xyz, tri, order, grid, radius=3)
+    if form == "efie":
+        ref = np.stack([op.matvec_efie(prob, f, xi) for xi in x])
+    else:
+        ref = np.stack([op.matvec_pmchwt(prob, f, xi, 1.0, 4.0) for xi in x])
+    assert _relerr(b, ref) <= TOL32
+
+
 @pytest.fixture(scope="module")
 def full_workload(torch_cuda):
     """The benchmark workload: 61440 unknowns, 64^3 grid padded to 128^3, 64 RHS."""
