@@ -479,7 +479,7 @@ constexpr int kNbRows = 32;        // rows per block at most
 constexpr int kNbWarps = 16;
 constexpr int kNbUmax = 448;       // target column union per block
 
-template <int F>
+template <int F, bool SPLIT>
 __global__ void __launch_bounds__(kNbWarps * 32) k_near_blk(
     const float2* __restrict__ part, const float2* __restrict__ xT, const int* __restrict__ nb_rows,
     const int* __restrict__ nb_ustart, const int* __restrict__ nb_ucols, const float4* __restrict__ ent,
@@ -497,6 +497,14 @@ __global__ void __launch_bounds__(kNbWarps * 32) k_near_blk(
     const int u0 = nb_ustart[blockIdx.x], nu = nb_ustart[blockIdx.x + 1] - u0;
     for (int bc = 0; bc < B; bc += 32) {
         const int nbc = min(32, B - bc);
+        // SPLIT (at most 16 RHS, instantiated separately so the wide form is unchanged): RB >= nbc
+        // RHS lanes, and 32 / RB lane groups each take every (32 / RB)-th entry of a row, so the
+        // warp applies several entries at once when the RHS fill only part of it
+        int RB = 32;
+        if (SPLIT)
+            for (RB = 1; RB < nbc; RB <<= 1) {
+            }
+        const int ngrp = 32 / RB, gsub = lane / RB, rl = lane % RB;
         // interpolation partials summed over the stencil slots, rows fastest (coalesced)
         for (int idx = threadIdx.x; idx < G * 32 * kNbRows; idx += blockDim.x) {
             const int r = idx % kNbRows, rest = idx / kNbRows;
@@ -538,13 +546,22 @@ __global__ void __launch_bounds__(kNbWarps * 32) k_near_blk(
                     if (e0 + 32 + lane < e1) nxt = __ldg(ent + e0 + 32 + lane);
                     const int cnt = min(32, e1 - e0);
 #pragma unroll 4
-                    for (int m = 0; m < cnt; ++m) {
+                    for (int m = gsub; m < cnt; m += ngrp) {
                         const float4 t = ebuf[warp][m];
-                        const float2 xv = xs[__float_as_int(t.x) * 32 + lane];
+                        const float2 xv = xs[__float_as_int(t.x) * 32 + rl];
                         rfma(a, t.y, xv);
                         rfma(p, t.z, xv);
                         rfma(q, t.w, xv);
                     }
+                }
+                // combine the entry groups (butterfly: every lane of a RHS ends with the same sum)
+                for (int off = RB; off < 32; off <<= 1) {
+                    a.x += __shfl_xor_sync(0xffffffffu, a.x, off);
+                    a.y += __shfl_xor_sync(0xffffffffu, a.y, off);
+                    p.x += __shfl_xor_sync(0xffffffffu, p.x, off);
+                    p.y += __shfl_xor_sync(0xffffffffu, p.y, off);
+                    q.x += __shfl_xor_sync(0xffffffffu, q.x, off);
+                    q.y += __shfl_xor_sync(0xffffffffu, q.y, off);
                 }
                 acc[k][3 * ph] = a;
                 acc[k][3 * ph + 1] = p;
@@ -1285,19 +1302,19 @@ static void run_fused(aimx_ctx* ctx, const NearC& nc, int B, const float2* xb, f
         const size_t smem = (size_t)ctx->nb_umax * 32 * sizeof(float2);
         const int* lp_ = ctx->linterm ? ctx->d_lin_ptr : nullptr;
         const int has_k = F == 8 ? 1 : (ctx->f32.ng != nullptr);
-        if (F == 8) {
-            set_smem(k_near_blk<8>, smem);
-            k_near_blk<8><<<ctx->nb_count, kNbWarps * 32, smem, s>>>(
+        auto go = [&](auto kern) {
+            set_smem(kern, smem);
+            kern<<<ctx->nb_count, kNbWarps * 32, smem, s>>>(
                 fb.part, fb.xT, ctx->d_nb_rows, ctx->d_nb_ustart, ctx->d_nb_ucols, ctx->d_nb_ent, ctx->d_row_ptr,
                 ctx->d_perm, lp_, ctx->d_lin_cols, ctx->f32.la, ctx->f32.lp, yb, nc, has_k, N, nunk, P, B, phiT,
                 ctx->d_btri_t, ctx->d_blen);
-        } else {
-            set_smem(k_near_blk<4>, smem);
-            k_near_blk<4><<<ctx->nb_count, kNbWarps * 32, smem, s>>>(
-                fb.part, fb.xT, ctx->d_nb_rows, ctx->d_nb_ustart, ctx->d_nb_ucols, ctx->d_nb_ent, ctx->d_row_ptr,
-                ctx->d_perm, lp_, ctx->d_lin_cols, ctx->f32.la, ctx->f32.lp, yb, nc, has_k, N, nunk, P, B, phiT,
-                ctx->d_btri_t, ctx->d_blen);
-        }
+        };
+        // up to 16 RHS: each warp applies several entries at once
+        const bool split = B <= 16;
+        if (F == 8)
+            split ? go(k_near_blk<8, true>) : go(k_near_blk<8, false>);
+        else
+            split ? go(k_near_blk<4, true>) : go(k_near_blk<4, false>);
     } else
     k_final<<<(N + kFinalRows - 1) / kFinalRows, kThreads, 0, s>>>(fb.part, fb.xT, ctx->d_row_ptr, ctx->d_cols,
                                                                    ctx->f32.na, ctx->f32.np,
