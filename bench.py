@@ -716,7 +716,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         ms64 = e0.elapsed_time(e1) / reps
         fp64 = {"value": round(ws * nb64 / (ms64 * 1e-3), 2), "unit": UNIT, "rhs_per_call": nb64,
-                "ms_per_call": round(ms64, 3), "path": "generic radix-2 FP64 (kernel spectra FP64)"}
+                "ms_per_call": round(ms64, 3), "path": "generic FP64, shared-memory line FFTs on the 128^3 pad (kernel spectra FP64)"}
         del x64, y64
 
     # the plain comparison path on the same GPU: generic projection / interpolation with cuFFT
