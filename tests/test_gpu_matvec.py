@@ -227,3 +227,34 @@ def test_mixed_radix_pads(torch_cuda, form):
         ctx.close()
         assert np.linalg.norm(y64 - ref) / np.linalg.norm(ref) <= 1e-9, pad
         assert np.linalg.norm(y32 - ref) / np.linalg.norm(ref) <= 1e-5, pad
+
+
+@pytest.mark.parametrize("grid,pad,nrhs", [((12, 12, 12), (24, 24, 24), 16), ((12, 12, 12), (32, 32, 32), 8),
+                                           ((12, 12, 12), (48, 48, 48), 4), ((8, 8, 8), (16, 16, 16), 32),
+                                           ((12, 12, 12), (64, 64, 64), 2)])
+def test_register_line_ffts(torch_cuda, grid, pad, nrhs):
+    """The generic path's register-line FFTs (one line per thread): FP32 lines of 16 to 64 points
+    always, FP64 lines of 16 to 48 points when a transform has at least 32768 z lines, which the
+    right-hand-side counts here reach (64 points: FP32 only).  The batched FP64 product must equal
+    the same product taken one RHS at a time (shared-memory line FFTs) to rounding, and both
+    precisions must match the oracle on the first and last RHS."""
+    torch = torch_cuda
+    from synth import icosphere, random_complex
+    from oracle import operator as op
+    from paper_2009_02281_gb300 import Context, EFIE
+    xyz, tri = icosphere(2)
+    ctx = Context(xyz, tri, grid, order=2, formulation=EFIE, pad=pad)
+    ctx.set_path(1)
+    f = 1.1 * C0 / (2 * np.pi)
+    x = random_complex((nrhs, ctx.nunk), seed=93)
+    x64 = torch.tensor(x, dtype=torch.complex128, device="cuda")
+    y64 = ctx.matvec(f, x64).cpu().numpy()
+    one = np.stack([ctx.matvec(f, x64[b:b + 1]).cpu().numpy()[0] for b in range(nrhs)])
+    y32 = ctx.matvec(f, torch.tensor(x, dtype=torch.complex64, device="cuda")).cpu().numpy()
+    ctx.close()
+    assert np.linalg.norm(y64 - one) / np.linalg.norm(one) <= 1e-12
+    prob = op.setup(xyz, tri, 2, grid, radius=3)
+    for b in (0, nrhs - 1):
+        ref = op.matvec_efie(prob, f, x[b])
+        assert np.linalg.norm(y64[b] - ref) / np.linalg.norm(ref) <= 1e-9
+        assert np.linalg.norm(y32[b] - ref) / np.linalg.norm(ref) <= 1e-5
