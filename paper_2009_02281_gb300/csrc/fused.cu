@@ -99,35 +99,46 @@ __global__ void __launch_bounds__(256) k_gather_tile(const float4* __restrict__ 
     const int b0 = blockIdx.y * 32;
     const int b = b0 + lane;
     const bool bok = b < B;
+    const int bc = bok ? b : B - 1;   // lanes past the last RHS compute a copy and store nothing
     for (int gl = warp; gl < TG; gl += 8) {
         const int64_t g = g0 + gl;
         float2 acc[F];
 #pragma unroll
         for (int f = 0; f < F; ++f) acc[f] = make_float2(0.f, 0.f);
-        if (g < NG && bok) {
+        if (g < NG) {   // warp-uniform
             const int e1 = node_ptr[g + 1];
-            for (int e = node_ptr[g]; e < e1; ++e) {
-                const int wi = node_w[e];
-                const float4 wv = __ldg(w + wi);
-                const int i = wi / U;
-                const float2 xj = __ldg(xT + (int64_t)i * B + b);
-                rfma(acc[0], wv.x, xj);
-                rfma(acc[1], wv.y, xj);
-                rfma(acc[2], wv.z, xj);
-                if (F == 8 || !tnode_ptr) rfma(acc[3], wv.w, xj);
-                if (F == 8) {
-                    const float2 xm = __ldg(xT + (int64_t)(N + i) * B + b);
-                    rfma(acc[4], wv.x, xm);
-                    rfma(acc[5], wv.y, xm);
-                    rfma(acc[6], wv.z, xm);
-                    rfma(acc[7], wv.w, xm);
+            // the node's entries 32 at a time: each lane loads one entry index and its weights
+            // (coalesced), then the warp walks them with shuffles, so the x gathers of several
+            // entries are in flight together instead of waiting on an index-then-weight chain
+            for (int e0 = node_ptr[g]; e0 < e1; e0 += 32) {
+                const int cnt = min(32, e1 - e0);
+                const int lwi = lane < cnt ? node_w[e0 + lane] : 0;
+                const float4 lw = lane < cnt ? __ldg(w + lwi) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 4
+                for (int m = 0; m < cnt; ++m) {
+                    const int wi = __shfl_sync(0xffffffffu, lwi, m);
+                    const float4 wv = make_float4(__shfl_sync(0xffffffffu, lw.x, m), __shfl_sync(0xffffffffu, lw.y, m),
+                                                  __shfl_sync(0xffffffffu, lw.z, m), __shfl_sync(0xffffffffu, lw.w, m));
+                    const int i = wi / U;
+                    const float2 xj = __ldg(xT + (int64_t)i * B + bc);
+                    rfma(acc[0], wv.x, xj);
+                    rfma(acc[1], wv.y, xj);
+                    rfma(acc[2], wv.z, xj);
+                    if (F == 8 || !tnode_ptr) rfma(acc[3], wv.w, xj);
+                    if (F == 8) {
+                        const float2 xm = __ldg(xT + (int64_t)(N + i) * B + bc);
+                        rfma(acc[4], wv.x, xm);
+                        rfma(acc[5], wv.y, xm);
+                        rfma(acc[6], wv.z, xm);
+                        rfma(acc[7], wv.w, xm);
+                    }
                 }
             }
             if (F == 4 && tnode_ptr) {
                 const int t1 = tnode_ptr[g + 1];
                 for (int e = tnode_ptr[g]; e < t1; ++e) {
                     const int wt = tnode_w[e];
-                    rfma(acc[3], __ldg(lp + wt), __ldg(qT + (int64_t)(wt / U) * B + b));
+                    rfma(acc[3], __ldg(lp + wt), __ldg(qT + (int64_t)(wt / U) * B + bc));
                 }
             }
         }
