@@ -695,7 +695,9 @@ __device__ __forceinline__ void zpass_tile(float2 (&v)[NZ], float2* sm, float2* 
     __syncthreads();
     // mix at (column, kz)
     const int Ox = Mx / 2 + 1, Oy = My / 2 + 1, Oz = MZ / 2 + 1;
-    const int64_t OT = (int64_t)Ox * Oy * Oz;
+    // spectra hold at most 8 arrays of 65^3 points and a column spans at most 64 planes of
+    // 4 x 64 x 64 points: 32-bit offsets (fewer index instructions than 64-bit ones)
+    const int OT = Ox * Oy * Oz;
     const int ky = 2 * kyp + py;
     const int oy = ky <= My / 2 ? ky : My - ky;
     // compile-time trip count (blockDim.x = 2 F TC divides TC MZ): the loop unrolls and every
@@ -709,7 +711,7 @@ __device__ __forceinline__ void zpass_tile(float2 (&v)[NZ], float2* sm, float2* 
         const int kx = 2 * (kx0 + cc) + px;
         const int ox = kx <= Mx / 2 ? kx : Mx - kx;
         const int oz = kz <= MZ / 2 ? kz : MZ - kz;
-        const int64_t oi = ((int64_t)oz * Oy + oy) * Ox + ox;
+        const int oi = (oz * Oy + oy) * Ox + ox;
         float2* g = sm + cc * LP + kz;
         constexpr int fs = FS;
         if (F == 4) {
@@ -752,8 +754,10 @@ __device__ __forceinline__ void zpass_tile(float2 (&v)[NZ], float2* sm, float2* 
     }
     __syncthreads();
     if (!pz) {
+        float2* col = S + base;
+        const int zs32 = (int)zs;
 #pragma unroll
-        for (int z = 0; z < NZ; ++z) S[base + z * zs] = v[z] + line[z];
+        for (int z = 0; z < NZ; ++z) col[z * zs32] = v[z] + line[z];
     }
 }
 
@@ -771,8 +775,10 @@ __global__ void __launch_bounds__(2 * F * 8) k_zpass_reg(float2* S, const float2
     const int64_t zs = 4 * (int64_t)NP;
     const int64_t base = (((int64_t)b * F + f) * NZ * 4 + q) * NP + (int64_t)kyp * Nx + kx0 + c;
     float2 v[NZ];
+    const float2* col = S + base;
+    const int zs32 = (int)zs;   // (NZ - 1) zs <= 63 * 4 * 64 * 64 < 2^31
 #pragma unroll
-    for (int z = 0; z < NZ; ++z) v[z] = S[base + z * zs];
+    for (int z = 0; z < NZ; ++z) v[z] = col[z * zs32];
     zpass_tile<NZ, F>(v, sm, S, spec, Nx, Ny, kx0, kyp, q, c, f, pz, base, zs);
 }
 
