@@ -1,7 +1,7 @@
 """Charge-form scalar potential of the EFIE with AIMx acceleration, by direct grid summation.
 
 Test infrastructure: only tests, the smoke check and the benchmark's CPU baseline may import
-this module.  It is the oracle of a formulation row that has no GPU path yet.
+this module.
 
 The EFIE's scalar-potential operator L^Phi_mn = int int div f_m div' f_n G is written through
 the charges the currents carry.  With the charge on triangle t as a pulse of density q_t / A_t,
@@ -27,6 +27,7 @@ import numpy as np
 
 from . import greens
 from . import grid as gridmod
+from .constants import ETA0
 from .operator import materials, near_dense, near_apply, conv_full, conv_nodes, _grid_matrices, _grid_parts
 from .potentials import tri_potentials
 from .quadrature import triangle_rule, map_points, projection_order
@@ -156,24 +157,13 @@ def dense_efie_charge(prob, ch, freq, eps_bg=1.0):
     return 1j * w * mu * (LA - lphi_charge_dense(prob, ch, k) / k ** 2)
 
 
-def matvec_efie_charge(prob, ch, freq, x, eps_bg=1.0, rows=None):
-    """y = j w mu [ (N^A + P_v^T H P_v) x - k^-2 D^T ((Pt_s,NR - Pt_s,P) + Lp^T H Lp) D x ]
-    by direct grid summation: the charge-form AIMx EFIE product (the RWG form is
-    ``operator.matvec_efie``).  With ``rows``, only those output rows: the scalar potential is
-    then evaluated on the two triangles of each row only (their stencil nodes, their near rows)."""
-    w, regs = materials(freq, eps_bg)
-    mu, eps, k = regs[0]
+def charge_lphi_apply(prob, ch, k, x, rows=None):
+    """D^T ((Pt_s,NR - Pt_s,P) + Lp^T H(k) Lp) D x by direct grid summation; with ``rows``, only
+    those output rows (the potential is then evaluated on their two triangles only: their stencil
+    nodes and their near rows)."""
     g = prob["grid"]
     Nx, Ny, Nz = g["n"]
     H = greens.kernel_table(k, g["n"], g["h"])
-    # vector potential exactly as in the RWG form
-    if rows is None:
-        f = gridmod.project(prob["lam"], prob["anc"], g, x, fields=(0, 1, 2))
-        GA = gridmod.interpolate(prob["lam"], prob["anc"], g, conv_full(H, f), fields=(0, 1, 2))
-    else:
-        GA = _grid_parts(prob, k, [x], rows, False)[0][0]
-    NA = near_apply(prob, "NA", x, rows)
-    # scalar potential from the triangle charges q = D x
     D = ch["D"]
     q = D @ x
     off = gridmod.stencil_offsets(g["order"])
@@ -194,6 +184,65 @@ def matvec_efie_charge(prob, ch, freq, x, eps_bg=1.0, rows=None):
     sel = np.isin(ch["rows"], tris)
     np.add.at(phi, ch["rows"][sel], ch["NPt"][sel] * q[ch["cols"][sel]])
     LPx = D.T @ phi
-    if rows is not None:
-        LPx = LPx[np.asarray(rows)]
+    return LPx if rows is None else LPx[np.asarray(rows)]
+
+
+def matvec_efie_charge(prob, ch, freq, x, eps_bg=1.0, rows=None):
+    """y = j w mu [ (N^A + P_v^T H P_v) x - k^-2 D^T ((Pt_s,NR - Pt_s,P) + Lp^T H Lp) D x ]
+    by direct grid summation: the charge-form AIMx EFIE product (the RWG form is
+    ``operator.matvec_efie``).  With ``rows``, only those output rows."""
+    w, regs = materials(freq, eps_bg)
+    mu, eps, k = regs[0]
+    g = prob["grid"]
+    H = greens.kernel_table(k, g["n"], g["h"])
+    # vector potential exactly as in the RWG form
+    if rows is None:
+        f = gridmod.project(prob["lam"], prob["anc"], g, x, fields=(0, 1, 2))
+        GA = gridmod.interpolate(prob["lam"], prob["anc"], g, conv_full(H, f), fields=(0, 1, 2))
+    else:
+        GA = _grid_parts(prob, k, [x], rows, False)[0][0]
+    NA = near_apply(prob, "NA", x, rows)
+    # scalar potential from the triangle charges q = D x
+    LPx = charge_lphi_apply(prob, ch, k, x, rows)
     return 1j * w * mu * ((NA + GA) - LPx / k ** 2)
+
+
+def dense_pmchwt_charge(prob, ch, freq, eps_out, eps_in, mu_in=1.0):
+    """The two-region PMCHWT AIMx matrix (``operator.dense_pmchwt``) with each region's scalar
+    potential in charge form, L_r = (N^A + P_v^T H_r P_v) - k_r^-2 D^T Pt(k_r) D, in the J block
+    (electric rows) and the M block (magnetic rows) alike; x = [J ; M/eta0]."""
+    w, regs = materials(freq, eps_out, eps_in, mu_in)
+    NA, NK = near_dense(prob, "NA"), near_dense(prob, "NK")
+    N = prob["N"]
+    Z = np.zeros((2 * N, 2 * N), dtype=np.complex128)
+    for mu, eps, k in regs:
+        GA, _, GK = _grid_matrices(prob, k, True)
+        L = (NA + GA) - lphi_charge_dense(prob, ch, k) / k ** 2
+        K = NK + GK
+        Z[:N, :N] += 1j * w * mu * L
+        Z[:N, N:] += ETA0 * K
+        Z[N:, :N] -= ETA0 * K
+        Z[N:, N:] += ETA0 ** 2 * 1j * w * eps * L
+    return Z
+
+
+def matvec_pmchwt_charge(prob, ch, freq, x, eps_out, eps_in, mu_in=1.0, rows=None):
+    """The two-region PMCHWT AIMx product (``operator.matvec_pmchwt``) with both regions' scalar
+    potentials in charge form, by direct grid summation; x = [J ; M/eta0], y = [E rows ;
+    eta0 H rows].  With ``rows`` (indices into 0..N-1), those rows of both blocks."""
+    N = prob["N"]
+    xJ, xM = x[:N], x[N:]
+    w, regs = materials(freq, eps_out, eps_in, mu_in)
+    nJ = {c: near_apply(prob, c, xJ, rows) for c in ("NA", "NK")}
+    nM = {c: near_apply(prob, c, xM, rows) for c in ("NA", "NK")}
+    yE = 0.0
+    yH = 0.0
+    for mu, eps, k in regs:
+        (GAJ, _, GKJ), (GAM, _, GKM) = _grid_parts(prob, k, [xJ, xM], rows, True)
+        LJ = (nJ["NA"] + GAJ) - charge_lphi_apply(prob, ch, k, xJ, rows) / k ** 2
+        LM = (nM["NA"] + GAM) - charge_lphi_apply(prob, ch, k, xM, rows) / k ** 2
+        KJ = nJ["NK"] + GKJ
+        KM = nM["NK"] + GKM
+        yE = yE + 1j * w * mu * LJ + ETA0 * KM
+        yH = yH - ETA0 * KJ + ETA0 ** 2 * 1j * w * eps * LM
+    return np.concatenate([yE, yH])

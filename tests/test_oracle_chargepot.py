@@ -1,4 +1,4 @@
-"""Pins for the charge-form scalar potential (oracle only; no GPU path yet).
+"""Pins for the charge-form scalar potential of the oracle (EFIE and two-region PMCHWT).
 
 References other than the module itself: the Euler count of the loop space, the exact identity
 L^Phi_s = D^T Pt_s D against the RWG static integrals, moments of the pulse weights against a
@@ -139,3 +139,37 @@ def test_sampled_rows_equal_full_product(small_sphere, ch1):
     y = cp.matvec_efie_charge(prob, ch1, f, x)
     ys = cp.matvec_efie_charge(prob, ch1, f, x, rows=rows)
     assert np.linalg.norm(ys - y[rows]) <= 1e-12 * np.linalg.norm(y[rows])
+
+
+def test_pmchwt_charge_against_its_parts(small_sphere, ch1):
+    """The two-region charge form assembled from pinned pieces: with M = 0 its electric rows are
+    the sum over the regions of the charge-form EFIE products in each region's material, and its
+    magnetic rows the RWG-form PMCHWT's (the K terms carry no scalar potential); with J = 0 its
+    magnetic rows are sum_r eps_r x (charge-form EFIE of region r) (eta0^2 eps / mu = eps_r for
+    mu = mu0) and its electric rows the RWG form's.  The dense matrix equals the product, and
+    sampled rows equal the full product."""
+    prob = small_sphere
+    N = prob["N"]
+    f = 0.6 * C0 / (2 * np.pi)
+    eo, ei = 1.0, 4.0
+    rng = np.random.default_rng(12)
+    xJ = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    xM = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    z = np.zeros(N, dtype=np.complex128)
+    yJ = cp.matvec_pmchwt_charge(prob, ch1, f, np.r_[xJ, z], eo, ei)
+    yM = cp.matvec_pmchwt_charge(prob, ch1, f, np.r_[z, xM], eo, ei)
+    eJ = sum(cp.matvec_efie_charge(prob, ch1, f, xJ, eps_bg=e) for e in (eo, ei))
+    eM = sum(e * cp.matvec_efie_charge(prob, ch1, f, xM, eps_bg=e) for e in (eo, ei))
+    rJ = op.matvec_pmchwt(prob, f, np.r_[xJ, z], eo, ei)
+    rM = op.matvec_pmchwt(prob, f, np.r_[z, xM], eo, ei)
+    assert np.linalg.norm(yJ[:N] - eJ) <= 1e-12 * np.linalg.norm(eJ)
+    assert np.linalg.norm(yJ[N:] - rJ[N:]) <= 1e-12 * np.linalg.norm(rJ[N:])
+    assert np.linalg.norm(yM[N:] - eM) <= 1e-12 * np.linalg.norm(eM)
+    assert np.linalg.norm(yM[:N] - rM[:N]) <= 1e-12 * np.linalg.norm(rM[:N])
+    x = np.r_[xJ, xM]
+    y = cp.matvec_pmchwt_charge(prob, ch1, f, x, eo, ei)
+    Z = cp.dense_pmchwt_charge(prob, ch1, f, eo, ei)
+    assert np.linalg.norm(Z @ x - y) <= 1e-11 * np.linalg.norm(y)
+    rows = np.array([0, 5, N // 2, N - 1])
+    ys = cp.matvec_pmchwt_charge(prob, ch1, f, x, eo, ei, rows=rows)
+    assert np.linalg.norm(ys - np.r_[y[rows], y[N + rows]]) <= 1e-12 * np.linalg.norm(ys)
