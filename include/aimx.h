@@ -361,9 +361,10 @@ int aimx_set_conventional_aim(aimx_ctx* ctx, int enable);
 
 /* ------------------------------------------------------------------ charge-form scalar potential
  * The discretisation of the augmented EFIE that the paper uses for its on-chip
- * examples (Sec. V-C to V-E), kept on the EFIE's RWG unknowns.  With enable = 1
- * the scalar-potential operator of this EFIE context is written through the
- * triangle charges q = D x (D_tn = +l_n on T+, -l_n on T-):
+ * examples (Sec. V-C to V-E), kept on the RWG unknowns.  With enable = 1 the
+ * scalar-potential operator of this EFIE context (or, for AIMX_PMCHWT, of each
+ * region in both the J and the M blocks) is written through the triangle
+ * charges q = D x (D_tn = +l_n on T+, -l_n on T-):
  *     L^Phi = D^T Pt D,   Pt = (Pt_s,NR - Pt_s,P) + Lp^T H(k) Lp,
  * Pt_ij = (A_i A_j)^-1 int_{T_i} int_{T_j} G the pulse-pulse potential, Lp the
  * pulse projection weights (moment matching of a unit charge on each
@@ -379,7 +380,11 @@ int aimx_set_conventional_aim(aimx_ctx* ctx, int enable);
  *   - Applies to aimx_matvec (both precisions, generic and plane-fused paths),
  *     aimx_solve, aimx_sweep, ports and batches.  Preconditioners keep the RWG
  *     static self terms.  aimx_matvec_noalloc returns AIMX_E_STATE while on.
- *   - AIMX_E_STATE for non-EFIE contexts, or with the linear term or the
+ *   - AIMX_PMCHWT: each region r contributes -k_r^-2 D^T Pt(k_r) D, with the
+ *     region's coefficient, to the J block (E rows) and the M block (H rows);
+ *     aimx_sweep_batched then returns AIMX_E_STATE (no multi-frequency
+ *     two-region charge product).
+ *   - AIMX_E_STATE for CFIE contexts, or with the linear term or the
  *     conventional-AIM mode on; AIMX_E_GRID if a triangle stencil leaves the
  *     grid.  enable = 0 returns to the RWG form.
  * Off by default. */

@@ -399,7 +399,7 @@ void charge_potential(aimx_ctx* ctx, const typename Cplx<T>::type* grid, int Fg,
                       const double2* cps = nullptr, const int* fidx = nullptr);
 // plane-fused path: qT = D x from xT ([nt][B]); phiT = sum of plane partials + cP N_Pt qT
 void charge_fused_q(aimx_ctx* ctx, const float2* xT, int B, cudaStream_t s);
-void charge_fused_phi(aimx_ctx* ctx, int B, float2 cP, cudaStream_t s);
+void charge_fused_phi(aimx_ctx* ctx, int B, float2 cP, float2 cP2, cudaStream_t s);
 void ensure_charge_buffers(aimx_ctx* ctx, int B);
 void matvec_fused(aimx_ctx* ctx, double freq, int nrhs, const float* x, float* y, cudaStream_t s);
 

@@ -243,8 +243,8 @@ int aimx_set_conventional_aim(aimx_ctx* ctx, int enable) {
 
 int aimx_set_charge_form(aimx_ctx* ctx, int enable) {
     if (!ctx || enable < 0 || enable > 1) return AIMX_E_ARG;
-    if (enable && ctx->form != AIMX_EFIE)
-        return fail(ctx, Error{AIMX_E_STATE, "the charge form is available for the EFIE"});
+    if (enable && ctx->form != AIMX_EFIE && ctx->form != AIMX_PMCHWT)
+        return fail(ctx, Error{AIMX_E_STATE, "the charge form is available for the EFIE and the PMCHWT"});
     if (enable && (ctx->linterm || ctx->aim))
         return fail(ctx, Error{AIMX_E_STATE,
                                "the charge form is not combined with the linear term or the conventional-AIM mode"});

@@ -127,7 +127,8 @@ static T* upload_vec(aimx_ctx* ctx, const std::vector<T>& v) {
 
 void build_charge(aimx_ctx* ctx) {
     if (ctx->charge_built) return;
-    if (ctx->form != AIMX_EFIE) throw Error{AIMX_E_STATE, "the charge form is available for the EFIE"};
+    if (ctx->form != AIMX_EFIE && ctx->form != AIMX_PMCHWT)
+        throw Error{AIMX_E_STATE, "the charge form is available for the EFIE and the PMCHWT"};
     const int nt = ctx->nt, N = ctx->N, P = ctx->P, U = ctx->U, order = ctx->order;
     const int nx = ctx->n[0], ny = ctx->n[1], nz = ctx->n[2];
 
@@ -426,6 +427,8 @@ __global__ void k_phi_fused(const float2* __restrict__ tpart, const int* __restr
     phiT[t] = s + cP * nr;
 }
 
+// Two-region forms (F = 8) keep the M charges, potentials and partials in a second block after
+// those of J: qT and phiT [2][nt][B], tpart [2][B][P][nt].
 void ensure_charge_buffers(aimx_ctx* ctx, int B) {
     if (ctx->charge_cap >= B) return;
     if (ctx->d_qT) dev_free(ctx, ctx->d_qT);
@@ -433,7 +436,7 @@ void ensure_charge_buffers(aimx_ctx* ctx, int B) {
     if (ctx->d_tpart) dev_free(ctx, ctx->d_tpart);
     ctx->d_qT = ctx->d_phiT = ctx->d_tpart = nullptr;
     ctx->charge_cap = 0;
-    const size_t nt = (size_t)ctx->nt;
+    const size_t nt = (size_t)ctx->nt * (ctx->F / 4);
     ctx->d_qT = (float*)dev_alloc(ctx, sizeof(float2) * nt * B);
     ctx->d_phiT = (float*)dev_alloc(ctx, sizeof(float2) * nt * B);
     ctx->d_tpart = (float*)dev_alloc(ctx, sizeof(float2) * nt * B * ctx->P);
@@ -442,16 +445,20 @@ void ensure_charge_buffers(aimx_ctx* ctx, int B) {
 
 void charge_fused_q(aimx_ctx* ctx, const float2* xT, int B, cudaStream_t s) {
     const int64_t tot = (int64_t)ctx->nt * B;
-    k_charge_qT<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(ctx->f32.tl, ctx->d_tinc, xT, ctx->nt, B,
-                                                              reinterpret_cast<float2*>(ctx->d_qT));
+    for (int g = 0; g < ctx->F / 4; ++g)   // J; two-region: M (rows N.. of xT)
+        k_charge_qT<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
+            ctx->f32.tl, ctx->d_tinc, xT + (int64_t)g * ctx->N * B, ctx->nt, B,
+            reinterpret_cast<float2*>(ctx->d_qT) + g * tot);
     AIMX_CUDA_TRY(cudaGetLastError());
 }
 
-void charge_fused_phi(aimx_ctx* ctx, int B, float2 cP, cudaStream_t s) {
+void charge_fused_phi(aimx_ctx* ctx, int B, float2 cP, float2 cP2, cudaStream_t s) {
     const int64_t tot = (int64_t)ctx->nt * B;
-    k_phi_fused<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
-        reinterpret_cast<const float2*>(ctx->d_tpart), ctx->d_trow_ptr, ctx->d_tcols, ctx->f32.npt,
-        reinterpret_cast<const float2*>(ctx->d_qT), cP, ctx->nt, B, ctx->P, reinterpret_cast<float2*>(ctx->d_phiT));
+    for (int g = 0; g < ctx->F / 4; ++g)
+        k_phi_fused<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
+            reinterpret_cast<const float2*>(ctx->d_tpart) + g * tot * ctx->P, ctx->d_trow_ptr, ctx->d_tcols,
+            ctx->f32.npt, reinterpret_cast<const float2*>(ctx->d_qT) + g * tot, g ? cP2 : cP, ctx->nt, B, ctx->P,
+            reinterpret_cast<float2*>(ctx->d_phiT) + g * tot);
     AIMX_CUDA_TRY(cudaGetLastError());
 }
 

@@ -84,14 +84,16 @@ __global__ void k_transpose_x(const float2* __restrict__ x, const int* __restric
 // right-hand sides; lane = right-hand side, so the x reads ([nunk][B] layout)
 // are contiguous and each node's (basis, weight) list is read once per warp as
 // broadcasts; a shared-memory transpose writes the projected grid node-fastest.
-// Charge form (tnode_ptr given, EFIE): the rho field is gathered from the triangle charges qT
-// with the pulse weights instead of from the RWG divergence weights.
+// Charge form (tnode_ptr given): the rho field(s) are gathered from the triangle charges qT
+// ([t][b] of J, then, two-region, of M at qT + qt_m) with the pulse weights instead of from the
+// RWG divergence weights.
 template <int F>
 __global__ void __launch_bounds__(256) k_gather_tile(const float4* __restrict__ w, const int* __restrict__ node_ptr,
                                                      const int* __restrict__ node_w, const float2* __restrict__ xT,
                                                      float2* G, int B, int N, int U, int64_t NG,
                                                      const int* __restrict__ tnode_ptr, const int* __restrict__ tnode_w,
-                                                     const float* __restrict__ lp, const float2* __restrict__ qT) {
+                                                     const float* __restrict__ lp, const float2* __restrict__ qT,
+                                                     int64_t qt_m) {
     constexpr int TG = 16;
     __shared__ float2 tile[F][32][TG + 1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -124,21 +126,25 @@ __global__ void __launch_bounds__(256) k_gather_tile(const float4* __restrict__ 
                     rfma(acc[0], wv.x, xj);
                     rfma(acc[1], wv.y, xj);
                     rfma(acc[2], wv.z, xj);
-                    if (F == 8 || !tnode_ptr) rfma(acc[3], wv.w, xj);
+                    if (!tnode_ptr) rfma(acc[3], wv.w, xj);
                     if (F == 8) {
                         const float2 xm = __ldg(xT + (int64_t)(N + i) * B + bc);
                         rfma(acc[4], wv.x, xm);
                         rfma(acc[5], wv.y, xm);
                         rfma(acc[6], wv.z, xm);
-                        rfma(acc[7], wv.w, xm);
+                        if (!tnode_ptr) rfma(acc[7], wv.w, xm);
                     }
                 }
             }
-            if (F == 4 && tnode_ptr) {
+            if (tnode_ptr) {
+                // triangle charges of J (and, two-region, of M: the second nt x B block of qT)
                 const int t1 = tnode_ptr[g + 1];
                 for (int e = tnode_ptr[g]; e < t1; ++e) {
                     const int wt = tnode_w[e];
-                    rfma(acc[3], __ldg(lp + wt), __ldg(qT + (int64_t)(wt / U) * B + bc));
+                    const float l = __ldg(lp + wt);
+                    const int64_t qi = (int64_t)(wt / U) * B + bc;
+                    rfma(acc[3], l, __ldg(qT + qi));
+                    if (F == 8) rfma(acc[7], l, __ldg(qT + qt_m + qi));
                 }
             }
         }
@@ -358,6 +364,7 @@ struct NearC {
     float2 c[6];
     float2 lin[4];   // linear-term coefficients (J rows: A, Phi; M rows: A, Phi)
     float2 cphi;     // charge form: coefficient of the triangle near part (c[1] is then 0)
+    float2 cphi2;    // two-region charge form: the same for the M rows (c[5] is then 0)
 };
 
 __global__ void __launch_bounds__(kThreads) k_final(const float2* __restrict__ part, const float2* __restrict__ xT,
@@ -368,7 +375,8 @@ __global__ void __launch_bounds__(kThreads) k_final(const float2* __restrict__ p
                                                     const float* __restrict__ la, const float* __restrict__ lp,
                                                     const float2* __restrict__ zn, float2* y, NearC nc, int F, int N,
                                                     int nunk, int P, int B, const float2* __restrict__ phiT,
-                                                    const int* __restrict__ btri_t, const double* __restrict__ blen) {
+                                                    const int* __restrict__ btri_t, const double* __restrict__ blen,
+                                                    int64_t pt_m) {
     __shared__ float2 accE[kFinalRows][kFinalB];
     __shared__ float2 accH[kFinalRows][kFinalB];
     const int G = F / 4;
@@ -463,12 +471,13 @@ __global__ void __launch_bounds__(kThreads) k_final(const float2* __restrict__ p
                 if (bl < nbc) {
                     float2 e = accE[r][bl] + nc.c[0] * aJ[h] + nc.c[1] * pJ[h];
                     if (F == 4 && nk) e = e + nc.c[2] * kJ[h];
-                    if (F == 4 && phiT)
-                        e = e + (float)blen[i] * (__ldg(phiT + (int64_t)btri_t[2 * i] * B + bc + bl) -
-                                                  __ldg(phiT + (int64_t)btri_t[2 * i + 1] * B + bc + bl));
+                    const int64_t tp = phiT ? (int64_t)btri_t[2 * i] * B + bc + bl : 0;
+                    const int64_t tm = phiT ? (int64_t)btri_t[2 * i + 1] * B + bc + bl : 0;
+                    if (phiT) e = e + (float)blen[i] * (__ldg(phiT + tp) - __ldg(phiT + tm));
                     if (F == 8) {
                         e = e + nc.c[2] * kM[h];
                         float2 hh = accH[r][bl] + nc.c[3] * kJ[h] + nc.c[4] * aM[h] + nc.c[5] * pM[h];
+                        if (phiT) hh = hh + (float)blen[i] * (__ldg(phiT + pt_m + tp) - __ldg(phiT + pt_m + tm));
                         y[(int64_t)(bc + bl) * nunk + N + perm[i]] = hh;
                     }
                     y[(int64_t)(bc + bl) * nunk + perm[i]] = e;
@@ -497,7 +506,7 @@ __global__ void __launch_bounds__(kNbWarps * 32) k_near_blk(
     const int* __restrict__ row_ptr, const int* __restrict__ perm, const int* __restrict__ lin_ptr,
     const int* __restrict__ lin_cols, const float* __restrict__ la, const float* __restrict__ lp, float2* y,
     NearC nc, int has_k, int N, int nunk, int P, int B, const float2* __restrict__ phiT,
-    const int* __restrict__ btri_t, const double* __restrict__ blen) {
+    const int* __restrict__ btri_t, const double* __restrict__ blen, int64_t pt_m) {
     extern __shared__ float2 xs[];                         // [union][32]
     __shared__ float2 accE[kNbRows][32];
     __shared__ float2 accH[F == 8 ? kNbRows : 1][32];
@@ -591,11 +600,12 @@ __global__ void __launch_bounds__(kNbWarps * 32) k_near_blk(
                 e = e + nc.c[2] * acc[k][5];
                 h = accH[r][lane] + nc.c[3] * acc[k][2] + nc.c[4] * acc[k][3] + nc.c[5] * acc[k][4];
             }
-            if (F == 4 && phiT) {
-                // charge form: D^T phi, phi the triangle potentials (nc.c[1] = 0 drops N^Phi)
-                const float2 pp = __ldg(phiT + (int64_t)btri_t[2 * i] * B + bc + lane);
-                const float2 pm = __ldg(phiT + (int64_t)btri_t[2 * i + 1] * B + bc + lane);
-                e = e + (float)blen[i] * (pp - pm);
+            if (phiT) {
+                // charge form: D^T phi, phi the triangle potentials (nc.c[1] = 0 drops N^Phi; two
+                // regions: the M rows' potentials follow at phiT + nt B and nc.c[5] = 0)
+                const int64_t tp = (int64_t)btri_t[2 * i] * B + bc + lane, tm = (int64_t)btri_t[2 * i + 1] * B + bc + lane;
+                e = e + (float)blen[i] * (__ldg(phiT + tp) - __ldg(phiT + tm));
+                if (F == 8) h = h + (float)blen[i] * (__ldg(phiT + pt_m + tp) - __ldg(phiT + pt_m + tm));
             }
             if (lin_ptr) {
                 // linear-term modification: a few overlapping pairs per row
@@ -1009,8 +1019,9 @@ __global__ void __launch_bounds__(2 * N) k_xy_inv_reg(const float2* __restrict__
             for (int x = 0; x < N; ++x) O[r * PITCH + x] = O[r * PITCH + x] + v[x];
         }
         __syncthreads();
-        if (CHG && f == 3) {
-            // charge form: triangle partials of the rho field, one per (triangle, stencil slot)
+        if (CHG && (f & 3) == 3) {
+            // charge form: triangle partials of the rho field (of J; f = 7: of M, the second
+            // block of tpart), one per (triangle, stencil slot)
             const int tlo = tplane[z], thi = tplane[Nz + z];
             for (int k = tlo + threadIdx.x; k < thi; k += blockDim.x) {
                 const int sx = tanc[3 * k], sy = tanc[3 * k + 1], slot = z - tanc[3 * k + 2];
@@ -1019,7 +1030,7 @@ __global__ void __launch_bounds__(2 * N) k_xy_inv_reg(const float2* __restrict__
                 for (int uy = 0; uy < P; ++uy)
                     for (int ux = 0; ux < P; ++ux)
                         rfma(sk, __ldg(lw + (int64_t)(uy * P + ux) * nt), O[(sy + uy) * PITCH + sx + ux]);
-                tpart[((int64_t)b * P + slot) * nt + k] = sk;
+                tpart[((int64_t)(f >> 2) * gridDim.z * P + (int64_t)b * P + slot) * nt + k] = sk;
             }
         } else if (P == 3) {
             // four bases per iteration so that their 36 weight gathers are in flight together
@@ -1230,13 +1241,15 @@ static void run_fused(aimx_ctx* ctx, const NearC& nc, int B, const float2* xb, f
     {
         const dim3 grid((unsigned)((NG + 15) / 16), (unsigned)((B + 31) / 32));
         const float4* w4 = reinterpret_cast<const float4*>(ctx->f32.w);
+        const int64_t qt_m = (int64_t)ctx->nt * B;   // M charges after the J charges (two-region)
         if (F == 8)
             k_gather_tile<8><<<grid, 256, 0, s>>>(w4, ctx->d_node_ptr, ctx->d_node_w, fb.xT, fb.G, B, N, U, NG,
-                                                  nullptr, nullptr, nullptr, nullptr);
+                                                  chg ? ctx->d_tnode_ptr : nullptr, ctx->d_tnode_w, ctx->f32.plw,
+                                                  reinterpret_cast<const float2*>(ctx->d_qT), qt_m);
         else
             k_gather_tile<4><<<grid, 256, 0, s>>>(w4, ctx->d_node_ptr, ctx->d_node_w, fb.xT, fb.G, B, N, U, NG,
                                                   chg ? ctx->d_tnode_ptr : nullptr, ctx->d_tnode_w, ctx->f32.plw,
-                                                  reinterpret_cast<const float2*>(ctx->d_qT));
+                                                  reinterpret_cast<const float2*>(ctx->d_qT), qt_m);
     }
     AIMX_CUDA_TRY(cudaGetLastError());
     delete sc;
@@ -1313,7 +1326,7 @@ static void run_fused(aimx_ctx* ctx, const NearC& nc, int B, const float2* xb, f
     AIMX_CUDA_TRY(cudaGetLastError());
     delete sc;
     sc = scope(ST_FINAL);
-    if (chg) charge_fused_phi(ctx, B, nc.cphi, s);
+    if (chg) charge_fused_phi(ctx, B, nc.cphi, nc.cphi2, s);
     const float2* phiT = chg ? reinterpret_cast<const float2*>(ctx->d_phiT) : nullptr;
     if (!ctx->aim && ctx->nb_count > 0) {
         const size_t smem = (size_t)ctx->nb_umax * 32 * sizeof(float2);
@@ -1324,7 +1337,7 @@ static void run_fused(aimx_ctx* ctx, const NearC& nc, int B, const float2* xb, f
             kern<<<ctx->nb_count, kNbWarps * 32, smem, s>>>(
                 fb.part, fb.xT, ctx->d_nb_rows, ctx->d_nb_ustart, ctx->d_nb_ucols, ctx->d_nb_ent, ctx->d_row_ptr,
                 ctx->d_perm, lp_, ctx->d_lin_cols, ctx->f32.la, ctx->f32.lp, yb, nc, has_k, N, nunk, P, B, phiT,
-                ctx->d_btri_t, ctx->d_blen);
+                ctx->d_btri_t, ctx->d_blen, (int64_t)ctx->nt * B);
         };
         // up to 16 RHS: each warp applies several entries at once
         const bool split = B <= 16;
@@ -1341,7 +1354,7 @@ static void run_fused(aimx_ctx* ctx, const NearC& nc, int B, const float2* xb, f
                                                                    ctx->aim ? reinterpret_cast<const float2*>(ctx->f32.zn)
                                                                             : nullptr,
                                                                    yb, nc, F, N, nunk, P, B, phiT, ctx->d_btri_t,
-                                                                   ctx->d_blen);
+                                                                   ctx->d_blen, (int64_t)ctx->nt * B);
     AIMX_CUDA_TRY(cudaGetLastError());
     delete sc;
 }
@@ -1351,11 +1364,16 @@ static NearC near_c(const aimx_ctx* ctx, double freq) {
     NearC nc;
     for (int k = 0; k < 6; ++k) nc.c[k] = make_float2((float)cf.near[k].x, (float)cf.near[k].y);
     for (int k = 0; k < 4; ++k) nc.lin[k] = make_float2((float)cf.lin[k].x, (float)cf.lin[k].y);
-    nc.cphi = make_float2(0.f, 0.f);
+    nc.cphi = nc.cphi2 = make_float2(0.f, 0.f);
     if (ctx->charge) {
         // charge form: the RWG N^Phi drops out; its coefficient scales the triangle near part
+        // (two regions: of the J rows, c[1], and of the M rows, c[5])
         nc.cphi = nc.c[1];
         nc.c[1] = make_float2(0.f, 0.f);
+        if (ctx->F == 8) {
+            nc.cphi2 = nc.c[5];
+            nc.c[5] = make_float2(0.f, 0.f);
+        }
     }
     if (ctx->aim) {
         // the per-frequency entries carry j w mu and -j w mu / k^2 already; they are exact on the

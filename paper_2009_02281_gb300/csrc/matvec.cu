@@ -155,8 +155,8 @@ __global__ void k_interp_near(const T* __restrict__ w, const T* __restrict__ wg,
                               const T* __restrict__ la, const T* __restrict__ lp,
                               const cplx_t<T>* __restrict__ zn,
                               const cplx_t<T>* __restrict__ grid, const cplx_t<T>* __restrict__ x,
-                              const cplx_t<T>* __restrict__ phi, const int* __restrict__ btri_t,
-                              const double* __restrict__ blen, int nt,
+                              const cplx_t<T>* __restrict__ phi, const cplx_t<T>* __restrict__ phim,
+                              const int* __restrict__ btri_t, const double* __restrict__ blen, int nt,
                               cplx_t<T>* y, NearCoefs nc0, const NearCoefs* __restrict__ ncs,
                               const int* __restrict__ fidx, int nrhs, int F, int two, int N, int nunk, int P,
                               int Mx, int My, int Mz) {
@@ -182,7 +182,7 @@ __global__ void k_interp_near(const T* __restrict__ w, const T* __restrict__ wg,
         if (wgi)
             for (int c = 0; c < 3; ++c) rfma(aE, wgi[3 * u + c], gb[(4 + c) * MT + node]);
         else if (two)
-            for (int f = 0; f < 4; ++f) rfma(aH, wi[4 * u + f], gb[(4 + f) * MT + node]);
+            for (int f = 0; f < nfe; ++f) rfma(aH, wi[4 * u + f], gb[(4 + f) * MT + node]);
     }
     const C* xb = x + (int64_t)b * nunk;
     if (lin_ptr) {
@@ -249,8 +249,17 @@ __global__ void k_interp_near(const T* __restrict__ w, const T* __restrict__ wg,
             rfma(pM, np[e], xm);
             rfma(kM, nk[e], xm);
         }
-        aE = aE + cA * aJ + cP * pJ + cK * kM;
-        aH = aH + dK * kJ + dA * aM + dP * pM;
+        if (phi) {
+            // two-region charge form: D^T phi of J in the E rows, of M (phim) in the H rows
+            const C* pb = phi + (int64_t)b * nt;
+            const C* qb = phim + (int64_t)b * nt;
+            const int tp = btri_t[2 * i], tm = btri_t[2 * i + 1];
+            aE = aE + cA * aJ + (T)blen[i] * (pb[tp] - pb[tm]) + cK * kM;
+            aH = aH + dK * kJ + dA * aM + (T)blen[i] * (qb[tp] - qb[tm]);
+        } else {
+            aE = aE + cA * aJ + cP * pJ + cK * kM;
+            aH = aH + dK * kJ + dA * aM + dP * pM;
+        }
         y[(int64_t)b * nunk + perm[i]] = aE;
         y[(int64_t)b * nunk + N + perm[i]] = aH;
     }
@@ -334,9 +343,11 @@ static void generic_product(aimx_ctx* ctx, double freq, const MultiFreq* mf, int
     }
     C* grid = reinterpret_cast<C*>(pd.grid);
     const bool chg = ctx->charge != 0;
-    C *cq = nullptr, *cphi = nullptr;
+    C *cq = nullptr, *cphi = nullptr, *cqm = nullptr, *cphim = nullptr;
+    if (chg && mf && two)
+        throw Error{AIMX_E_STATE, "the two-region charge form has no multi-frequency product"};
     if (chg) {
-        const size_t need = 2 * (size_t)ctx->nt * chunk;
+        const size_t need = (two ? 4 : 2) * (size_t)ctx->nt * chunk;
         if (pd.cwork_elems < need) {
             if (pd.cwork) dev_free(ctx, pd.cwork);
             pd.cwork = (T*)dev_alloc(ctx, sizeof(C) * need);
@@ -344,6 +355,10 @@ static void generic_product(aimx_ctx* ctx, double freq, const MultiFreq* mf, int
         }
         cq = reinterpret_cast<C*>(pd.cwork);
         cphi = cq + (size_t)ctx->nt * chunk;
+        if (two) {   // M charges and potentials (two-region form)
+            cqm = cphi + (size_t)ctx->nt * chunk;
+            cphim = cqm + (size_t)ctx->nt * chunk;
+        }
     }
     const C* xc = reinterpret_cast<const C*>(x);
     C* yc = reinterpret_cast<C*>(y);
@@ -360,7 +375,10 @@ static void generic_product(aimx_ctx* ctx, double freq, const MultiFreq* mf, int
             pd.w, ctx->d_node_ptr, ctx->d_node_w, ctx->d_node_x, xc + (int64_t)b0 * ctx->nunk, grid, nb,
             two ? 8 : 4, F, ctx->N, ctx->nunk, ctx->n[0], ctx->n[1], ctx->n[2], ctx->M[0], ctx->M[1], ctx->M[2]);
         AIMX_CUDA_TRY(cudaGetLastError());
-        if (chg) charge_project<T>(ctx, xc + (int64_t)b0 * ctx->nunk, nb, cq, grid, F, 3, s);
+        if (chg) {
+            charge_project<T>(ctx, xc + (int64_t)b0 * ctx->nunk, nb, cq, grid, F, 3, s);
+            if (two) charge_project<T>(ctx, xc + (int64_t)b0 * ctx->nunk + ctx->N, nb, cqm, grid, F, 7, s);
+        }
         if (ctx->path == 2)
             cufft_padded<T>(ctx, grid, nb * F, CUFFT_FORWARD, s);
         else
@@ -378,16 +396,20 @@ static void generic_product(aimx_ctx* ctx, double freq, const MultiFreq* mf, int
             cufft_padded<T>(ctx, grid, nb * F, CUFFT_INVERSE, s);
         else
             fft3d_padded<T>(reinterpret_cast<T*>(grid), nb * F, ctx->M, act, true, s);
-        if (chg)
+        if (chg) {
             charge_potential<T>(ctx, grid, F, 3, nb, cq, cphi, nc.c[1], s, mf ? mf->d_cphi : nullptr,
                                 mf ? mf->d_fidx + b0 : nullptr);
+            // two-region: the M rows' potentials, with the M block's scalar-potential coefficient
+            if (two) charge_potential<T>(ctx, grid, F, 7, nb, cqm, cphim, nc.c[5], s, nullptr, nullptr);
+        }
         int64_t tn = (int64_t)ctx->N * nb;
         k_interp_near<T><<<(unsigned)((tn + 127) / 128), 128, 0, s>>>(
             pd.w, ctx->form == AIMX_CFIE ? pd.wg : nullptr, ctx->d_anc, ctx->d_perm, ctx->d_row_ptr, ctx->d_cols,
             pd.na, pd.np, ctx->form == AIMX_EFIE ? nullptr : pd.nk, two ? nullptr : pd.ng,
             ctx->linterm && !ctx->aim ? ctx->d_lin_ptr : nullptr, ctx->d_lin_cols, pd.la, pd.lp,
             ctx->aim ? reinterpret_cast<const C*>(pd.zn) : nullptr, grid,
-            xc + (int64_t)b0 * ctx->nunk, chg ? cphi : nullptr, ctx->d_btri_t, ctx->d_blen, ctx->nt,
+            xc + (int64_t)b0 * ctx->nunk, chg ? cphi : nullptr, chg ? cphim : nullptr, ctx->d_btri_t, ctx->d_blen,
+            ctx->nt,
             yc + (int64_t)b0 * ctx->nunk, nc, mf ? mf->d_ncs : nullptr, mf ? mf->d_fidx + b0 : nullptr, nb, F,
             two ? 1 : 0, ctx->N, ctx->nunk, ctx->P, ctx->M[0], ctx->M[1], ctx->M[2]);
         AIMX_CUDA_TRY(cudaGetLastError());

@@ -1,4 +1,5 @@
-"""GPU parity of the charge-form scalar potential (L^Phi = D^T Pt D with Pt in AIMx form).
+"""GPU parity of the charge-form scalar potential (L^Phi = D^T Pt D with Pt in AIMx form),
+for the EFIE and for both regions of the PMCHWT.
 
 Setup against the oracle (``oracle/chargepot.py``, pinned by its own CPU tests): triangle
 anchors and the triangle near pattern bit-exact, pulse weights and the static near values
@@ -203,9 +204,9 @@ def test_solve_matches_dense_lu(l2, torch_cuda):
 
 def test_state_errors(torch_cuda):
     from synth import icosphere
-    from paper_2009_02281_gb300 import AimxError, Context, EFIE, PMCHWT
+    from paper_2009_02281_gb300 import AimxError, Context, EFIE, CFIE
     xyz, tri = icosphere(1)
-    c = Context(xyz, tri, (8, 8, 8), formulation=PMCHWT, eps_in=2.0)
+    c = Context(xyz, tri, (8, 8, 8), formulation=CFIE)
     with pytest.raises(AimxError) as e:
         c.set_charge_form(True)
     assert e.value.code == -7
@@ -224,3 +225,95 @@ def test_state_errors(torch_cuda):
         c.set_conventional_aim(True)
     assert e.value.code == -7
     c.close()
+
+
+# ------------------------------------------------------------------ two-region (PMCHWT) charge form
+
+@pytest.fixture(scope="module")
+def l2p(torch_cuda):
+    """Level-2 icosphere, eps_r = 4 inside, 16^3 grid (plane-fused path), two-region charge form."""
+    from synth import icosphere
+    from oracle import operator as op, chargepot as cp
+    from paper_2009_02281_gb300 import Context, PMCHWT
+    xyz, tri = icosphere(2)
+    grid = (16, 16, 16)
+    ctx = Context(xyz, tri, grid, order=2, formulation=PMCHWT, eps_out=1.0, eps_in=4.0)
+    ctx.set_charge_form(True)
+    prob = op.setup(xyz, tri, 2, grid, radius=3)
+    ch = cp.setup_charge(prob)
+    yield ctx, prob, ch
+    ctx.close()
+
+
+@pytest.mark.parametrize("nrhs", [1, 5, 37])
+@pytest.mark.parametrize("path", [0, 1])
+def test_pmchwt_product_matches_oracle(l2p, torch_cuda, nrhs, path):
+    """Both regions' scalar potentials in charge form, in the J and the M blocks, against
+    ``matvec_pmchwt_charge``: plane-fused and generic paths, FP32 per RHS and FP64."""
+    torch = torch_cuda
+    from synth import random_complex
+    from oracle import chargepot as cp
+    from paper_2009_02281_gb300 import F32
+    ctx, prob, ch = l2p
+    ctx.set_path(path)
+    assert ctx.matvec_path(F32) == path
+    f = 1.1 * C0 / (2 * np.pi)
+    x = random_complex((nrhs, ctx.nunk), seed=80 + nrhs)
+    ref = np.stack([cp.matvec_pmchwt_charge(prob, ch, f, xi, 1.0, 4.0) for xi in x])
+    y32 = ctx.matvec(f, torch.tensor(x, dtype=torch.complex64, device="cuda")).cpu().numpy()
+    y64 = ctx.matvec(f, torch.tensor(x, dtype=torch.complex128, device="cuda")).cpu().numpy()
+    ctx.set_path(0)
+    for b in range(nrhs):
+        assert _rel(y32[b], ref[b]) <= TOL32, b
+    assert _rel(y64, ref) <= TOL64
+
+
+def test_pmchwt_solve_matches_dense_lu_and_sweep_refused(l2p, torch_cuda):
+    """Plane-wave solve of the two-region charge form against the oracle's dense LU (1e-4);
+    the batched sweep has no two-region charge product and says so."""
+    from synth import planewave_batch
+    from oracle import chargepot as cp, solve as osolve, excitation
+    from oracle.constants import ETA0
+    from paper_2009_02281_gb300 import AimxError
+    ctx, prob, ch = l2p
+    k = 0.9
+    f = k * C0 / (2 * np.pi)
+    dirs, pols = planewave_batch(1, seed=15)
+    b = ctx.rhs_planewave(f, dirs, pols)
+    x, stats, rc = ctx.solve(f, b, tol=1e-9, restart=100, max_iter=3000)
+    assert rc == 0, stats
+    Z = cp.dense_pmchwt_charge(prob, ch, f, 1.0, 4.0)
+    VE, VH = excitation.planewave_rhs(prob["rwg"], k, dirs[0], pols[0], eta=ETA0)
+    ref = osolve.lu_solve(Z, np.r_[VE, ETA0 * VH])
+    assert _rel(x.cpu().numpy()[0], ref) <= 1e-4
+    with pytest.raises(AimxError) as e:
+        ctx.sweep_batched(np.array([f, 1.1 * f]), torch_cuda.stack([b, b]), tol=1e-6)
+    assert e.value.code == -7
+
+
+def test_pmchwt_sampled_rows_larger_mesh(torch_cuda):
+    """Level-4 icosphere (15360 unknowns) on a 32^3 grid, 40 RHS through the plane-fused path:
+    sampled rows of both blocks against the oracle's row-restricted two-region product."""
+    torch = torch_cuda
+    from synth import icosphere, random_complex
+    from oracle import operator as op, chargepot as cp
+    from oracle.rwg import rwg_arrays
+    from paper_2009_02281_gb300 import Context, PMCHWT, F32
+    xyz, tri = icosphere(4)
+    grid = (32, 32, 32)
+    ctx = Context(xyz, tri, grid, order=2, formulation=PMCHWT, eps_out=1.0, eps_in=4.0)
+    ctx.set_charge_form(True)
+    assert ctx.matvec_path(F32) == 0
+    N = ctx.N
+    rows = np.array([0, N // 3, N - 1])
+    prob = op.setup(xyz, tri, 2, grid, radius=3, near_rows=rows)
+    tris = np.unique(rwg_arrays(prob["rwg"])[0][rows].ravel())
+    ch = cp.setup_charge(prob, tri_rows=tris)
+    f = 3.0 * C0 / (2 * np.pi)
+    B = 40
+    x = random_complex((B, ctx.nunk), seed=81)
+    y = ctx.matvec(f, torch.tensor(x, dtype=torch.complex64, device="cuda")).cpu().numpy()
+    ctx.close()
+    for b in (0, B - 1):
+        ref = cp.matvec_pmchwt_charge(prob, ch, f, x[b], 1.0, 4.0, rows=rows)
+        assert _rel(np.r_[y[b, rows], y[b, N + rows]], ref) <= TOL32, b
