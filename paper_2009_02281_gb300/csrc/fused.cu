@@ -23,6 +23,9 @@
 // Every sum has a fixed order, so results are bitwise reproducible.
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -1119,7 +1122,19 @@ static bool reg_path(const aimx_ctx* ctx) { return ctx->sched_variant != 1 && re
 
 template <class K>
 static void set_smem(K kernel, size_t bytes) {
-    AIMX_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    // The limit is one value per kernel and device for the whole process, and the host threads
+    // of a batch launch the same kernel for members of different sizes: it only ever grows, so a
+    // launch never finds it lowered by another thread between setting it and launching.
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> granted;
+    int dev = 0;
+    AIMX_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& g = granted[{dev, reinterpret_cast<const void*>(kernel)}];
+    if (bytes > g) {
+        AIMX_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+        g = bytes;
+    }
 }
 
 static int num_sms() {
